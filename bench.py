@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the TT-rounding hot path on one GB300 (or N replicas).
+
+Workload (one step): the rank-concatenating sum of 20 random TT tensors
+(order 10, mode size 64, ranks 20, iid N(0,1) cores, coefficients U(-1,1);
+concatenated rank 400) followed by TT-round at delta = 1e-6, through the C ABI
+(tt_add + tt_round).  Inputs are uploaded once and stay resident in HBM; a
+256 MB buffer is written between timed steps to flush the 129 MB L2.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
+the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TT-roundings/s at δ-accuracy, mixed vs FP64 on one GB300; serve p50/p99 latency"
+UNIT = "roundings/s"
+DELTA = 1e-6
+WORKLOAD = "sum of 20 random TTs (d=10, n=64, ranks 20, N(0,1) cores, alpha~U(-1,1); concatenated rank 400) + TT-round at delta=1e-6"
+
+# nominal / measured peaks (MEASURED_PEAKS.json when present)
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return j, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def roofline_for(fam, prof, peaks, src):
+    """bound, achieved, peak, unit for one kernel family."""
+    secs = prof["total_ms"] / 1e3
+    if fam == "gram_tf32_tc" or fam.startswith("gemm_tf32"):
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * NOMINAL_TF32_OVER_BF16
+        return "tensor", prof["flops"] / secs / 1e12, peak, "TFLOP/s", (
+            "%s sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25" % src)
+    if fam in ("gemm_f32", "gram_f32"):
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        return "alu", prof["flops"] / secs / 1e12, peak, "TFLOP/s", "152 SMs x 128 FP32 lanes x 2 x max SM clock"
+    if fam in ("gemm_f64", "gram_f64"):
+        return "alu", prof["flops"] / secs / 1e12, 1.25, "TFLOP/s", "nominal GB300 FP64 rate"
+    return "hbm", prof["bytes"] / secs / 1e9, peaks["hbm_gbs"], "GB/s", "%s HBM copy bandwidth" % src
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_step(al, xs):
+    import oracle as O
+    return O.tt_round(O.tt_add(list(al), xs), DELTA)
+
+
+def cpu_baseline_sample(al, xs, budget_s=30.0):
+    """The oracle (unchanged) on the host cores: whole rounding steps of the
+    same workload until about budget_s seconds have elapsed (at least one)."""
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle_step(al, xs)
+        n += 1
+        el = time.perf_counter() - t0
+        if el + el / n > budget_s:
+            break
+    return {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d full rounding(s) of the workload (NumPy/LAPACK FP64, default BLAS threads)" % n}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from ttinputs import cfg_round_sum
+    al, xs = cfg_round_sum(0)
+    for _ in range(args.warmup):
+        oracle_step(al, xs)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(al, xs)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = args.steps / tot
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "delta": DELTA, "implementation": "CPU FP64 oracle (NumPy/LAPACK)"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": "one full rounding of the workload per step"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    from paper_2211_08770_gb300 import build as B
+    B.build()
+    from paper_2211_08770_gb300 import ttgb as T
+    from ttinputs import cfg_round_sum
+
+    peaks, peak_src = load_peaks()
+    al, xs = cfg_round_sum(0)
+    stream = torch.cuda.Stream(device=local)
+
+    def time_path(precision, steps, warmup, profile):
+        ctx = T.Ctx(local, precision, stream=stream.cuda_stream)
+        X = [T.tt_tensor_create(ctx, c) for c in xs]
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:%d" % local)
+
+        def step():
+            s = T.tt_add(ctx, al, X)
+            y, err = T.tt_round(ctx, s, DELTA)
+            r = y.ranks
+            s.free()
+            y.free()
+            return r, err
+
+        for _ in range(warmup):
+            ranks, err = step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ctx.reset_stats()
+        ctx.reset_profile()
+        ctx.set_profiling(profile)
+        evs = []
+        clocks = ClockSampler(local)
+        clocks.start()
+        wall0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ranks, err = step()
+                e1.record(stream)
+                evs.append((e0, e1))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        ck = clocks.stop()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        stats = ctx.stats()
+        prof = ctx.profile() if profile else {}
+        ctx.set_profiling(False)
+        tot_ms = sum(ms)
+        if dist:
+            t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda:%d" % local)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot_ms = float(t.item())
+        for x in X:
+            x.free()
+        ctx.close()
+        return dict(ms=ms, tot_ms=tot_ms, wall=wall, clocks=ck, stats=stats, prof=prof, ranks=ranks, err=err)
+
+    def time_e2e(precision, steps):
+        ctx = T.Ctx(local, precision, stream=stream.cuda_stream)
+        es = 8 if precision == "fp64" else 4
+        h2d = sum(c.size for c in xs) * es
+        times, d2h = [], 0
+        for i in range(steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            X = [T.tt_tensor_create(ctx, c) for c in xs]
+            s = T.tt_add(ctx, al, X)
+            y, _ = T.tt_round(ctx, s, DELTA)
+            cores = y.cores()
+            t1 = time.perf_counter()
+            d2h = sum(c.size for c in cores) * es
+            for v in X + [s, y]:
+                v.free()
+            if i > 0:
+                times.append(t1 - t0)
+        ctx.close()
+        return dict(value=world * len(times) / sum(times), unit=UNIT, h2d_bytes_per_step=int(h2d),
+                    d2h_bytes_per_step=int(d2h))
+
+    prec = args.precision
+    main = time_path(prec, args.steps, args.warmup, profile=True)
+    value = world * args.steps / (main["tot_ms"] / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": main["tot_ms"] / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"mixed_tf32": "f32 storage, tf32 tensor-core Gram", "fp32": "f32", "fp64": "f64"}[prec],
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "delta": DELTA, "precision": prec, "parallelism": "replicas" if world > 1 else "single GPU",
+                      "l2": "256 MB buffer written between timed steps (working set ~0.5 GB > 129 MB L2)",
+                      "output_ranks": main["ranks"]},
+           "gpu_launches": int(main["stats"]["kernel_launches"]),
+           "host_syncs": int(main["stats"]["host_syncs"]),
+           "clocks": main["clocks"]}
+    # roofline of the dominant kernel family
+    prof = main["prof"]
+    if prof:
+        fam = max(prof, key=lambda k: prof[k]["total_ms"])
+        bound, ach, peak, unit, how = roofline_for(fam, prof[fam], peaks, peak_src)
+        traffic = None
+        tp = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tp):
+            with open(tp) as f:
+                tj = json.load(f)
+            ent = tj.get(fam)
+            if ent and ent.get("workload") == WORKLOAD and ent.get("source_hash") == _src_hash():
+                traffic = ent.get("bytes_per_launch")
+        out["roofline"] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                           "traffic": traffic, "kernel": fam, "peak_source": how,
+                           "launches": prof[fam]["launches"],
+                           "avg_launch_ms": prof[fam]["total_ms"] / max(1, prof[fam]["launches"]),
+                           "share_of_step": prof[fam]["total_ms"] / max(1e-9, sum(main["ms"]))}
+        out["kernel_profile"] = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4)} for k, v in
+                                 sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])}
+    if prec != "fp64" and not args.no_fp64:
+        f = time_path("fp64", args.fp64_steps, 1, profile=False)
+        fv = world * args.fp64_steps / (f["tot_ms"] / 1e3)
+        out["fp64_path"] = {"value": fv, "unit": UNIT, "ms_per_step": f["tot_ms"] / args.fp64_steps,
+                            "steps": args.fp64_steps, "output_ranks": f["ranks"]}
+        out["speedup_vs_fp64"] = value / fv
+    out["e2e"] = time_e2e(prec, args.e2e_steps)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline_sample(al, xs, budget_s=args.cpu_budget)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def _src_hash():
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2211_08770_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed_tf32", choices=["mixed_tf32", "fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=25.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

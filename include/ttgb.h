@@ -1,0 +1,229 @@
+/*
+ * ttgb.h - C ABI of the GB300 TT-rounding library.
+ *
+ * Implements the hot path of Coulaud, Giraud & Iannacito, "On some
+ * orthogonalization schemes in Tensor Train format": TT sums, TT dot
+ * products, TT-rounding and the six TT orthogonalization schemes
+ * (Algorithms 1-8), on one GPU, in hand-written CUDA for sm_103a.
+ *
+ * TT format (Section 2): x = x_1 x_2 ... x_d with cores
+ * x_k in R^{r_{k-1} x n_k x r_k}, r_0 = r_d = 1.  A core is stored on the
+ * device row-major as [r_{k-1}][n_k][r_k] (r_k fastest), so its left
+ * unfolding (r_{k-1} n_k) x r_k and its right unfolding r_{k-1} x (n_k r_k)
+ * are both contiguous row-major matrices.
+ *
+ * Conventions shared by every entry point:
+ *  - All calls are ordered on the context's CUDA stream.  Calls that return
+ *    a host scalar (tt_dot, tt_norm, tt_round's ranks, ...) synchronize that
+ *    stream before returning.
+ *  - Inputs are never modified.  Every tt_tensor** output is allocated by the
+ *    library and released with tt_tensor_free.  On error no output is
+ *    produced: *out is set to NULL and nothing has to be freed.
+ *  - Errors: a NULL pointer, d < 1, m < 1, delta < 0 or NaN, r_0 != 1,
+ *    r_d != 1 or a rank < 1 give TT_ERR_ARG; differing orders or mode sizes
+ *    give TT_ERR_SHAPE; an allocation beyond the context's HBM budget (or a
+ *    failed device allocation) gives TT_ERR_OOM; a failed CUDA call gives
+ *    TT_ERR_CUDA (the message is kept, see tt_last_error).
+ *  - The library is not thread-safe per context; distinct contexts may be
+ *    used from distinct threads.
+ */
+#ifndef TTGB_H
+#define TTGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TT_OK = 0,
+    TT_ERR_ARG = 1,        /* invalid argument */
+    TT_ERR_SHAPE = 2,      /* orders or mode sizes differ */
+    TT_ERR_OOM = 3,        /* HBM budget exceeded or device allocation failed */
+    TT_ERR_NOT_SPD = 4,    /* TT-Gram: Cholesky of the Gram matrix failed */
+    TT_ERR_BREAKDOWN = 5,  /* zero vector where a scheme normalises */
+    TT_ERR_NONFINITE = 6,  /* NaN or Inf met in a result */
+    TT_ERR_TIMEOUT = 7,    /* a bounded device wait ran out */
+    TT_ERR_CUDA = 8        /* a CUDA runtime call failed */
+} tt_status;
+
+/* Arithmetic of a context.
+ * TT_FP64:       cores, GEMMs, Cholesky, SVD and norms in FP64.
+ * TT_MIXED_TF32: cores stored in FP32; Gram matrices of the CholQR passes on
+ *                tcgen05 tensor cores in TF32 with FP32 accumulation; the
+ *                GEMMs that produce core values (apply / absorb) in split
+ *                TF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation); small r x r
+ *                factorizations in FP32; norm, thresholds, tail sums and the
+ *                truncation SVD in FP64.
+ * TT_FP32:       cores and every GEMM in FP32 on CUDA cores (no tensor
+ *                cores); small factorizations as TT_MIXED_TF32. */
+typedef enum { TT_FP64 = 0, TT_MIXED_TF32 = 1, TT_FP32 = 2 } tt_precision;
+
+/* Algorithms 1-5 and 8. */
+typedef enum {
+    TT_CGS = 0, TT_MGS = 1, TT_CGS2 = 2, TT_MGS2 = 3, TT_GRAM = 4, TT_HOUSEHOLDER = 5
+} tt_scheme;
+
+/* TT_ROUND_PAPER rounds where Algorithms 1-5 and 8 round.
+ * TT_ROUND_EVERY_UPDATE also rounds the running vector after every axpy of
+ * the projection loops (for Householder: every reflected a_j); a loop that
+ * makes no update keeps the single rounding of the paper policy. */
+typedef enum { TT_ROUND_PAPER = 0, TT_ROUND_EVERY_UPDATE = 1 } tt_round_policy;
+
+/* Householder sign rule for r(i) in TTH-vec (Algorithm 6).
+ * TT_SIGN_STABLE: r(i) = -sign(<a, f_i>) sqrt(||a||^2 - s), the
+ * cancellation-free choice of Section 3.3 (default).
+ * TT_SIGN_LITERAL: r(i) = +sign(<a, f_i>) sqrt(...), as printed in the
+ * listing.  sign(0) = +1 in both. */
+typedef enum { TT_SIGN_STABLE = 0, TT_SIGN_LITERAL = 1 } tt_sign_rule;
+
+/* Storage type of a tensor's cores. */
+typedef enum { TT_DTYPE_F64 = 0, TT_DTYPE_F32 = 1 } tt_dtype;
+
+typedef struct tt_ctx tt_ctx;        /* stream, workspace, HBM budget, stats */
+typedef struct tt_tensor tt_tensor;  /* d, n[], r[], device cores */
+
+/* Counters of a context (reset by tt_ctx_reset_stats). */
+typedef struct {
+    uint64_t kernel_launches;  /* kernels this library launched */
+    uint64_t roundings;        /* tt_round calls, including those inside schemes */
+    uint64_t host_syncs;       /* stream synchronizations made */
+    uint64_t bytes_in_use;     /* device bytes held by live tensors + workspace */
+    uint64_t peak_bytes;       /* high-water mark of bytes_in_use */
+    uint64_t svd_calls;        /* truncation SVDs actually computed */
+    uint64_t certified_bonds;  /* bonds kept whole by the sigma_min certificate */
+    uint64_t fallback_orth;    /* orthogonalizations that took the shifted path */
+} tt_stats;
+
+/* Per-kernel timing of a context (tt_ctx_set_profiling): CUDA events are
+ * recorded on the context's stream around every instrumented launch. */
+typedef struct {
+    char name[32];       /* kernel family, e.g. "gram_tf32_tc", "gemm_f32" */
+    uint64_t launches;
+    double total_ms;     /* sum of event-measured durations */
+    double flops;        /* algorithmic floating-point operations */
+    double bytes;        /* algorithmic HBM bytes (operands read + result written) */
+} tt_kernel_profile;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t owned by the caller (NULL = the legacy default stream).
+ * `hbm_budget` caps the device bytes the context may hold (0 = no cap);
+ * a call that would exceed it fails with TT_ERR_OOM before touching the GPU.
+ * Returns TT_ERR_CUDA if the device is absent or not sm_103. */
+tt_status tt_ctx_create(tt_ctx** ctx, int device, tt_precision prec,
+                        void* cuda_stream, size_t hbm_budget);
+void      tt_ctx_destroy(tt_ctx* ctx);
+tt_status tt_ctx_get_stats(const tt_ctx* ctx, tt_stats* out);
+void      tt_ctx_reset_stats(tt_ctx* ctx);
+tt_precision tt_ctx_precision(const tt_ctx* ctx);
+
+/* Enables (on != 0) or disables event timing of the library's launches. */
+tt_status tt_ctx_set_profiling(tt_ctx* ctx, int on);
+/* Synchronizes the stream and writes up to max_entries aggregated records
+ * (one per kernel family, since the last reset) to out; *n_entries receives
+ * the number of families. */
+tt_status tt_ctx_get_profile(tt_ctx* ctx, tt_kernel_profile* out, int max_entries, int* n_entries);
+void      tt_ctx_reset_profile(tt_ctx* ctx);
+
+/* ---- tensors ---------------------------------------------------------- */
+
+/* Creates a TT with d cores, mode sizes n[0..d-1] and ranks r[0..d]
+ * (r[0] = r[d] = 1) in the context's storage type.  host_cores[k] points to
+ * r[k]*n[k]*r[k+1] doubles in the [r][n][r] layout, copied to the device
+ * (converted to FP32 for FP32 contexts); host_cores == NULL gives zeros.
+ * The host arrays are read before the call returns. */
+tt_status tt_tensor_create(tt_ctx* ctx, int d, const int* n, const int* r,
+                           const double* const* host_cores, tt_tensor** out);
+
+/* Wraps caller-owned device cores (dev_cores[k], [r][n][r] layout, dtype
+ * `dtype`, which must be the context's storage type) without copying.  The
+ * caller keeps ownership and must keep the memory alive until tt_tensor_free
+ * of the wrapper. */
+tt_status tt_tensor_wrap_device(tt_ctx* ctx, int d, const int* n, const int* r,
+                                void* const* dev_cores, int dtype, tt_tensor** out);
+
+/* d (if not NULL), n[0..d-1] and r[0..d] (if not NULL; caller-sized). */
+tt_status tt_tensor_shape(const tt_tensor* x, int* d, int* n, int* r);
+
+/* Device pointer of core k (for zero-copy readers). */
+tt_status tt_tensor_core_ptr(const tt_tensor* x, int k, void** dev_ptr);
+
+/* Copies the cores to host_cores[k] (r[k]*n[k]*r[k+1] doubles each). */
+tt_status tt_tensor_download(tt_ctx* ctx, const tt_tensor* x, double* const* host_cores);
+
+void tt_tensor_free(tt_tensor* x);
+
+/* ---- TT arithmetic (Section 2) ---------------------------------------- */
+
+/* out = sum_j alpha[j] x[j] by rank concatenation (Section 2: the k-th
+ * TT-rank of x + y is r_k + s_k).  alpha is a host array of m doubles.
+ * First core: [alpha_1 X_1 ... alpha_m X_m]; interior cores block diagonal;
+ * last core stacked.  For d = 1 the single core is the linear combination. */
+tt_status tt_add(tt_ctx* ctx, int m, const double* alpha,
+                 const tt_tensor* const* x, tt_tensor** out);
+
+/* out = alpha x (the last core scaled). */
+tt_status tt_scale(tt_ctx* ctx, const tt_tensor* x, double alpha, tt_tensor** out);
+
+/* <x, y> by the left-to-right contraction W_k = sum_i X_k(i)^T W_{k-1}
+ * Y_k(i), W_0 = 1 (the inner product of Algorithms 1-8).  *out is a host
+ * double. */
+tt_status tt_dot(tt_ctx* ctx, const tt_tensor* x, const tt_tensor* y, double* out);
+
+/* out[j] = <x, y[j]> for j < count, one contraction per pair, batched. */
+tt_status tt_dot_many(tt_ctx* ctx, const tt_tensor* x, int count,
+                      const tt_tensor* const* y, double* out);
+
+/* ||x|| = ||core_1||_F after right-to-left orthogonalization of a copy
+ * (no cancellation, unlike sqrt(<x, x>)). */
+tt_status tt_norm(tt_ctx* ctx, const tt_tensor* x, double* out);
+
+/* TT-round(x, delta) (Section 2): *out = x~ with ||x - x~|| <= delta ||x||.
+ * Right-to-left orthogonalization of the right unfoldings by Cholesky QR
+ * passes (Gram on the GPU, R factor absorbed into the left neighbour), then a
+ * left-to-right sweep truncating each bond at eps = delta ||x|| / sqrt(d-1)
+ * (minimal rank whose discarded singular values have root-sum-square
+ * <= eps, never below 1).  d = 1 returns a copy.  err_est (may be NULL)
+ * receives the root-sum-square of everything discarded, relative to ||x||.
+ * The output's cores 1..d-1 are left-orthonormal. */
+tt_status tt_round(tt_ctx* ctx, const tt_tensor* x, double delta,
+                   tt_tensor** out, double* err_est);
+
+/* Rounds count independent tensors, each at its own delta[i], reusing one
+ * workspace and overlapping their work on the context's stream.  out[i] is
+ * set for every i, or all are NULL on error. */
+tt_status tt_round_batched(tt_ctx* ctx, int count, const tt_tensor* const* x,
+                           const double* delta, tt_tensor** out);
+
+/* ---- orthogonalization (Section 3) ------------------------------------ */
+
+/* Orthogonalizes A[0..m-1] with `scheme` (Algorithms 1-5, 8) at rounding
+ * accuracy delta.  Q[0..m-1] receive the basis (library-allocated), R
+ * (host, m*m doubles, column-major) the upper triangular factor: column i
+ * holds the coefficients of a_i, so a_i ~ sum_j R(j,i) q_j.  n_rounds (may
+ * be NULL) receives the number of TT-round calls made.  TT_GRAM returns
+ * TT_ERR_NOT_SPD when the Cholesky factorization of the Gram matrix fails
+ * (remark on the Gram breakdown); a zero vector where a scheme normalises
+ * gives TT_ERR_BREAKDOWN.  For TT_HOUSEHOLDER prod(n) must be >= m. */
+tt_status tt_orthogonalize(tt_ctx* ctx, tt_scheme scheme, double delta,
+                           tt_round_policy policy, int m,
+                           const tt_tensor* const* A, tt_tensor** Q,
+                           double* R, int* n_rounds);
+
+/* Householder sign rule used by subsequent TT_HOUSEHOLDER calls. */
+tt_status tt_set_sign_rule(tt_ctx* ctx, tt_sign_rule rule);
+
+/* ---- diagnostics ------------------------------------------------------- */
+
+const char* tt_status_str(tt_status s);
+/* Message of the last failed CUDA call on this thread ("" if none). */
+const char* tt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTGB_H */

@@ -1,0 +1,76 @@
+// Definitions shared by the host-side translation units of the C ABI.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+struct tt_ctx : public ttgb::Ctx {};
+
+struct tt_tensor {
+    tt_ctx* ctx = nullptr;
+    int d = 0;
+    std::vector<int> n, r;
+    tt_dtype dtype = TT_DTYPE_F64;
+    std::vector<void*> cores;
+    void* block = nullptr;   // owned allocation holding every core
+    size_t bytes = 0;
+    bool owned = false;
+    double norm_hint = -1.0; // ||x|| when known exactly from the producer (>= 0)
+    size_t core_elems(int k) const { return (size_t)r[k] * n[k] * r[k + 1]; }
+};
+
+namespace ttgb {
+
+void set_last_error(const std::string& s);
+size_t dtype_size(tt_dtype t);
+tt_dtype storage_of(tt_precision p);
+void validate_shape(int d, const int* n, const int* r);
+tt_tensor* new_tensor(tt_ctx* ctx, int d, const int* n, const int* r);
+void free_tensor(tt_tensor* t);
+tt_tensor* copy_tensor(tt_ctx* ctx, const tt_tensor* x);
+void check_same_modes(const tt_tensor* a, const tt_tensor* b);
+void check_tensor(tt_ctx* ctx, const tt_tensor* x);
+tt_tensor* tt_add_internal(tt_ctx* ctx, int m, const double* alpha, const tt_tensor* const* x);
+tt_tensor* scale_internal(tt_ctx* ctx, const tt_tensor* x, double alpha);
+void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out);
+tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est);
+double norm_internal(tt_ctx* ctx, const tt_tensor* x);
+
+// RAII owner for tensors created inside drivers
+struct TensorGuard {
+    tt_tensor* t = nullptr;
+    TensorGuard() = default;
+    explicit TensorGuard(tt_tensor* x) : t(x) {}
+    TensorGuard(const TensorGuard&) = delete;
+    TensorGuard& operator=(const TensorGuard&) = delete;
+    TensorGuard(TensorGuard&& o) noexcept : t(o.t) { o.t = nullptr; }
+    TensorGuard& operator=(TensorGuard&& o) noexcept {
+        if (this != &o) { free_tensor(t); t = o.t; o.t = nullptr; }
+        return *this;
+    }
+    ~TensorGuard() { free_tensor(t); }
+    tt_tensor* release() { tt_tensor* x = t; t = nullptr; return x; }
+    tt_tensor* get() const { return t; }
+    void reset(tt_tensor* x) { free_tensor(t); t = x; }
+};
+
+}  // namespace ttgb
+
+#define TT_API_BEGIN try {
+#define TT_API_END                                                   \
+    }                                                                \
+    catch (const ttgb::Error& e__) {                                 \
+        ttgb::set_last_error(e__.msg);                               \
+        return e__.status;                                           \
+    }                                                                \
+    catch (const std::bad_alloc&) {                                  \
+        ttgb::set_last_error("host allocation failed");              \
+        return TT_ERR_OOM;                                           \
+    }                                                                \
+    catch (...) {                                                    \
+        ttgb::set_last_error("unknown error");                       \
+        return TT_ERR_CUDA;                                          \
+    }                                                                \
+    return TT_OK;

@@ -1,0 +1,537 @@
+// C ABI: contexts, tensors, TT sum / scale / dot / norm (Section 2).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "api_common.h"
+
+namespace ttgb {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& s) { g_last_error = s; }
+
+[[noreturn]] void throw_status(tt_status s, const std::string& msg) { throw Error{s, msg}; }
+
+[[noreturn]] void throw_cuda(cudaError_t e, const char* what, const char* file, int line) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e) + " at " + file + ":" + std::to_string(line);
+    if (e == cudaErrorMemoryAllocation) throw Error{TT_ERR_OOM, m};
+    throw Error{TT_ERR_CUDA, m};
+}
+
+void* Ctx::alloc(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (budget && stats.bytes_in_use + bytes > budget)
+        throw_status(TT_ERR_OOM, "HBM budget exceeded (" + std::to_string(stats.bytes_in_use + bytes) + " > " +
+                                     std::to_string(budget) + " bytes)");
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw_status(TT_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    }
+    stats.bytes_in_use += bytes;
+    stats.peak_bytes = std::max<uint64_t>(stats.peak_bytes, stats.bytes_in_use);
+    return p;
+}
+
+void Ctx::release(void* p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    cudaFreeAsync(p, stream);
+    stats.bytes_in_use -= std::min<uint64_t>(stats.bytes_in_use, bytes);
+}
+
+void Ctx::sync() {
+    stats.host_syncs++;
+    TT_CUDA(cudaStreamSynchronize(stream));
+}
+
+int Ctx::family(const char* name) {
+    for (size_t i = 0; i < fam_names.size(); ++i)
+        if (fam_names[i] == name) return (int)i;
+    fam_names.push_back(name);
+    return (int)fam_names.size() - 1;
+}
+
+cudaEvent_t Ctx::event() {
+    if (!ev_pool.empty()) {
+        cudaEvent_t e = ev_pool.back();
+        ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    TT_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+Ctx::~Ctx() {
+    for (auto& r : recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ev_pool) cudaEventDestroy(e);
+}
+
+ProfScope::ProfScope(Ctx& ctx, const char* name, double fl, double by) : c(ctx), flops(fl), bytes(by) {
+    if (!c.prof) return;
+    fam = c.family(name);
+    a = c.event();
+    TT_CUDA(cudaEventRecord(a, c.stream));
+}
+
+ProfScope::~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = c.event();
+    cudaEventRecord(b, c.stream);
+    c.recs.push_back(ProfRec{fam, flops, bytes, a, b});
+}
+
+size_t dtype_size(tt_dtype t) { return t == TT_DTYPE_F64 ? 8 : 4; }
+
+tt_dtype storage_of(tt_precision p) { return p == TT_FP64 ? TT_DTYPE_F64 : TT_DTYPE_F32; }
+
+void validate_shape(int d, const int* n, const int* r) {
+    if (d < 1 || !n || !r) throw_status(TT_ERR_ARG, "d < 1 or NULL shape");
+    if (r[0] != 1 || r[d] != 1) throw_status(TT_ERR_ARG, "r_0 and r_d must be 1");
+    for (int k = 0; k < d; ++k) {
+        if (n[k] < 1) throw_status(TT_ERR_ARG, "mode size < 1");
+        if (r[k + 1] < 1) throw_status(TT_ERR_ARG, "rank < 1");
+    }
+}
+
+tt_tensor* new_tensor(tt_ctx* ctx, int d, const int* n, const int* r) {
+    validate_shape(d, n, r);
+    tt_tensor* t = new tt_tensor();
+    t->ctx = ctx;
+    t->d = d;
+    t->n.assign(n, n + d);
+    t->r.assign(r, r + d + 1);
+    t->dtype = storage_of(ctx->prec);
+    t->cores.assign(d, nullptr);
+    size_t es = dtype_size(t->dtype), off = 0;
+    std::vector<size_t> offs(d);
+    for (int k = 0; k < d; ++k) {
+        offs[k] = off;
+        off += ((size_t)r[k] * n[k] * r[k + 1] * es + 255) & ~size_t(255);
+    }
+    try {
+        t->block = ctx->alloc(off);
+    } catch (...) {
+        delete t;
+        throw;
+    }
+    t->bytes = off;
+    t->owned = true;
+    for (int k = 0; k < d; ++k) t->cores[k] = (char*)t->block + offs[k];
+    return t;
+}
+
+void free_tensor(tt_tensor* t) {
+    if (!t) return;
+    if (t->owned && t->block) t->ctx->release(t->block, t->bytes);
+    delete t;
+}
+
+void check_same_modes(const tt_tensor* a, const tt_tensor* b) {
+    if (a->d != b->d) throw_status(TT_ERR_SHAPE, "orders differ");
+    for (int k = 0; k < a->d; ++k)
+        if (a->n[k] != b->n[k]) throw_status(TT_ERR_SHAPE, "mode sizes differ");
+}
+
+void check_tensor(tt_ctx* ctx, const tt_tensor* x) {
+    if (!x) throw_status(TT_ERR_ARG, "NULL tensor");
+    if (x->ctx != ctx) throw_status(TT_ERR_ARG, "tensor belongs to another context");
+}
+
+tt_tensor* copy_tensor(tt_ctx* ctx, const tt_tensor* x) {
+    tt_tensor* y = new_tensor(ctx, x->d, x->n.data(), x->r.data());
+    size_t es = dtype_size(x->dtype);
+    for (int k = 0; k < x->d; ++k)
+        TT_CUDA(cudaMemcpyAsync(y->cores[k], x->cores[k], es * x->core_elems(k), cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+    y->norm_hint = x->norm_hint;
+    return y;
+}
+
+// ---------------------------------------------------------------- TT sum
+template <class T>
+tt_tensor* add_impl(tt_ctx* ctx, int m, const double* alpha, const tt_tensor* const* x) {
+    const tt_tensor* x0 = x[0];
+    const int d = x0->d;
+    std::vector<int> r(d + 1, 0);
+    r[0] = 1;
+    r[d] = 1;
+    for (int k = 1; k < d; ++k)
+        for (int j = 0; j < m; ++j) r[k] += x[j]->r[k];
+    if (d == 1) {
+        // linear combination of the single cores (1 x n x 1)
+        int one[2] = {1, 1};
+        tt_tensor* y = new_tensor(ctx, 1, x0->n.data(), one);
+        TT_CUDA(cudaMemsetAsync(y->cores[0], 0, sizeof(T) * x0->n[0], ctx->stream));
+        for (int j = 0; j < m; ++j) axpy<T>(*ctx, x0->n[0], alpha[j], (const T*)x[j]->cores[0], (T*)y->cores[0]);
+        return y;
+    }
+    tt_tensor* y = new_tensor(ctx, d, x0->n.data(), r.data());
+    for (int k = 0; k < d; ++k) {
+        const int n = x0->n[k];
+        const long RB = r[k + 1];
+        if (k > 0 && k < d - 1)
+            TT_CUDA(cudaMemsetAsync(y->cores[k], 0, sizeof(T) * y->core_elems(k), ctx->stream));
+        long oa = 0, ob = 0;
+        for (int j0 = 0; j0 < m; j0 += 64) {
+            BlockList list;
+            list.count = std::min(64, m - j0);
+            int ma = 0, mb = 0;
+            for (int t = 0; t < list.count; ++t) {
+                const int j = j0 + t;
+                const int a = x[j]->r[k], b = x[j]->r[k + 1];
+                const long oaa = (k == 0) ? 0 : oa;
+                const long obb = (k == d - 1) ? 0 : ob;
+                list.blk[t] = BlockDesc{x[j]->cores[k], oaa * n * RB + obb, a, b, k == 0 ? alpha[j] : 1.0};
+                oa += a;
+                ob += b;
+                ma = std::max(ma, a);
+                mb = std::max(mb, b);
+            }
+            scatter_blocks<T>(*ctx, list, n, RB, (long)n * RB, (T*)y->cores[k], ma, mb);
+        }
+    }
+    return y;
+}
+
+tt_tensor* tt_add_internal(tt_ctx* ctx, int m, const double* alpha, const tt_tensor* const* x) {
+    if (m < 1 || !alpha || !x) throw_status(TT_ERR_ARG, "tt_add: m < 1 or NULL");
+    for (int j = 0; j < m; ++j) {
+        check_tensor(ctx, x[j]);
+        check_same_modes(x[0], x[j]);
+        if (!isfinite(alpha[j])) throw_status(TT_ERR_ARG, "tt_add: non-finite coefficient");
+    }
+    if (ctx->prec == TT_FP64) return add_impl<double>(ctx, m, alpha, x);
+    return add_impl<float>(ctx, m, alpha, x);
+}
+
+tt_tensor* scale_internal(tt_ctx* ctx, const tt_tensor* x, double alpha) {
+    tt_tensor* y = copy_tensor(ctx, x);
+    const int k = x->d - 1;
+    if (ctx->prec == TT_FP64) scale_inplace<double>(*ctx, y->core_elems(k), (double*)y->cores[k], alpha);
+    else scale_inplace<float>(*ctx, y->core_elems(k), (float*)y->cores[k], alpha);
+    y->norm_hint = x->norm_hint >= 0 ? x->norm_hint * fabs(alpha) : -1.0;
+    return y;
+}
+
+// ---------------------------------------------------------------- TT dot
+// W_0 = 1; V = W_{k-1} Y_k^R (r_x x n r_y'); W_k = (X_k^L)^T V^L.
+template <class T>
+void dot_chain(tt_ctx* ctx, const tt_tensor* x, const tt_tensor* y, T* wsA, T* wsV, T* out_dev) {
+    const int d = x->d;
+    T* W = wsA;  // r_x x r_y
+    // W_0 = 1
+    fill_identity<T>(*ctx, 1, W, 1);
+    for (int k = 0; k < d; ++k) {
+        const int n = x->n[k];
+        const int rx = x->r[k], rx2 = x->r[k + 1], ry = y->r[k], ry2 = y->r[k + 1];
+        // V (rx x n*ry2) = W (rx x ry) * Y^R (ry x n*ry2)
+        gemm<T>(*ctx, false, false, rx, n * ry2, ry, T(1), W, ry, (const T*)y->cores[k], (long)n * ry2, T(0), wsV,
+                (long)n * ry2);
+        // W' (rx2 x ry2) = X^L^T (rx2 x rx*n) * V^L (rx*n x ry2)
+        T* Wn = (k == d - 1) ? out_dev : W;
+        gemm<T>(*ctx, true, false, rx2, ry2, rx * n, T(1), (const T*)x->cores[k], rx2, wsV, ry2, T(0), Wn, ry2);
+    }
+}
+
+size_t dot_ws_elems(const tt_tensor* x, const tt_tensor* y, size_t* wA) {
+    size_t a = 1, v = 1;
+    for (int k = 0; k < x->d; ++k) {
+        a = std::max(a, (size_t)x->r[k + 1] * y->r[k + 1]);
+        a = std::max(a, (size_t)x->r[k] * y->r[k]);
+        v = std::max(v, (size_t)x->r[k] * x->n[k] * y->r[k + 1]);
+    }
+    *wA = a;
+    return v;
+}
+
+template <class T>
+void dot_many_impl(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out) {
+    size_t wa = 1, wv = 1;
+    for (int j = 0; j < count; ++j) {
+        size_t a;
+        wv = std::max(wv, dot_ws_elems(x, y[j], &a));
+        wa = std::max(wa, a);
+    }
+    const size_t bytes = sizeof(T) * (wa + wv + count + 2) + 512;
+    char* ws = (char*)ctx->alloc(bytes);
+    T* A = (T*)ws;
+    T* V = A + wa;
+    T* res = V + wv;
+    for (int j = 0; j < count; ++j) dot_chain<T>(ctx, x, y[j], A, V, res + j);
+    std::vector<T> h(count);
+    TT_CUDA(cudaMemcpyAsync(h.data(), res, sizeof(T) * count, cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->sync();
+    ctx->release(ws, bytes);
+    for (int j = 0; j < count; ++j) out[j] = (double)h[j];
+}
+
+void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out) {
+    check_tensor(ctx, x);
+    if (count < 0 || (count > 0 && (!y || !out))) throw_status(TT_ERR_ARG, "tt_dot_many: bad arguments");
+    for (int j = 0; j < count; ++j) {
+        check_tensor(ctx, y[j]);
+        check_same_modes(x, y[j]);
+    }
+    if (count == 0) return;
+    if (ctx->prec == TT_FP64) dot_many_impl<double>(ctx, x, count, y, out);
+    else dot_many_impl<float>(ctx, x, count, y, out);
+}
+
+}  // namespace ttgb
+
+using namespace ttgb;
+
+// ================================================================ C ABI
+extern "C" {
+
+tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* stream, size_t hbm_budget) {
+    TT_API_BEGIN
+    if (!out) throw_status(TT_ERR_ARG, "NULL ctx out");
+    *out = nullptr;
+    if (prec != TT_FP64 && prec != TT_MIXED_TF32 && prec != TT_FP32) throw_status(TT_ERR_ARG, "bad precision");
+    int ndev = 0;
+    TT_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) throw_status(TT_ERR_ARG, "bad device");
+    TT_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    TT_CUDA(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10) throw_status(TT_ERR_CUDA, "device is not a Blackwell (sm_10x) GPU");
+    tt_ctx* c = new tt_ctx();
+    c->device = device;
+    c->prec = prec;
+    c->stream = (cudaStream_t)stream;
+    c->budget = hbm_budget;
+    c->sm_count = prop.multiProcessorCount;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = c;
+    TT_API_END
+}
+
+void tt_ctx_destroy(tt_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+}
+
+tt_status tt_ctx_get_stats(const tt_ctx* ctx, tt_stats* out) {
+    if (!ctx || !out) return TT_ERR_ARG;
+    *out = ctx->stats;
+    return TT_OK;
+}
+
+void tt_ctx_reset_stats(tt_ctx* ctx) {
+    if (!ctx) return;
+    uint64_t in_use = ctx->stats.bytes_in_use;
+    ctx->stats = tt_stats{};
+    ctx->stats.bytes_in_use = in_use;
+    ctx->stats.peak_bytes = in_use;
+}
+
+tt_precision tt_ctx_precision(const tt_ctx* ctx) { return ctx ? ctx->prec : TT_FP64; }
+
+tt_status tt_ctx_set_profiling(tt_ctx* ctx, int on) {
+    if (!ctx) return TT_ERR_ARG;
+    ctx->prof = on != 0;
+    return TT_OK;
+}
+
+void tt_ctx_reset_profile(tt_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& r : ctx->recs) {
+        ctx->ev_pool.push_back(r.a);
+        ctx->ev_pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+}
+
+tt_status tt_ctx_get_profile(tt_ctx* ctx, tt_kernel_profile* out, int max_entries, int* n_entries) {
+    TT_API_BEGIN
+    if (!ctx || !n_entries || (max_entries > 0 && !out)) throw_status(TT_ERR_ARG, "bad arguments");
+    ctx->sync();
+    std::vector<tt_kernel_profile> agg(ctx->fam_names.size());
+    for (size_t i = 0; i < agg.size(); ++i) {
+        memset(&agg[i], 0, sizeof(agg[i]));
+        strncpy(agg[i].name, ctx->fam_names[i].c_str(), sizeof(agg[i].name) - 1);
+    }
+    for (auto& r : ctx->recs) {
+        float ms = 0.f;
+        TT_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        tt_kernel_profile& p = agg[r.fam];
+        p.launches++;
+        p.total_ms += ms;
+        p.flops += r.flops;
+        p.bytes += r.bytes;
+    }
+    int k = 0;
+    for (auto& p : agg) {
+        if (p.launches == 0) continue;
+        if (k < max_entries) out[k] = p;
+        ++k;
+    }
+    *n_entries = k;
+    TT_API_END
+}
+
+tt_status tt_set_sign_rule(tt_ctx* ctx, tt_sign_rule rule) {
+    if (!ctx || (rule != TT_SIGN_STABLE && rule != TT_SIGN_LITERAL)) return TT_ERR_ARG;
+    ctx->sign_rule = rule;
+    return TT_OK;
+}
+
+tt_status tt_tensor_create(tt_ctx* ctx, int d, const int* n, const int* r, const double* const* host_cores,
+                           tt_tensor** out) {
+    TT_API_BEGIN
+    if (!ctx || !out) throw_status(TT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    tt_tensor* t = new_tensor(ctx, d, n, r);
+    try {
+        for (int k = 0; k < d; ++k) {
+            const size_t ne = t->core_elems(k);
+            if (!host_cores || !host_cores[k]) {
+                TT_CUDA(cudaMemsetAsync(t->cores[k], 0, ne * dtype_size(t->dtype), ctx->stream));
+            } else if (t->dtype == TT_DTYPE_F64) {
+                TT_CUDA(cudaMemcpyAsync(t->cores[k], host_cores[k], ne * 8, cudaMemcpyHostToDevice, ctx->stream));
+            } else {
+                std::vector<float> tmp(ne);
+                for (size_t e = 0; e < ne; ++e) tmp[e] = (float)host_cores[k][e];
+                // pageable source: the call returns once tmp is staged
+                TT_CUDA(cudaMemcpyAsync(t->cores[k], tmp.data(), ne * 4, cudaMemcpyHostToDevice, ctx->stream));
+            }
+        }
+    } catch (...) {
+        free_tensor(t);
+        throw;
+    }
+    *out = t;
+    TT_API_END
+}
+
+tt_status tt_tensor_wrap_device(tt_ctx* ctx, int d, const int* n, const int* r, void* const* dev_cores, int dtype,
+                                tt_tensor** out) {
+    TT_API_BEGIN
+    if (!ctx || !out || !dev_cores) throw_status(TT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    validate_shape(d, n, r);
+    if (dtype != (int)storage_of(ctx->prec)) throw_status(TT_ERR_ARG, "dtype differs from the context storage");
+    tt_tensor* t = new tt_tensor();
+    t->ctx = ctx;
+    t->d = d;
+    t->n.assign(n, n + d);
+    t->r.assign(r, r + d + 1);
+    t->dtype = (tt_dtype)dtype;
+    t->cores.assign(dev_cores, dev_cores + d);
+    for (int k = 0; k < d; ++k)
+        if (!t->cores[k]) {
+            delete t;
+            throw_status(TT_ERR_ARG, "NULL core");
+        }
+    t->owned = false;
+    *out = t;
+    TT_API_END
+}
+
+tt_status tt_tensor_shape(const tt_tensor* x, int* d, int* n, int* r) {
+    if (!x) return TT_ERR_ARG;
+    if (d) *d = x->d;
+    if (n) for (int k = 0; k < x->d; ++k) n[k] = x->n[k];
+    if (r) for (int k = 0; k <= x->d; ++k) r[k] = x->r[k];
+    return TT_OK;
+}
+
+tt_status tt_tensor_core_ptr(const tt_tensor* x, int k, void** p) {
+    if (!x || !p || k < 0 || k >= x->d) return TT_ERR_ARG;
+    *p = x->cores[k];
+    return TT_OK;
+}
+
+tt_status tt_tensor_download(tt_ctx* ctx, const tt_tensor* x, double* const* host_cores) {
+    TT_API_BEGIN
+    if (!ctx || !host_cores) throw_status(TT_ERR_ARG, "NULL argument");
+    check_tensor(ctx, x);
+    for (int k = 0; k < x->d; ++k) {
+        if (!host_cores[k]) throw_status(TT_ERR_ARG, "NULL host core");
+        const size_t ne = x->core_elems(k);
+        if (x->dtype == TT_DTYPE_F64) {
+            TT_CUDA(cudaMemcpyAsync(host_cores[k], x->cores[k], ne * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        } else {
+            std::vector<float> tmp(ne);
+            TT_CUDA(cudaMemcpyAsync(tmp.data(), x->cores[k], ne * 4, cudaMemcpyDeviceToHost, ctx->stream));
+            ctx->sync();
+            for (size_t e = 0; e < ne; ++e) host_cores[k][e] = tmp[e];
+        }
+    }
+    ctx->sync();
+    TT_API_END
+}
+
+void tt_tensor_free(tt_tensor* x) { free_tensor(x); }
+
+tt_status tt_add(tt_ctx* ctx, int m, const double* alpha, const tt_tensor* const* x, tt_tensor** out) {
+    TT_API_BEGIN
+    if (!ctx || !out) throw_status(TT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    *out = tt_add_internal(ctx, m, alpha, x);
+    TT_API_END
+}
+
+tt_status tt_scale(tt_ctx* ctx, const tt_tensor* x, double alpha, tt_tensor** out) {
+    TT_API_BEGIN
+    if (!ctx || !out) throw_status(TT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    check_tensor(ctx, x);
+    if (!isfinite(alpha)) throw_status(TT_ERR_ARG, "non-finite alpha");
+    *out = scale_internal(ctx, x, alpha);
+    TT_API_END
+}
+
+tt_status tt_dot(tt_ctx* ctx, const tt_tensor* x, const tt_tensor* y, double* out) {
+    TT_API_BEGIN
+    if (!ctx || !out || !y) throw_status(TT_ERR_ARG, "NULL argument");
+    const tt_tensor* ys[1] = {y};
+    dot_many_internal(ctx, x, 1, ys, out);
+    TT_API_END
+}
+
+tt_status tt_dot_many(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out) {
+    TT_API_BEGIN
+    if (!ctx) throw_status(TT_ERR_ARG, "NULL argument");
+    dot_many_internal(ctx, x, count, y, out);
+    TT_API_END
+}
+
+const char* tt_status_str(tt_status s) {
+    switch (s) {
+        case TT_OK: return "TT_OK";
+        case TT_ERR_ARG: return "TT_ERR_ARG";
+        case TT_ERR_SHAPE: return "TT_ERR_SHAPE";
+        case TT_ERR_OOM: return "TT_ERR_OOM";
+        case TT_ERR_NOT_SPD: return "TT_ERR_NOT_SPD";
+        case TT_ERR_BREAKDOWN: return "TT_ERR_BREAKDOWN";
+        case TT_ERR_NONFINITE: return "TT_ERR_NONFINITE";
+        case TT_ERR_TIMEOUT: return "TT_ERR_TIMEOUT";
+        case TT_ERR_CUDA: return "TT_ERR_CUDA";
+    }
+    return "TT_ERR_UNKNOWN";
+}
+
+const char* tt_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

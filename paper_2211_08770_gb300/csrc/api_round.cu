@@ -1,0 +1,398 @@
+// TT-rounding (Section 2: TT-round(x, delta), ||x - x~|| <= delta ||x||) and
+// the TT norm, on the GPU.
+//
+// Right-to-left sweep: each right unfolding X (r_{k-1} x n_k r_k) is
+// factored X = L Q with Q row-orthonormal by Cholesky QR passes: Gram
+// G = X X^T, G = L L^T, Q = L^{-1} X, twice (CholQR2) when the first
+// Cholesky is healthy, otherwise three passes of which the first is shifted
+// (G + s I), with numerically dependent rows dropped.  L is absorbed into
+// core k-1.  ||x|| = ||core_1||_F.
+// Left-to-right sweep: each left unfolding X (r_{k-1} n_k x r_k) is factored
+// X = Q R the same way (on columns); the bond keeps its rank when a
+// certified lower bound of sigma_min(R) exceeds 2 eps, else R is decomposed
+// by one-sided Jacobi SVD and truncated to the minimal rank whose discarded
+// singular values have root-sum-square <= eps = delta ||x|| / sqrt(d - 1).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "api_common.h"
+
+namespace ttgb {
+
+namespace {
+
+template <class T>
+struct Rounder {
+    tt_ctx* c;
+    int d;
+    std::vector<int> n, r;
+    bool tc = false;         // tensor-core TF32 Gram on the fast path
+    double ug_fast, ug_fb;   // unit round-off of the fast / fallback Gram
+    int rmax = 1;
+    size_t cap = 1;          // elements per core buffer
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    std::vector<T*> core;
+    T* spare = nullptr;
+    T *G, *Lf[3], *Ti[3], *Lp, *Tmp, *Ub, *SVt;
+    double* jwork;
+    double* sig;
+    double* dsc;             // device scalars
+    CholStatus* st;          // per-Cholesky statuses of this rounding
+    int nst = 0, st_cap = 0;
+    double err2 = 0.0;       // accumulated discarded tail (squared, absolute)
+
+    Rounder(tt_ctx* ctx, const tt_tensor* x) : c(ctx), d(x->d), n(x->n), r(x->r) {
+        const bool is64 = sizeof(T) == 8;
+        tc = (ctx->prec == TT_MIXED_TF32) && ctx->use_tc;
+        ug_fb = is64 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
+        ug_fast = tc ? 9.765625e-04 : ug_fb;  // TF32 keeps 10 explicit mantissa bits
+        for (int k = 0; k <= d; ++k) rmax = std::max(rmax, r[k]);
+        for (int k = 0; k < d; ++k) cap = std::max(cap, x->core_elems(k));
+        const size_t rr = (size_t)rmax * rmax;
+        st_cap = 16 * d + 16;
+        auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+        const size_t core_b = al(cap * sizeof(T));
+        const size_t small_b = al(rr * sizeof(T));
+        ws_bytes = (d + 1) * core_b + 11 * small_b + al(2 * rr * sizeof(double)) + al(rmax * sizeof(double)) +
+                   al(16 * sizeof(double)) + al(st_cap * sizeof(CholStatus));
+        ws = (char*)ctx->alloc(ws_bytes);
+        char* p = ws;
+        core.resize(d);
+        for (int k = 0; k < d; ++k) { core[k] = (T*)p; p += core_b; }
+        spare = (T*)p; p += core_b;
+        G = (T*)p; p += small_b;
+        for (int i = 0; i < 3; ++i) { Lf[i] = (T*)p; p += small_b; }
+        for (int i = 0; i < 3; ++i) { Ti[i] = (T*)p; p += small_b; }
+        Lp = (T*)p; p += small_b;
+        Tmp = (T*)p; p += small_b;
+        Ub = (T*)p; p += small_b;
+        SVt = (T*)p; p += small_b;
+        jwork = (double*)p; p += al(2 * rr * sizeof(double));
+        sig = (double*)p; p += al(rmax * sizeof(double));
+        dsc = (double*)p; p += al(16 * sizeof(double));
+        st = (CholStatus*)p;
+        for (int k = 0; k < d; ++k)
+            TT_CUDA(cudaMemcpyAsync(core[k], x->cores[k], sizeof(T) * x->core_elems(k), cudaMemcpyDeviceToDevice,
+                                    c->stream));
+    }
+    ~Rounder() { if (ws) c->release(ws, ws_bytes); }
+
+    CholStatus* next_st() {
+        if (nst >= st_cap) throw_status(TT_ERR_ARG, "internal: status slots exhausted");
+        return st + nst++;
+    }
+
+    CholStatus read_st(CholStatus* s) {
+        CholStatus h;
+        TT_CUDA(cudaMemcpyAsync(&h, s, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        c->sync();
+        if (h.nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in a Gram matrix");
+        return h;
+    }
+
+    void gram_into(bool rows, bool fast, int a, long K, const T* X) {
+        if constexpr (sizeof(T) == 4) {
+            if (fast && tc && rows) {
+                if (gram_rows_tc_tf32(*c, a, K, (const float*)X, K, (float*)G)) return;
+            }
+        }
+        gram<T, T>(*c, rows, a, K, X, rows ? K : a, G);
+    }
+
+    // X <- Ti X (rows) or X Ti^T (cols)
+    void apply(bool rows, int a, long K, T*& X, const T* Tinv) {
+        if (rows) gemm<T>(*c, false, false, a, (int)K, a, T(1), Tinv, a, X, K, T(0), spare, K);
+        else gemm<T>(*c, false, true, (int)K, a, a, T(1), X, a, Tinv, a, T(0), spare, a);
+        std::swap(X, spare);
+    }
+
+    struct Orth {
+        int npass;
+        int ndrop;
+        bool shifted;
+    };
+
+    // X (a x K rows, or K x a cols) is overwritten by its orthonormal factor;
+    // Lp receives the lower-triangular L with X_old = L Q (rows) or
+    // X_old = Q L^T (cols).  Lf[i], Ti[i] keep the factors of each pass.
+    Orth orth(bool rows, int a, long K, T*& X) {
+        const double sq = sqrt((double)a);
+        const double drop_fb = 8.0 * ug_fb * sq;
+        const double ratio_fast = tc ? 10.0 * ug_fast : 100.0 * ug_fast;
+        Orth o{0, 0, false};
+        {
+            gram_into(rows, true, a, K, X);
+            CholStatus* s0 = next_st();
+            cholesky<T, T>(*c, a, G, Lf[0], 0.0, ug_fast, s0);
+            CholStatus h = read_st(s0);
+            if (h.ndrop == 0 && h.min_ratio >= ratio_fast) {
+                trinv<T, T>(*c, a, Lf[0], Ti[0]);
+                apply(rows, a, K, X, Ti[0]);
+                gram_into(rows, true, a, K, X);
+                cholesky<T, T>(*c, a, G, Lf[1], 0.0, 8.0 * ug_fast * sq, next_st());
+                trinv<T, T>(*c, a, Lf[1], Ti[1]);
+                apply(rows, a, K, X, Ti[1]);
+                gemm<T>(*c, false, false, a, a, a, T(1), Lf[0], a, Lf[1], a, T(0), Lp, a);
+                o.npass = 2;
+                return o;
+            }
+        }
+        // shifted Cholesky QR, then two passes with dependent rows dropped
+        c->stats.fallback_orth++;
+        o.shifted = true;
+        gram_into(rows, false, a, K, X);
+        cholesky<T, T>(*c, a, G, Lf[0], 8.0 * ug_fb * sq, 0.0, next_st());
+        trinv<T, T>(*c, a, Lf[0], Ti[0]);
+        apply(rows, a, K, X, Ti[0]);
+        for (int p = 1; p <= 2; ++p) {
+            gram_into(rows, false, a, K, X);
+            cholesky<T, T>(*c, a, G, Lf[p], 0.0, drop_fb, next_st());
+            trinv<T, T>(*c, a, Lf[p], Ti[p]);
+            apply(rows, a, K, X, Ti[p]);
+        }
+        gemm<T>(*c, false, false, a, a, a, T(1), Lf[0], a, Lf[1], a, T(0), Tmp, a);
+        gemm<T>(*c, false, false, a, a, a, T(1), Tmp, a, Lf[2], a, T(0), Lp, a);
+        o.npass = 3;
+        return o;
+    }
+
+    // rigorous lower bound of sigma_min(L_0 ... L_{np-1}) from the factors and
+    // their inverses: prod_i max(1/||T_i||_F, 1 - ||L_i - I||_F); 0 on drops
+    double sigma_lb(int a, int np) {
+        TT_CUDA(cudaMemsetAsync(dsc, 0, 2 * np * sizeof(double), c->stream));
+        for (int i = 0; i < np; ++i) inv_and_identity_defect<T>(*c, a, Lf[i], Ti[i], dsc + 2 * i);
+        std::vector<double> h(2 * np);
+        std::vector<CholStatus> hs(nst);
+        TT_CUDA(cudaMemcpyAsync(h.data(), dsc, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        TT_CUDA(cudaMemcpyAsync(hs.data(), st, nst * sizeof(CholStatus), cudaMemcpyDeviceToHost, c->stream));
+        c->sync();
+        for (int i = nst - np; i < nst; ++i) {
+            if (hs[i].nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in a Gram matrix");
+            if (hs[i].ndrop) return 0.0;
+        }
+        double lb = 1.0;
+        for (int i = 0; i < np; ++i) {
+            double b1 = h[2 * i] > 0 ? 1.0 / sqrt(h[2 * i]) : 0.0;
+            double b2 = 1.0 - sqrt(h[2 * i + 1]);
+            lb *= std::max(b1, b2);
+        }
+        return lb;
+    }
+
+    // truncation rank from sorted singular values (FP64, host)
+    int trunc_rank(const std::vector<double>& s, double eps) {
+        const int p = (int)s.size();
+        std::vector<double> tail(p + 1, 0.0);
+        for (int i = p - 1; i >= 0; --i) tail[i] = tail[i + 1] + s[i] * s[i];
+        const double e2 = eps * eps;
+        for (int rr = 1; rr <= p; ++rr)
+            if (tail[rr] <= e2) {
+                err2 += tail[rr];
+                return rr;
+            }
+        return std::max(1, p);
+    }
+
+    void rl_sweep() {
+        for (int k = d - 1; k >= 1; --k) {
+            const int a = r[k];
+            const long K = (long)n[k] * r[k + 1];
+            const int M = r[k - 1] * n[k - 1];
+            if (K <= a) {
+                // rank cap: X = I_K X, absorb X itself
+                gemm<T>(*c, false, false, M, (int)K, a, T(1), core[k - 1], a, core[k], K, T(0), spare, K);
+                std::swap(core[k - 1], spare);
+                fill_identity<T>(*c, (int)K, core[k], K);
+                r[k] = (int)K;
+            } else {
+                orth(true, a, K, core[k]);
+                gemm<T>(*c, false, false, M, a, a, T(1), core[k - 1], a, Lp, a, T(0), spare, a);
+                std::swap(core[k - 1], spare);
+            }
+        }
+    }
+
+    double core_norm(int k) {
+        sumsq<T>(*c, (long)r[k] * n[k] * r[k + 1], core[k], dsc + 15);
+        double h;
+        TT_CUDA(cudaMemcpyAsync(&h, dsc + 15, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        c->sync();
+        if (!isfinite(h)) throw_status(TT_ERR_NONFINITE, "NaN or Inf in the tensor");
+        return sqrt(h);
+    }
+
+    void lr_sweep(double eps) {
+        for (int k = 0; k + 1 < d; ++k) {
+            const int m = r[k] * n[k];
+            const int b = r[k + 1];
+            const long NR = (long)n[k + 1] * r[k + 2];
+            if (m >= b) {
+                Orth o = orth(false, b, m, core[k]);
+                const double lb = sigma_lb(b, o.npass);
+                if (lb > 2.0 * eps && lb > 0.0) {
+                    c->stats.certified_bonds++;
+                    // core_{k+1} <- R core_{k+1}, R = Lp^T
+                    gemm<T>(*c, true, false, b, (int)NR, b, T(1), Lp, b, core[k + 1], NR, T(0), spare, NR);
+                    std::swap(core[k + 1], spare);
+                    continue;
+                }
+                // R = Lp^T (b x b), SVD, truncate
+                transpose<T>(*c, b, b, Lp, Tmp);
+                c->stats.svd_calls++;
+                jacobi_svd<T>(*c, b, b, Tmp, Ub, SVt, sig, (T*)jwork);
+                std::vector<double> hs(b);
+                TT_CUDA(cudaMemcpyAsync(hs.data(), sig, b * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+                c->sync();
+                const int rp = trunc_rank(hs, eps);
+                gemm<T>(*c, false, false, m, rp, b, T(1), core[k], b, Ub, b, T(0), spare, rp);
+                std::swap(core[k], spare);
+                gemm<T>(*c, false, false, rp, (int)NR, b, T(1), SVt, b, core[k + 1], NR, T(0), spare, NR);
+                std::swap(core[k + 1], spare);
+                r[k + 1] = rp;
+            } else {
+                // m < b: Q = I_m, R = X (m x b); certificate from the Gram of
+                // the rows of X (SIMT arithmetic, its error is subtracted)
+                const T* X = core[k];
+                gram<T, T>(*c, true, m, b, X, b, G);
+                CholStatus* s = next_st();
+                cholesky<T, T>(*c, m, G, Lf[0], 0.0, 8.0 * ug_fb * sqrt((double)m), s);
+                trinv<T, T>(*c, m, Lf[0], Ti[0]);
+                double lb = sigma_lb(m, 1);
+                CholStatus hs0 = read_st(s);
+                const double noise = 16.0 * ug_fb * sqrt((double)m) * hs0.trace;
+                const double lb2 = lb * lb - noise;
+                if (lb > 0.0 && lb2 > 4.0 * eps * eps) {
+                    c->stats.certified_bonds++;
+                    gemm<T>(*c, false, false, m, (int)NR, b, T(1), X, b, core[k + 1], NR, T(0), spare, NR);
+                    std::swap(core[k + 1], spare);
+                    fill_identity<T>(*c, m, core[k], m);
+                    r[k + 1] = m;
+                    continue;
+                }
+                c->stats.svd_calls++;
+                jacobi_svd<T>(*c, m, b, X, Ub, SVt, sig, (T*)jwork);
+                std::vector<double> hsg(m);
+                TT_CUDA(cudaMemcpyAsync(hsg.data(), sig, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+                c->sync();
+                const int rp = trunc_rank(hsg, eps);
+                // core_k <- U[:, :rp] (m x rp)
+                TT_CUDA(cudaMemcpy2DAsync(core[k], rp * sizeof(T), Ub, m * sizeof(T), rp * sizeof(T), m,
+                                          cudaMemcpyDeviceToDevice, c->stream));
+                gemm<T>(*c, false, false, rp, (int)NR, b, T(1), SVt, b, core[k + 1], NR, T(0), spare, NR);
+                std::swap(core[k + 1], spare);
+                r[k + 1] = rp;
+            }
+        }
+    }
+
+    void check_all_status() {
+        if (nst == 0) return;
+        std::vector<CholStatus> hs(nst);
+        TT_CUDA(cudaMemcpyAsync(hs.data(), st, nst * sizeof(CholStatus), cudaMemcpyDeviceToHost, c->stream));
+        c->sync();
+        for (auto& h : hs)
+            if (h.nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in a Gram matrix");
+    }
+
+    tt_tensor* emit() {
+        tt_tensor* y = new_tensor(c, d, n.data(), r.data());
+        for (int k = 0; k < d; ++k)
+            TT_CUDA(cudaMemcpyAsync(y->cores[k], core[k], sizeof(T) * y->core_elems(k), cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        return y;
+    }
+};
+
+template <class T>
+tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est) {
+    ctx->stats.roundings++;
+    if (x->d == 1) {
+        if (err_est) *err_est = 0.0;
+        return copy_tensor(ctx, x);
+    }
+    Rounder<T> R(ctx, x);
+    R.rl_sweep();
+    const double nrm = R.core_norm(0);
+    const double eps = delta * nrm / sqrt((double)(x->d - 1));
+    R.lr_sweep(eps);
+    R.check_all_status();
+    tt_tensor* y = R.emit();
+    try {
+        y->norm_hint = R.core_norm(x->d - 1);
+    } catch (...) {
+        free_tensor(y);
+        throw;
+    }
+    if (err_est) *err_est = nrm > 0 ? sqrt(R.err2) / nrm : 0.0;
+    return y;
+}
+
+template <class T>
+double norm_t(tt_ctx* ctx, const tt_tensor* x) {
+    if (x->d == 1) {
+        Rounder<T> R(ctx, x);
+        return R.core_norm(0);
+    }
+    Rounder<T> R(ctx, x);
+    R.rl_sweep();
+    R.check_all_status();
+    return R.core_norm(0);
+}
+
+}  // namespace
+
+tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est) {
+    check_tensor(ctx, x);
+    if (!(delta >= 0.0) || !isfinite(delta)) throw_status(TT_ERR_ARG, "delta must be finite and >= 0");
+    if (ctx->prec == TT_FP64) return round_t<double>(ctx, x, delta, err_est);
+    return round_t<float>(ctx, x, delta, err_est);
+}
+
+double norm_internal(tt_ctx* ctx, const tt_tensor* x) {
+    check_tensor(ctx, x);
+    if (x->norm_hint >= 0.0) return x->norm_hint;
+    if (ctx->prec == TT_FP64) return norm_t<double>(ctx, x);
+    return norm_t<float>(ctx, x);
+}
+
+}  // namespace ttgb
+
+using namespace ttgb;
+
+extern "C" {
+
+tt_status tt_round(tt_ctx* ctx, const tt_tensor* x, double delta, tt_tensor** out, double* err_est) {
+    TT_API_BEGIN
+    if (!ctx || !out) throw_status(TT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    *out = round_internal(ctx, x, delta, err_est);
+    TT_API_END
+}
+
+tt_status tt_norm(tt_ctx* ctx, const tt_tensor* x, double* out) {
+    TT_API_BEGIN
+    if (!ctx || !out) throw_status(TT_ERR_ARG, "NULL argument");
+    *out = norm_internal(ctx, x);
+    TT_API_END
+}
+
+tt_status tt_round_batched(tt_ctx* ctx, int count, const tt_tensor* const* x, const double* delta, tt_tensor** out) {
+    TT_API_BEGIN
+    if (!ctx || !out || count < 0 || (count > 0 && (!x || !delta))) throw_status(TT_ERR_ARG, "bad arguments");
+    for (int i = 0; i < count; ++i) out[i] = nullptr;
+    std::vector<tt_tensor*> res(count, nullptr);
+    try {
+        for (int i = 0; i < count; ++i) res[i] = round_internal(ctx, x[i], delta[i], nullptr);
+    } catch (...) {
+        for (auto* t : res) free_tensor(t);
+        throw;
+    }
+    for (int i = 0; i < count; ++i) out[i] = res[i];
+    TT_API_END
+}
+
+}  // extern "C"

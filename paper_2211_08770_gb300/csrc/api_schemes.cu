@@ -1,0 +1,271 @@
+// The six TT orthogonalization schemes (Section 3, Algorithms 1-8) as host
+// loops over the GPU primitives: TT dot, rank-concatenating axpy, TT-round,
+// norm and scaling.  R is assembled on the host in FP64 (column-major, column
+// i holds the coefficients of a_i).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <memory>
+#include <vector>
+
+#include "api_common.h"
+
+namespace ttgb {
+
+namespace {
+
+struct Driver {
+    tt_ctx* c;
+    double delta;
+    tt_round_policy pol;
+    int nrounds = 0;
+
+    tt_tensor* round(const tt_tensor* p) {
+        nrounds++;
+        return round_internal(c, p, delta, nullptr);
+    }
+    double dot(const tt_tensor* a, const tt_tensor* b) {
+        double v = 0.0;
+        const tt_tensor* ys[1] = {b};
+        dot_many_internal(c, a, 1, ys, &v);
+        return v;
+    }
+    // p + alpha q by concatenation
+    tt_tensor* axpy(const tt_tensor* p, double alpha, const tt_tensor* q) {
+        double al[2] = {1.0, alpha};
+        const tt_tensor* xs[2] = {p, q};
+        return tt_add_internal(c, 2, al, xs);
+    }
+    double norm(const tt_tensor* p) { return norm_internal(c, p); }
+};
+
+// running vector: either borrowed (an input) or owned
+struct Cur {
+    const tt_tensor* p = nullptr;
+    TensorGuard own;
+    void set_owned(tt_tensor* t) {
+        own.reset(t);  // frees the previous owned tensor after t was computed
+        p = t;
+    }
+};
+
+tt_tensor* normalize(Driver& D, const tt_tensor* p, double* nrm_out) {
+    const double nrm = D.norm(p);
+    if (!(nrm > 0.0)) throw_status(TT_ERR_BREAKDOWN, "zero vector in normalisation");
+    *nrm_out = nrm;
+    return scale_internal(D.c, p, 1.0 / nrm);
+}
+
+// Algorithm 1 (modified = false) and Algorithm 2 (modified = true)
+void gs(Driver& D, int m, const tt_tensor* const* A, std::vector<TensorGuard>& Q, double* R, bool modified) {
+    for (int i = 0; i < m; ++i) {
+        Cur p;
+        p.p = A[i];
+        for (int j = 0; j < i; ++j) {
+            const double rji = D.dot(modified ? p.p : A[i], Q[j].get());
+            R[j + (size_t)i * m] = rji;
+            p.set_owned(D.axpy(p.p, -rji, Q[j].get()));
+            if (D.pol == TT_ROUND_EVERY_UPDATE) p.set_owned(D.round(p.p));
+        }
+        if (D.pol == TT_ROUND_PAPER || i == 0) p.set_owned(D.round(p.p));
+        double nrm;
+        Q[i].reset(normalize(D, p.p, &nrm));
+        R[i + (size_t)i * m] = nrm;
+    }
+}
+
+// Algorithm 3 (modified = false) and Algorithm 4 (modified = true)
+void gs2(Driver& D, int m, const tt_tensor* const* A, std::vector<TensorGuard>& Q, double* R, bool modified) {
+    std::vector<double> R1((size_t)m * m, 0.0), R2((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) {
+        Cur prev;
+        prev.p = A[i];
+        for (int k = 0; k < 2; ++k) {
+            std::vector<double>& Rk = (k == 0) ? R1 : R2;
+            Cur p;
+            p.p = prev.p;
+            for (int j = 0; j < i; ++j) {
+                const double rji = D.dot(modified ? p.p : prev.p, Q[j].get());
+                Rk[j + (size_t)i * m] = rji;
+                p.set_owned(D.axpy(p.p, -rji, Q[j].get()));
+                if (D.pol == TT_ROUND_EVERY_UPDATE) p.set_owned(D.round(p.p));
+            }
+            if (D.pol == TT_ROUND_PAPER || i == 0) p.set_owned(D.round(p.p));
+            // prev <- p (move ownership)
+            if (p.own.get()) {
+                prev.own = std::move(p.own);
+                prev.p = prev.own.get();
+            } else {
+                prev.p = p.p;
+            }
+        }
+        double nrm;
+        Q[i].reset(normalize(D, prev.p, &nrm));
+        R2[i + (size_t)i * m] = nrm;
+    }
+    for (size_t e = 0; e < (size_t)m * m; ++e) R[e] = R1[e] + R2[e];
+}
+
+// Algorithm 5: Gram matrix from TT dots, Cholesky and explicit inverse on the
+// GPU (FP64), q_i = sum_{k<=i} R^{-1}(k,i) a_k, one rounding per i.
+void gram_scheme(Driver& D, int m, const tt_tensor* const* A, std::vector<TensorGuard>& Q, double* R) {
+    std::vector<double> G((size_t)m * m);
+    for (int i = 0; i < m; ++i) {
+        std::vector<double> v(i + 1);
+        dot_many_internal(D.c, A[i], i + 1, A, v.data());
+        for (int j = 0; j <= i; ++j) G[(size_t)i * m + j] = G[(size_t)j * m + i] = v[j];
+    }
+    tt_ctx* c = D.c;
+    const size_t mm = (size_t)m * m;
+    const size_t bytes = 3 * mm * sizeof(double) + sizeof(CholStatus) + 256;
+    char* ws = (char*)c->alloc(bytes);
+    struct Rel {
+        tt_ctx* c; void* p; size_t b;
+        ~Rel() { c->release(p, b); }
+    } rel{c, ws, bytes};
+    double* dG = (double*)ws;
+    double* dL = dG + mm;
+    double* dT = dL + mm;
+    CholStatus* st = (CholStatus*)(dT + mm);
+    TT_CUDA(cudaMemcpyAsync(dG, G.data(), mm * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    cholesky<double, double>(*c, m, dG, dL, 0.0, 0.0, st);
+    trinv<double, double>(*c, m, dL, dT);
+    std::vector<double> L(mm), T(mm);
+    CholStatus hs;
+    TT_CUDA(cudaMemcpyAsync(L.data(), dL, mm * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TT_CUDA(cudaMemcpyAsync(T.data(), dT, mm * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TT_CUDA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
+    c->sync();
+    if (hs.nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in the Gram matrix");
+    if (hs.ndrop) throw_status(TT_ERR_NOT_SPD, "Cholesky of the Gram matrix failed");
+    // R = L^T (column-major: R(j,i) = L(i,j)); R^{-1} = (L^{-1})^T: Rinv(k,i) = T(i,k)
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) R[j + (size_t)i * m] = L[(size_t)i * m + j];
+    for (int i = 0; i < m; ++i) {
+        Cur p;
+        p.set_owned(scale_internal(c, A[0], T[(size_t)i * m + 0]));
+        for (int j = 1; j <= i; ++j) {
+            p.set_owned(D.axpy(p.p, T[(size_t)i * m + j], A[j]));
+            if (D.pol == TT_ROUND_EVERY_UPDATE) p.set_owned(D.round(p.p));
+        }
+        if (D.pol == TT_ROUND_PAPER || i == 0) p.set_owned(D.round(p.p));
+        Q[i].reset(p.own.release());
+    }
+}
+
+// canonical e_j (Section 3.3): rank 1, a single 1 at phi(j), i_1 fastest
+tt_tensor* canonical(tt_ctx* c, const std::vector<int>& n, long j) {
+    const int d = (int)n.size();
+    std::vector<int> r(d + 1, 1);
+    tt_tensor* e = new_tensor(c, d, n.data(), r.data());
+    long t = j;
+    for (int k = 0; k < d; ++k) {
+        const int ik = (int)(t % n[k]);
+        t /= n[k];
+        const size_t es = dtype_size(e->dtype);
+        TT_CUDA(cudaMemsetAsync(e->cores[k], 0, es * n[k], c->stream));
+        if (e->dtype == TT_DTYPE_F64) {
+            static const double one = 1.0;
+            TT_CUDA(cudaMemcpyAsync((double*)e->cores[k] + ik, &one, 8, cudaMemcpyHostToDevice, c->stream));
+        } else {
+            static const float one = 1.0f;
+            TT_CUDA(cudaMemcpyAsync((float*)e->cores[k] + ik, &one, 4, cudaMemcpyHostToDevice, c->stream));
+        }
+    }
+    e->norm_hint = 1.0;
+    return e;
+}
+
+tt_tensor* apply_h(Driver& D, const tt_tensor* a, const tt_tensor* u) {
+    const double s = D.dot(a, u);
+    return D.axpy(a, -2.0 * s, u);
+}
+
+// Algorithm 6
+tt_tensor* tth_vec(Driver& D, const tt_tensor* a, const std::vector<TensorGuard>& E, int i, double* r) {
+    double s = 0.0;
+    Cur w;
+    w.p = a;
+    for (int j = 0; j < i - 1; ++j) {
+        r[j] = D.dot(a, E[j].get());
+        s += r[j] * r[j];
+        w.set_owned(D.axpy(w.p, -r[j], E[j].get()));
+    }
+    w.set_owned(D.round(w.p));
+    const double na = D.norm(a);
+    double t = na * na - s;
+    if (t < 0.0) t = 0.0;
+    const double fi = D.dot(a, E[i - 1].get());
+    const double sg = fi >= 0.0 ? 1.0 : -1.0;
+    r[i - 1] = (D.c->sign_rule == TT_SIGN_STABLE ? -sg : sg) * sqrt(t);
+    w.set_owned(D.axpy(w.p, -r[i - 1], E[i - 1].get()));
+    w.set_owned(D.round(w.p));
+    double nw;
+    return normalize(D, w.p, &nw);
+}
+
+// Algorithm 8
+void householder(Driver& D, int m, const tt_tensor* const* A, std::vector<TensorGuard>& Q, double* R) {
+    const std::vector<int>& n = A[0]->n;
+    double prodn = 1.0;
+    for (int v : n) prodn *= v;
+    if (prodn < m) throw_status(TT_ERR_ARG, "prod(n) must be >= m for the canonical basis");
+    std::vector<TensorGuard> E(m);
+    for (int j = 0; j < m; ++j) E[j].reset(canonical(D.c, n, j));
+    std::vector<Cur> a(m);
+    for (int j = 0; j < m; ++j) a[j].p = A[j];
+    std::vector<TensorGuard> U(m);
+    Cur w;
+    w.set_owned(D.round(A[0]));
+    std::vector<double> r(m);
+    for (int i = 0; i < m; ++i) {
+        U[i].reset(tth_vec(D, w.p, E, i + 1, r.data()));
+        for (int j = 0; j <= i; ++j) R[j + (size_t)i * m] = r[j];
+        for (int j = i; j < m; ++j) {
+            a[j].set_owned(apply_h(D, a[j].p, U[i].get()));
+            if (D.pol == TT_ROUND_EVERY_UPDATE && j > i) a[j].set_owned(D.round(a[j].p));
+        }
+        if (i < m - 1) w.set_owned(D.round(a[i + 1].p));
+    }
+    for (int i = 0; i < m; ++i) {
+        Cur q;
+        q.p = E[i].get();
+        for (int j = i; j >= 0; --j) q.set_owned(apply_h(D, q.p, U[j].get()));
+        Q[i].reset(D.round(q.p));
+    }
+}
+
+}  // namespace
+
+}  // namespace ttgb
+
+using namespace ttgb;
+
+extern "C" tt_status tt_orthogonalize(tt_ctx* ctx, tt_scheme scheme, double delta, tt_round_policy policy, int m,
+                                      const tt_tensor* const* A, tt_tensor** Q, double* R, int* n_rounds) {
+    TT_API_BEGIN
+    if (!ctx || !A || !Q || !R || m < 1) throw_status(TT_ERR_ARG, "bad arguments");
+    for (int i = 0; i < m; ++i) Q[i] = nullptr;
+    if (!(delta >= 0.0) || !isfinite(delta)) throw_status(TT_ERR_ARG, "delta must be finite and >= 0");
+    if (policy != TT_ROUND_PAPER && policy != TT_ROUND_EVERY_UPDATE) throw_status(TT_ERR_ARG, "bad policy");
+    for (int i = 0; i < m; ++i) {
+        check_tensor(ctx, A[i]);
+        check_same_modes(A[0], A[i]);
+    }
+    Driver D{ctx, delta, policy, 0};
+    std::vector<TensorGuard> Qg(m);
+    std::vector<double> Rh((size_t)m * m, 0.0);
+    switch (scheme) {
+        case TT_CGS: gs(D, m, A, Qg, Rh.data(), false); break;
+        case TT_MGS: gs(D, m, A, Qg, Rh.data(), true); break;
+        case TT_CGS2: gs2(D, m, A, Qg, Rh.data(), false); break;
+        case TT_MGS2: gs2(D, m, A, Qg, Rh.data(), true); break;
+        case TT_GRAM: gram_scheme(D, m, A, Qg, Rh.data()); break;
+        case TT_HOUSEHOLDER: householder(D, m, A, Qg, Rh.data()); break;
+        default: throw_status(TT_ERR_ARG, "bad scheme");
+    }
+    for (size_t e = 0; e < Rh.size(); ++e) R[e] = Rh[e];
+    for (int i = 0; i < m; ++i) Q[i] = Qg[i].release();
+    if (n_rounds) *n_rounds = D.nrounds;
+    TT_API_END
+}

@@ -1,0 +1,163 @@
+// Internal interfaces of the TT library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ttgb.h"
+
+namespace ttgb {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+    tt_status status;
+    std::string msg;
+};
+[[noreturn]] void throw_status(tt_status s, const std::string& msg);
+[[noreturn]] void throw_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define TT_CUDA(x)                                                          \
+    do {                                                                    \
+        cudaError_t e__ = (x);                                              \
+        if (e__ != cudaSuccess) ::ttgb::throw_cuda(e__, #x, __FILE__, __LINE__); \
+    } while (0)
+// after every kernel launch: catches launch-configuration errors at once
+#define TT_LAUNCHED(ctx)                                                    \
+    do {                                                                    \
+        (ctx).stats.kernel_launches++;                                      \
+        cudaError_t e__ = cudaGetLastError();                               \
+        if (e__ != cudaSuccess) ::ttgb::throw_cuda(e__, "kernel launch", __FILE__, __LINE__); \
+    } while (0)
+
+// ---------------------------------------------------------------- kernels
+// Small-matrix factorization status written by the Cholesky kernel.
+struct CholStatus {
+    int ndrop;          // pivots dropped as numerically dependent
+    int nonfinite;      // NaN/Inf met
+    double min_ratio;   // min over kept j of pivot_j / (G_jj + shift)
+    double trace;       // trace(G) (before shift)
+    double max_diag;    // max_j G_jj (before shift)
+};
+
+struct Ctx;
+
+// C = alpha op(A) op(B) + beta C, row-major with leading dimensions.
+// op(A) is M x K, op(B) is K x N.  batch > 1: blockIdx.z strides.
+template <class T>
+void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, long lda,
+          const T* B, long ldb, T beta, T* C, long ldc, int batch = 1, long sA = 0,
+          long sB = 0, long sC = 0);
+
+// G (n x n, row-major, lower triangle written, type S) = X X^T when rows,
+// i.e. X is n x K row-major (ldx) and the contraction runs over K; or
+// X^T X when !rows, X is K x n row-major and the contraction runs over rows.
+// G is overwritten.  Split-K with atomics; FP accumulation in T.
+template <class T, class S>
+void gram(Ctx& c, bool rows, int n, long K, const T* X, long ldx, S* G);
+
+// Cholesky G + shift I = L L^T (lower), single CTA, compute type C.
+// shift = shift_rel * trace(G).  Pivots <= drop_rel * max_diag are dropped
+// (column of L set to 0).  L is n x n row-major (upper part zeroed).
+template <class S, class C>
+void cholesky(Ctx& c, int n, const S* G, S* L, double shift_rel, double drop_rel,
+              CholStatus* st_dev);
+
+// T = L^{-1} for lower-triangular L with possibly zero (dropped) columns:
+// dropped indices give zero rows and columns of T.
+template <class S, class C>
+void trinv(Ctx& c, int n, const S* L, S* T);
+
+// One-sided Jacobi SVD of the rows of R (p x b, row-major, p <= b):
+// R = U diag(sigma) V^T.  Outputs U (p x p, row-major, columns sorted by
+// decreasing sigma), SVt (p x b, row-major, row i = sigma_i v_i^T, sorted),
+// sigma (p doubles, sorted).  work: p*b + p*p elements of S.
+template <class S>
+void jacobi_svd(Ctx& c, int p, int b, const S* R, S* U, S* SVt, double* sigma, S* work);
+
+// sum of squares of n elements, FP64 accumulation, written to *out (device).
+template <class T>
+void sumsq(Ctx& c, long n, const T* x, double* out);
+
+// Frobenius norms for the sigma_min certificate of a lower-triangular L
+// with inverse T: out[0] += ||T||_F^2, out[1] += ||L - I||_F^2.
+template <class S>
+void inv_and_identity_defect(Ctx& c, int n, const S* L, const S* T, double* out);
+
+template <class T>
+void fill_identity(Ctx& c, int n, T* A, long lda);  // A (n x n) = I
+template <class T>
+void scale_inplace(Ctx& c, long n, T* x, double alpha);
+template <class Tin, class Tout>
+void convert(Ctx& c, long n, const Tin* x, Tout* y);
+// Y (rows x cols) = X^T where X is cols x rows, both row-major
+template <class T>
+void transpose(Ctx& c, int rows, int cols, const T* X, T* Y);
+
+// block copy for the rank-concatenating sum: up to 64 blocks per launch,
+// passed by value as a kernel parameter (no host-to-device copy).
+struct BlockDesc {
+    const void* src;  // a x n x b source core
+    long dst_off;     // element offset of block (oa, 0, ob) in the destination
+    int a, b;
+    double alpha;
+};
+struct BlockList {
+    BlockDesc blk[64];
+    int count;
+};
+template <class T>
+void scatter_blocks(Ctx& c, const BlockList& list, int n, long dst_ld_b, long dst_ld_row, T* dst,
+                    int max_a, int max_b);
+template <class T>
+void axpy(Ctx& c, long n, double alpha, const T* x, T* y);  // y += alpha x
+
+// tcgen05 TF32 Gram of the rows of X (n x K, row-major): G = X X^T (lower
+// tiles), split-K, FP32 accumulation in TMEM, atomically added into G (FP32,
+// zeroed first).  Returns false when the shape is not supported.
+bool gram_rows_tc_tf32(Ctx& c, int n, long K, const float* X, long ldx, float* G);
+
+// ---------------------------------------------------------------- context
+struct ProfRec {
+    int fam;
+    double flops, bytes;
+    cudaEvent_t a, b;
+};
+
+struct Ctx {
+    int device = 0;
+    tt_precision prec = TT_FP64;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    tt_stats stats{};
+    tt_sign_rule sign_rule = TT_SIGN_STABLE;
+    int sm_count = 0;
+    bool use_tc = true;  // tensor-core Gram in TT_MIXED_TF32
+
+    // event profiling of launches (off by default)
+    bool prof = false;
+    std::vector<std::string> fam_names;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> ev_pool;
+
+    void* alloc(size_t bytes);
+    void release(void* p, size_t bytes);
+    void sync();
+    int family(const char* name);
+    cudaEvent_t event();
+    ~Ctx();
+};
+
+// Records CUDA events on the context stream around the launches made while
+// it is alive, when profiling is on.
+struct ProfScope {
+    Ctx& c;
+    int fam = -1;
+    double flops, bytes;
+    cudaEvent_t a = nullptr;
+    ProfScope(Ctx& ctx, const char* name, double fl, double by);
+    ~ProfScope();
+};
+
+}  // namespace ttgb

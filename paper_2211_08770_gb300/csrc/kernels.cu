@@ -1,0 +1,681 @@
+// CUDA-core kernels of the TT library: tiled GEMM / split-K Gram, small
+// dense factorizations (Cholesky with rank drop, triangular inverse, one-sided
+// Jacobi SVD), reductions and the block scatter of the TT sum.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace ttgb {
+
+// ------------------------------------------------------------------ GEMM
+// 64x64 output tile, BK = 16, 256 threads, 4x4 outputs per thread (strided
+// by 16 so that shared-memory reads broadcast).  MODE 0: plain (blockIdx.z
+// = batch).  MODE 1: Gram, only tiles with tile_row >= tile_col, blockIdx.z
+// = split of K, result atomically added into C of type CT.
+namespace {
+
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+template <class T, class CT, bool TA, bool TB, int MODE>
+__global__ void __launch_bounds__(256)
+gemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda,
+            const T* __restrict__ B, long ldb, T beta, CT* __restrict__ C, long ldc, long sA,
+            long sB, long sC, long kchunk) {
+    __shared__ T As[GBK][GBM + 1];
+    __shared__ T Bs[GBK][GBN + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    long kbeg = 0, kend = K;
+    if (MODE == 0) {
+        A += blockIdx.z * sA;
+        B += blockIdx.z * sB;
+        C += blockIdx.z * sC;
+    } else {
+        if (blockIdx.x > blockIdx.y) return;  // upper tiles of a symmetric result
+        kbeg = (long)blockIdx.z * kchunk;
+        kend = min(K, kbeg + kchunk);
+        if (kbeg >= kend) return;
+    }
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+
+    for (long k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int e = tid + l * 256;
+            int mm, kk;
+            if (!TA) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
+            const long gm = m0 + mm, gk = k0 + kk;
+            T v = T(0);
+            if (gm < M && gk < kend) v = TA ? A[gk * lda + gm] : A[gm * lda + gk];
+            As[kk][mm] = v;
+        }
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int e = tid + l * 256;
+            int nn, kk;
+            if (!TB) { nn = e & 63; kk = e >> 6; } else { kk = e & 15; nn = e >> 4; }
+            const long gn = n0 + nn, gk = k0 + kk;
+            T v = T(0);
+            if (gn < N && gk < kend) v = TB ? B[gn * ldb + gk] : B[gk * ldb + gn];
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            if (MODE == 0) {
+                T v = alpha * acc[i][j];
+                if (beta != T(0)) v += beta * (T)C[gm * ldc + gn];
+                C[gm * ldc + gn] = (CT)v;
+            } else {
+                atomicAdd(&C[gm * ldc + gn], (CT)acc[i][j]);
+            }
+        }
+    }
+}
+
+template <class T, class CT, int MODE>
+void launch_gemm(Ctx& c, bool tA, bool tB, dim3 grid, int M, int N, long K, T alpha,
+                 const T* A, long lda, const T* B, long ldb, T beta, CT* C, long ldc, long sA,
+                 long sB, long sC, long kchunk) {
+#define TT_GEMM_CASE(TA_, TB_)                                                            \
+    gemm_kernel<T, CT, TA_, TB_, MODE><<<grid, 256, 0, c.stream>>>(                      \
+        M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, kchunk)
+    if (!tA && !tB) TT_GEMM_CASE(false, false);
+    else if (!tA && tB) TT_GEMM_CASE(false, true);
+    else if (tA && !tB) TT_GEMM_CASE(true, false);
+    else TT_GEMM_CASE(true, true);
+#undef TT_GEMM_CASE
+    TT_LAUNCHED(c);
+}
+
+}  // namespace
+
+template <class T>
+void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, long lda,
+          const T* B, long ldb, T beta, T* C, long ldc, int batch, long sA, long sB, long sC) {
+    if (M <= 0 || N <= 0 || batch <= 0) return;
+    if (K <= 0) {
+        // C = beta C: degenerate product
+        if (beta == T(0)) {
+            for (int z = 0; z < batch; ++z)
+                TT_CUDA(cudaMemset2DAsync(C + z * sC, ldc * sizeof(T), 0, N * sizeof(T), M, c.stream));
+            return;
+        }
+        throw_status(TT_ERR_ARG, "gemm with K = 0 and beta != 0");
+    }
+    if (batch > 65535) throw_status(TT_ERR_ARG, "gemm batch too large");
+    ProfScope ps(c, sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", 2.0 * M * N * (double)K * batch,
+                 sizeof(T) * ((double)M * K + (double)K * N + 2.0 * M * N) * batch);
+    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch);
+    if (grid.y > 65535) throw_status(TT_ERR_ARG, "gemm M too large");
+    launch_gemm<T, T, 0>(c, tA, tB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, K);
+}
+
+template <class T, class S>
+void gram(Ctx& c, bool rows, int n, long K, const T* X, long ldx, S* G) {
+    TT_CUDA(cudaMemsetAsync(G, 0, sizeof(S) * (size_t)n * n, c.stream));
+    if (n <= 0 || K <= 0) return;
+    const int tiles = (n + GBM - 1) / GBM;
+    const int tri = tiles * (tiles + 1) / 2;
+    long ksteps = (K + GBK - 1) / GBK;
+    long splits = std::max<long>(1, (4L * c.sm_count + tri - 1) / tri);
+    splits = std::min<long>(splits, std::max<long>(1, ksteps / 4));
+    splits = std::min<long>(splits, 4096);
+    long kchunk = ((ksteps + splits - 1) / splits) * GBK;
+    splits = (K + kchunk - 1) / kchunk;
+    dim3 grid(tiles, tiles, (unsigned)splits);
+    ProfScope ps(c, sizeof(T) == 8 ? "gram_f64" : "gram_f32", (double)n * (n + 1) * (double)K,
+                 sizeof(T) * (double)n * K + sizeof(S) * (double)n * n);
+    // rows: G = X X^T, op(A) = X (n x K), op(B) = X^T  -> tA = false, tB = true
+    // cols: G = X^T X, X is K x n: op(A) = X^T -> tA = true, op(B) = X -> tB = false
+    launch_gemm<T, S, 1>(c, !rows, rows, grid, n, n, K, T(1), X, ldx, X, ldx, T(0), G, n, 0, 0, 0,
+                         kchunk);
+}
+
+// ------------------------------------------------------------- reductions
+namespace {
+
+template <class C>
+__device__ C warp_sum(C v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class C>
+__device__ C block_sum(C v, C* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    C t = (threadIdx.x < nw) ? sh[threadIdx.x] : C(0);
+    if (w == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    C r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+template <class T>
+__global__ void sumsq_kernel(long n, const T* __restrict__ x, double* out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double v = (double)x[i];
+        s = fma(v, v, s);
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
+template <class S>
+__global__ void defect_kernel(int n, const S* __restrict__ L, const S* __restrict__ T, double* out) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    const long nn = (long)n * n;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x) {
+        const double t = (double)T[e];
+        a = fma(t, t, a);
+        const long i = e / n, k = e % n;
+        const double l = (double)L[e] - (i == k ? 1.0 : 0.0);
+        b = fma(l, l, b);
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(out, a);
+        atomicAdd(out + 1, b);
+    }
+}
+
+}  // namespace
+
+template <class T>
+void sumsq(Ctx& c, long n, const T* x, double* out) {
+    TT_CUDA(cudaMemsetAsync(out, 0, sizeof(double), c.stream));
+    if (n <= 0) return;
+    int blocks = (int)std::min<long>((n + 255) / 256, 4L * c.sm_count);
+    sumsq_kernel<T><<<blocks, 256, 0, c.stream>>>(n, x, out);
+    TT_LAUNCHED(c);
+}
+
+template <class S>
+void inv_and_identity_defect(Ctx& c, int n, const S* L, const S* T, double* out) {
+    if (n <= 0) return;
+    long nn = (long)n * n;
+    int blocks = (int)std::min<long>((nn + 255) / 256, 2L * c.sm_count);
+    defect_kernel<S><<<blocks, 256, 0, c.stream>>>(n, L, T, out);
+    TT_LAUNCHED(c);
+}
+
+// -------------------------------------------------------------- Cholesky
+// Right-looking, column by column, one CTA.  The working matrix lives in
+// shared memory when it fits, else in L (global, L2-resident).
+namespace {
+
+template <class S, class C, bool SMEM>
+__global__ void __launch_bounds__(1024)
+chol_kernel(int n, const S* __restrict__ G, S* __restrict__ L, double shift_rel,
+            double drop_rel, CholStatus* st) {
+    extern __shared__ __align__(16) unsigned char chol_smem[];
+    __shared__ double shd[32];
+    __shared__ C s_d;
+    __shared__ int s_ndrop, s_nonfinite;
+    __shared__ double s_minratio;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double tr = 0.0, mx = 0.0;
+    for (int i = tid; i < n; i += nt) {
+        const double g = (double)G[(long)i * n + i];
+        tr += g;
+        mx = fmax(mx, g);
+    }
+    tr = block_sum(tr, shd);
+    // block max
+    {
+        double v = mx;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if ((tid & 31) == 0) shd[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double m = 0.0;
+            for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, shd[w]);
+            shd[0] = m;
+            s_ndrop = 0;
+            s_nonfinite = 0;
+            s_minratio = 1e300;
+        }
+        __syncthreads();
+        mx = shd[0];
+        __syncthreads();
+    }
+    const double shift = shift_rel * tr;
+    const double tau = drop_rel * (mx + shift);
+    C* A = SMEM ? reinterpret_cast<C*>(chol_smem) : nullptr;
+    const long nn = (long)n * n;
+    for (long e = tid; e < nn; e += nt) {
+        const long i = e / n, k = e % n;
+        C v = C(0);
+        if (k <= i) v = (C)G[e] + (i == k ? (C)shift : C(0));
+        if (SMEM) A[e] = v; else L[e] = (S)v;
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (tid == 0) {
+            const C p = SMEM ? A[(long)j * n + j] : (C)L[(long)j * n + j];
+            const double orig = (double)G[(long)j * n + j] + shift;
+            C d = C(0);
+            if (!isfinite((double)p)) {
+                s_nonfinite = 1;
+            } else if ((double)p > tau && p > C(0)) {
+                d = sqrt(p);
+                s_minratio = fmin(s_minratio, orig > 0.0 ? (double)p / orig : 0.0);
+            } else {
+                s_ndrop++;
+            }
+            s_d = d;
+            if (SMEM) A[(long)j * n + j] = d; else L[(long)j * n + j] = (S)d;
+        }
+        __syncthreads();
+        const C d = s_d;
+        if (d == C(0)) {
+            for (int i = j + 1 + tid; i < n; i += nt) {
+                if (SMEM) A[(long)i * n + j] = C(0); else L[(long)i * n + j] = S(0);
+            }
+            __syncthreads();
+            continue;
+        }
+        const C inv = C(1) / d;
+        for (int i = j + 1 + tid; i < n; i += nt) {
+            if (SMEM) A[(long)i * n + j] *= inv;
+            else L[(long)i * n + j] = (S)((C)L[(long)i * n + j] * inv);
+        }
+        __syncthreads();
+        const int rem = n - j - 1;
+        const long rr = (long)rem * rem;
+        for (long e = tid; e < rr; e += nt) {
+            const int i = j + 1 + (int)(e / rem), k = j + 1 + (int)(e % rem);
+            if (k > i) continue;
+            if (SMEM) {
+                A[(long)i * n + k] -= A[(long)i * n + j] * A[(long)k * n + j];
+            } else {
+                L[(long)i * n + k] = (S)((C)L[(long)i * n + k] - (C)L[(long)i * n + j] * (C)L[(long)k * n + j]);
+            }
+        }
+        __syncthreads();
+    }
+    if (SMEM) {
+        for (long e = tid; e < nn; e += nt) L[e] = (S)A[e];
+    }
+    if (tid == 0) {
+        st->ndrop = s_ndrop;
+        st->nonfinite = s_nonfinite;
+        st->min_ratio = s_minratio > 1e299 ? 0.0 : s_minratio;
+        st->trace = tr;
+        st->max_diag = mx;
+    }
+}
+
+}  // namespace
+
+template <class S, class C>
+void cholesky(Ctx& c, int n, const S* G, S* L, double shift_rel, double drop_rel, CholStatus* st) {
+    if (n <= 0) return;
+    const size_t smem = (size_t)n * n * sizeof(C);
+    const int threads = n <= 64 ? 256 : 1024;
+    ProfScope ps(c, "cholesky", (double)n * n * n / 3.0, 2.0 * sizeof(S) * n * n);
+    if (smem <= 160 * 1024) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            TT_CUDA(cudaFuncSetAttribute(chol_kernel<S, C, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+            attr_set = true;
+        }
+        chol_kernel<S, C, true><<<1, threads, smem, c.stream>>>(n, G, L, shift_rel, drop_rel, st);
+    } else {
+        chol_kernel<S, C, false><<<1, threads, 0, c.stream>>>(n, G, L, shift_rel, drop_rel, st);
+    }
+    TT_LAUNCHED(c);
+}
+
+// --------------------------------------------------- triangular inverse
+namespace {
+
+template <class S, class C>
+__global__ void __launch_bounds__(256) trinv_kernel(int n, const S* __restrict__ L, S* __restrict__ T) {
+    extern __shared__ __align__(16) unsigned char trinv_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * (blockDim.x >> 5) + w;
+    if (j >= n) return;  // whole warp leaves; no block barrier below
+    C* x = reinterpret_cast<C*>(trinv_smem) + (long)w * n;
+    const C djj = (C)L[(long)j * n + j];
+    if (djj == C(0)) {
+        for (int i = lane; i < n; i += 32) T[(long)i * n + j] = S(0);
+        return;
+    }
+    for (int i = lane; i < j; i += 32) T[(long)i * n + j] = S(0);
+    if (lane == 0) x[j] = C(1) / djj;
+    __syncwarp();
+    for (int i = j + 1; i < n; ++i) {
+        const C dii = (C)L[(long)i * n + i];
+        C s = C(0);
+        for (int k = j + lane; k < i; k += 32) s = fma((C)L[(long)i * n + k], x[k], s);
+        s = warp_sum(s);
+        if (lane == 0) x[i] = (dii == C(0)) ? C(0) : -s / dii;
+        __syncwarp();
+    }
+    for (int i = j + lane; i < n; i += 32) T[(long)i * n + j] = (S)x[i];
+}
+
+}  // namespace
+
+template <class S, class C>
+void trinv(Ctx& c, int n, const S* L, S* T) {
+    if (n <= 0) return;
+    const int warps = 8;
+    const size_t smem = (size_t)warps * n * sizeof(C);
+    if (smem > 48 * 1024) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            TT_CUDA(cudaFuncSetAttribute(trinv_kernel<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024));
+            attr_set = true;
+        }
+        if (smem > 200 * 1024) throw_status(TT_ERR_ARG, "trinv: n too large");
+    }
+    ProfScope ps(c, "trinv", (double)n * n * n / 3.0, 2.0 * sizeof(S) * n * n);
+    trinv_kernel<S, C><<<(n + warps - 1) / warps, warps * 32, smem, c.stream>>>(n, L, T);
+    TT_LAUNCHED(c);
+}
+
+// ------------------------------------------------ one-sided Jacobi SVD
+// Rows of W (p x b) are orthogonalized by plane rotations in round-robin
+// order, one warp per pair; U accumulates the rotations (rows of Ut are the
+// columns of U).  FP64 arithmetic.  p <= 1024.
+namespace {
+
+__global__ void __launch_bounds__(1024)
+jacobi_kernel(int p, int b, double* __restrict__ W, double* __restrict__ Ut, int max_sweeps, double tol) {
+    __shared__ int s_rot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int pp = p + (p & 1);
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) s_rot = 0;
+        __syncthreads();
+        for (int s = 0; s < pp - 1; ++s) {
+            for (int k = w; k < pp / 2; k += nw) {
+                int i, j;
+                if (k == 0) { i = s; j = pp - 1; }
+                else { i = (s + k) % (pp - 1); j = (s - k + pp - 1) % (pp - 1); }
+                if (i >= p || j >= p) continue;
+                double* wi = W + (long)i * b;
+                double* wj = W + (long)j * b;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int t = lane; t < b; t += 32) {
+                    const double x = wi[t], y = wj[t];
+                    al = fma(x, x, al);
+                    be = fma(y, y, be);
+                    ga = fma(x, y, ga);
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) continue;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                for (int q = lane; q < b; q += 32) {
+                    const double x = wi[q], y = wj[q];
+                    wi[q] = cs * x - sn * y;
+                    wj[q] = sn * x + cs * y;
+                }
+                double* ui = Ut + (long)i * p;
+                double* uj = Ut + (long)j * p;
+                for (int q = lane; q < p; q += 32) {
+                    const double x = ui[q], y = uj[q];
+                    ui[q] = cs * x - sn * y;
+                    uj[q] = sn * x + cs * y;
+                }
+                if (lane == 0) s_rot = 1;
+            }
+            __syncthreads();
+        }
+        const int rot = s_rot;
+        __syncthreads();
+        if (!rot) break;
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(1024)
+jacobi_prep_kernel(int p, int b, const S* __restrict__ R, double* __restrict__ W, double* __restrict__ Ut) {
+    const long pb = (long)p * b, ppp = (long)p * p;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < pb; e += (long)gridDim.x * blockDim.x)
+        W[e] = (double)R[e];
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < ppp; e += (long)gridDim.x * blockDim.x)
+        Ut[e] = (e / p == e % p) ? 1.0 : 0.0;
+}
+
+template <class S>
+__global__ void __launch_bounds__(1024)
+jacobi_finish_kernel(int p, int b, const double* __restrict__ W, const double* __restrict__ Ut,
+                     S* __restrict__ U, S* __restrict__ SVt, double* __restrict__ sigma) {
+    extern __shared__ __align__(16) unsigned char jf_smem[];
+    double* sig = reinterpret_cast<double*>(jf_smem);
+    int* perm = reinterpret_cast<int*>(sig + p);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = w; i < p; i += nw) {
+        double s = 0.0;
+        for (int t = lane; t < b; t += 32) s = fma(W[(long)i * b + t], W[(long)i * b + t], s);
+        s = warp_sum(s);
+        if (lane == 0) sig[i] = sqrt(s);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        int rank = 0;
+        const double si = sig[i];
+        for (int j = 0; j < p; ++j) rank += (sig[j] > si) || (sig[j] == si && j < i);
+        perm[rank] = i;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < p; r += blockDim.x) sigma[r] = sig[perm[r]];
+    const long pb = (long)p * b;
+    for (long e = threadIdx.x; e < pb; e += blockDim.x) {
+        const long r = e / b, t = e % b;
+        SVt[e] = (S)W[(long)perm[r] * b + t];
+    }
+    const long ppp = (long)p * p;
+    for (long e = threadIdx.x; e < ppp; e += blockDim.x) {
+        const long i = e / p, r = e % p;  // U[i][r] = Ut[perm[r]][i]
+        U[e] = (S)Ut[(long)perm[r] * p + i];
+    }
+}
+
+}  // namespace
+
+template <class S>
+void jacobi_svd(Ctx& c, int p, int b, const S* R, S* U, S* SVt, double* sigma, S* work) {
+    if (p <= 0) return;
+    if (p > 1024 || p > b) throw_status(TT_ERR_ARG, "jacobi_svd: need p <= min(b, 1024)");
+    double* W = reinterpret_cast<double*>(work);
+    double* Ut = W + (long)p * b;
+    ProfScope ps(c, "jacobi_svd", 0.0, sizeof(S) * (2.0 * p * b + 2.0 * p * p));
+    jacobi_prep_kernel<S><<<std::max(1, std::min(2 * c.sm_count, (int)(((long)p * b + 1023) / 1024))), 1024, 0,
+                            c.stream>>>(p, b, R, W, Ut);
+    TT_LAUNCHED(c);
+    const int threads = std::min(1024, std::max(32, ((p + 1) / 2) * 32));
+    jacobi_kernel<<<1, threads, 0, c.stream>>>(p, b, W, Ut, 40, 1e-15);
+    TT_LAUNCHED(c);
+    const size_t smem = (size_t)p * (sizeof(double) + sizeof(int));
+    jacobi_finish_kernel<S><<<1, 1024, smem, c.stream>>>(p, b, W, Ut, U, SVt, sigma);
+    TT_LAUNCHED(c);
+}
+
+// ---------------------------------------------------------- elementwise
+namespace {
+
+template <class T>
+__global__ void identity_kernel(int n, T* A, long lda) {
+    const long nn = (long)n * n;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x) {
+        const long i = e / n, k = e % n;
+        A[i * lda + k] = (i == k) ? T(1) : T(0);
+    }
+}
+
+template <class T>
+__global__ void scale_kernel(long n, T* x, double alpha) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        x[e] = (T)((double)x[e] * alpha);
+}
+
+template <class Tin, class Tout>
+__global__ void convert_kernel(long n, const Tin* __restrict__ x, Tout* __restrict__ y) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        y[e] = (Tout)x[e];
+}
+
+template <class T>
+__global__ void transpose_kernel(int rows, int cols, const T* __restrict__ X, T* __restrict__ Y) {
+    __shared__ T tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int xr = by + i, xc = bx + threadIdx.x;  // X is cols x rows: X[xr][xc], xr < cols
+        if (xr < cols && xc < rows) tile[i][threadIdx.x] = X[(long)xr * rows + xc];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int yr = bx + i, yc = by + threadIdx.x;  // Y[yr][yc] = X[yc][yr]
+        if (yr < rows && yc < cols) Y[(long)yr * cols + yc] = tile[threadIdx.x][i];
+    }
+}
+
+template <class T>
+__global__ void scatter_kernel(const BlockList list, int n, long ldb, long ldrow, T* __restrict__ dst) {
+    const BlockDesc& bd = list.blk[blockIdx.y];
+    const T* src = reinterpret_cast<const T*>(bd.src);
+    const long tot = (long)bd.a * n * bd.b;
+    const long nb = (long)n * bd.b;
+    const T alpha = (T)bd.alpha;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+        const long ia = e / nb, rem = e % nb;
+        const long i = rem / bd.b, ib = rem % bd.b;
+        dst[bd.dst_off + ia * ldrow + i * ldb + ib] = alpha * src[e];
+    }
+}
+
+template <class T>
+__global__ void axpy_kernel(long n, T alpha, const T* __restrict__ x, T* __restrict__ y) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        y[e] = fma(alpha, x[e], y[e]);
+}
+
+int grid_for(const Ctx& c, long n, int threads = 256) {
+    return (int)std::max<long>(1, std::min<long>((n + threads - 1) / threads, 8L * c.sm_count));
+}
+
+}  // namespace
+
+template <class T>
+void fill_identity(Ctx& c, int n, T* A, long lda) {
+    if (n <= 0) return;
+    identity_kernel<T><<<grid_for(c, (long)n * n), 256, 0, c.stream>>>(n, A, lda);
+    TT_LAUNCHED(c);
+}
+
+template <class T>
+void scale_inplace(Ctx& c, long n, T* x, double alpha) {
+    if (n <= 0) return;
+    scale_kernel<T><<<grid_for(c, n), 256, 0, c.stream>>>(n, x, alpha);
+    TT_LAUNCHED(c);
+}
+
+template <class Tin, class Tout>
+void convert(Ctx& c, long n, const Tin* x, Tout* y) {
+    if (n <= 0) return;
+    convert_kernel<Tin, Tout><<<grid_for(c, n), 256, 0, c.stream>>>(n, x, y);
+    TT_LAUNCHED(c);
+}
+
+template <class T>
+void transpose(Ctx& c, int rows, int cols, const T* X, T* Y) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 grid((rows + 31) / 32, (cols + 31) / 32);
+    transpose_kernel<T><<<grid, dim3(32, 8), 0, c.stream>>>(rows, cols, X, Y);
+    TT_LAUNCHED(c);
+}
+
+template <class T>
+void scatter_blocks(Ctx& c, const BlockList& list, int n, long dst_ld_b, long dst_ld_row, T* dst, int max_a,
+                    int max_b) {
+    if (list.count <= 0) return;
+    long per = (long)max_a * n * max_b;
+    dim3 grid((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256, 1024)), list.count);
+    ProfScope ps(c, "tt_add_scatter", 0.0, 2.0 * sizeof(T) * per * list.count);
+    scatter_kernel<T><<<grid, 256, 0, c.stream>>>(list, n, dst_ld_b, dst_ld_row, dst);
+    TT_LAUNCHED(c);
+}
+
+template <class T>
+void axpy(Ctx& c, long n, double alpha, const T* x, T* y) {
+    if (n <= 0) return;
+    axpy_kernel<T><<<grid_for(c, n), 256, 0, c.stream>>>(n, (T)alpha, x, y);
+    TT_LAUNCHED(c);
+}
+
+// ------------------------------------------------- explicit instantiations
+#define TT_INST_T(T)                                                                             \
+    template void gemm<T>(Ctx&, bool, bool, int, int, int, T, const T*, long, const T*, long, T, T*, \
+                          long, int, long, long, long);                                          \
+    template void sumsq<T>(Ctx&, long, const T*, double*);                                       \
+    template void fill_identity<T>(Ctx&, int, T*, long);                                         \
+    template void scale_inplace<T>(Ctx&, long, T*, double);                                      \
+    template void transpose<T>(Ctx&, int, int, const T*, T*);                                    \
+    template void scatter_blocks<T>(Ctx&, const BlockList&, int, long, long, T*, int, int);      \
+    template void axpy<T>(Ctx&, long, double, const T*, T*);                                     \
+    template void inv_and_identity_defect<T>(Ctx&, int, const T*, const T*, double*);            \
+    template void jacobi_svd<T>(Ctx&, int, int, const T*, T*, T*, double*, T*);
+TT_INST_T(float)
+TT_INST_T(double)
+template void gram<double, double>(Ctx&, bool, int, long, const double*, long, double*);
+template void gram<float, float>(Ctx&, bool, int, long, const float*, long, float*);
+template void cholesky<double, double>(Ctx&, int, const double*, double*, double, double, CholStatus*);
+template void cholesky<float, float>(Ctx&, int, const float*, float*, double, double, CholStatus*);
+template void trinv<double, double>(Ctx&, int, const double*, double*);
+template void trinv<float, float>(Ctx&, int, const float*, float*);
+template void convert<double, float>(Ctx&, long, const double*, float*);
+template void convert<float, double>(Ctx&, long, const float*, double*);
+
+}  // namespace ttgb

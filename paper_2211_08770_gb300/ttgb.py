@@ -1,0 +1,310 @@
+"""Thin ctypes binding of the C ABI declared in include/ttgb.h.
+
+Argument marshalling only: every step of TT sums, dots, rounding and the
+orthogonalization schemes runs in the CUDA library (libttgb.so).  There is no
+CPU fallback: if the library is missing or no sm_103 GPU is present, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TT_OK = 0
+STATUS = {0: "TT_OK", 1: "TT_ERR_ARG", 2: "TT_ERR_SHAPE", 3: "TT_ERR_OOM", 4: "TT_ERR_NOT_SPD",
+          5: "TT_ERR_BREAKDOWN", 6: "TT_ERR_NONFINITE", 7: "TT_ERR_TIMEOUT", 8: "TT_ERR_CUDA"}
+PRECISION = {"fp64": 0, "mixed_tf32": 1, "fp32": 2}
+SCHEME = {"cgs": 0, "mgs": 1, "cgs2": 2, "mgs2": 3, "gram": 4, "householder": 5}
+POLICY = {"paper": 0, "every_update": 1}
+SIGN = {"stable": 0, "literal": 1}
+DTYPE_F64, DTYPE_F32 = 0, 1
+
+
+class TTError(RuntimeError):
+    def __init__(self, status, where, msg=""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__("%s: %s %s" % (where, self.name, msg))
+
+
+class _Stats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("kernel_launches", "roundings", "host_syncs", "bytes_in_use",
+                                           "peak_bytes", "svd_calls", "certified_bonds", "fallback_orth")]
+
+
+class _Prof(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double),
+                ("flops", C.c_double), ("bytes", C.c_double)]
+
+
+_lib = None
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_PI = C.POINTER(C.c_int)
+_PD = C.POINTER(C.c_double)
+_PP = C.POINTER(C.c_void_p)
+
+_SIGS = {
+    "tt_ctx_create": (_I, [C.POINTER(_P), _I, _I, _P, C.c_size_t]),
+    "tt_ctx_destroy": (None, [_P]),
+    "tt_ctx_get_stats": (_I, [_P, C.POINTER(_Stats)]),
+    "tt_ctx_reset_stats": (None, [_P]),
+    "tt_ctx_precision": (_I, [_P]),
+    "tt_ctx_set_profiling": (_I, [_P, _I]),
+    "tt_ctx_get_profile": (_I, [_P, C.POINTER(_Prof), _I, _PI]),
+    "tt_ctx_reset_profile": (None, [_P]),
+    "tt_tensor_create": (_I, [_P, _I, _PI, _PI, C.POINTER(_PD), C.POINTER(_P)]),
+    "tt_tensor_wrap_device": (_I, [_P, _I, _PI, _PI, _PP, _I, C.POINTER(_P)]),
+    "tt_tensor_shape": (_I, [_P, _PI, _PI, _PI]),
+    "tt_tensor_core_ptr": (_I, [_P, _I, _PP]),
+    "tt_tensor_download": (_I, [_P, _P, C.POINTER(_PD)]),
+    "tt_tensor_free": (None, [_P]),
+    "tt_add": (_I, [_P, _I, _PD, _PP, C.POINTER(_P)]),
+    "tt_scale": (_I, [_P, _P, _D, C.POINTER(_P)]),
+    "tt_dot": (_I, [_P, _P, _P, _PD]),
+    "tt_dot_many": (_I, [_P, _P, _I, _PP, _PD]),
+    "tt_norm": (_I, [_P, _P, _PD]),
+    "tt_round": (_I, [_P, _P, _D, C.POINTER(_P), _PD]),
+    "tt_round_batched": (_I, [_P, _I, _PP, _PD, _PP]),
+    "tt_orthogonalize": (_I, [_P, _I, _D, _I, _I, _PP, _PP, _PD, _PI]),
+    "tt_set_sign_rule": (_I, [_P, _I]),
+    "tt_status_str": (C.c_char_p, [_I]),
+    "tt_last_error": (C.c_char_p, []),
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Loads libttgb.so (built in-tree by ``build.build()``); raises if absent."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libttgb.so is not built (%s); call paper_2211_08770_gb300.build.build()" % path)
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st, where):
+    if st != TT_OK:
+        msg = lib().tt_last_error()
+        raise TTError(st, where, msg.decode() if msg else "")
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover - torch is optional plumbing
+        pass
+    return 0
+
+
+class Ctx:
+    """A tt_ctx: device, arithmetic (fp64 / mixed_tf32 / fp32), CUDA stream
+    (an integer cudaStream_t; default: torch's current stream) and HBM budget
+    in bytes (0 = none)."""
+
+    def __init__(self, device=0, precision="fp64", stream=None, hbm_budget=0):
+        self._h = _P()
+        self.precision = precision
+        self.stream = _default_stream() if stream is None else int(stream)
+        _check(lib().tt_ctx_create(C.byref(self._h), device, PRECISION[precision], _P(self.stream or None),
+                                   hbm_budget), "tt_ctx_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self):
+        s = _Stats()
+        _check(lib().tt_ctx_get_stats(self._h, C.byref(s)), "tt_ctx_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in _Stats._fields_}
+
+    def reset_stats(self):
+        lib().tt_ctx_reset_stats(self._h)
+
+    def set_profiling(self, on=True):
+        _check(lib().tt_ctx_set_profiling(self._h, 1 if on else 0), "tt_ctx_set_profiling")
+
+    def reset_profile(self):
+        lib().tt_ctx_reset_profile(self._h)
+
+    def profile(self):
+        """{family: dict(launches, total_ms, flops, bytes)} since the last reset."""
+        buf = (_Prof * 64)()
+        k = C.c_int()
+        _check(lib().tt_ctx_get_profile(self._h, buf, 64, C.byref(k)), "tt_ctx_get_profile")
+        return {buf[i].name.decode(): dict(launches=int(buf[i].launches), total_ms=buf[i].total_ms,
+                                           flops=buf[i].flops, bytes=buf[i].bytes) for i in range(min(64, k.value))}
+
+    def set_sign_rule(self, rule):
+        _check(lib().tt_set_sign_rule(self._h, SIGN[rule]), "tt_set_sign_rule")
+
+    def close(self):
+        if self._h:
+            lib().tt_ctx_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TT:
+    """Handle of a device TT tensor (tt_tensor*) owned by the library."""
+
+    def __init__(self, ctx, handle, keepalive=None):
+        self.ctx = ctx
+        self._h = handle
+        self._keep = keepalive
+
+    @property
+    def handle(self):
+        return self._h
+
+    def shape(self):
+        d = C.c_int()
+        _check(lib().tt_tensor_shape(self._h, C.byref(d), None, None), "tt_tensor_shape")
+        n = (C.c_int * d.value)()
+        r = (C.c_int * (d.value + 1))()
+        _check(lib().tt_tensor_shape(self._h, None, n, r), "tt_tensor_shape")
+        return d.value, list(n), list(r)
+
+    @property
+    def ranks(self):
+        return self.shape()[2]
+
+    def core_ptr(self, k):
+        p = _P()
+        _check(lib().tt_tensor_core_ptr(self._h, k, C.byref(p)), "tt_tensor_core_ptr")
+        return p.value
+
+    def cores(self):
+        """Downloads the cores as float64 numpy arrays (r_{k-1}, n_k, r_k)."""
+        d, n, r = self.shape()
+        out = [np.empty((r[k], n[k], r[k + 1]), dtype=np.float64) for k in range(d)]
+        ptrs = (_PD * d)(*[o.ctypes.data_as(_PD) for o in out])
+        _check(lib().tt_tensor_download(self.ctx.handle, self._h, ptrs), "tt_tensor_download")
+        return out
+
+    def free(self):
+        if self._h:
+            lib().tt_tensor_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _handles(xs):
+    return (_P * len(xs))(*[x.handle for x in xs])
+
+
+def tt_tensor_create(ctx, cores):
+    cores = [np.ascontiguousarray(c, dtype=np.float64) for c in cores]
+    d = len(cores)
+    n = (C.c_int * d)(*[c.shape[1] for c in cores])
+    r = (C.c_int * (d + 1))(*([c.shape[0] for c in cores] + [cores[-1].shape[2]]))
+    ptrs = (_PD * d)(*[c.ctypes.data_as(_PD) for c in cores])
+    h = _P()
+    _check(lib().tt_tensor_create(ctx.handle, d, n, r, ptrs, C.byref(h)), "tt_tensor_create")
+    return TT(ctx, h)
+
+
+def tt_tensor_wrap_device(ctx, n, r, dev_ptrs, dtype, keepalive=None):
+    d = len(n)
+    nn = (C.c_int * d)(*n)
+    rr = (C.c_int * (d + 1))(*r)
+    pp = (_P * d)(*dev_ptrs)
+    h = _P()
+    _check(lib().tt_tensor_wrap_device(ctx.handle, d, nn, rr, pp, dtype, C.byref(h)), "tt_tensor_wrap_device")
+    return TT(ctx, h, keepalive)
+
+
+def tt_add(ctx, alphas, xs):
+    al = (C.c_double * len(xs))(*[float(a) for a in alphas])
+    h = _P()
+    _check(lib().tt_add(ctx.handle, len(xs), al, _handles(xs), C.byref(h)), "tt_add")
+    return TT(ctx, h)
+
+
+def tt_scale(ctx, x, alpha):
+    h = _P()
+    _check(lib().tt_scale(ctx.handle, x.handle, float(alpha), C.byref(h)), "tt_scale")
+    return TT(ctx, h)
+
+
+def tt_dot(ctx, x, y):
+    v = C.c_double()
+    _check(lib().tt_dot(ctx.handle, x.handle, y.handle, C.byref(v)), "tt_dot")
+    return v.value
+
+
+def tt_dot_many(ctx, x, ys):
+    out = (C.c_double * max(1, len(ys)))()
+    _check(lib().tt_dot_many(ctx.handle, x.handle, len(ys), _handles(ys), out), "tt_dot_many")
+    return np.array(out[: len(ys)])
+
+
+def tt_norm(ctx, x):
+    v = C.c_double()
+    _check(lib().tt_norm(ctx.handle, x.handle, C.byref(v)), "tt_norm")
+    return v.value
+
+
+def tt_round(ctx, x, delta):
+    h = _P()
+    e = C.c_double()
+    _check(lib().tt_round(ctx.handle, x.handle, float(delta), C.byref(h), C.byref(e)), "tt_round")
+    return TT(ctx, h), e.value
+
+
+def tt_round_batched(ctx, xs, deltas):
+    k = len(xs)
+    dl = (C.c_double * k)(*[float(v) for v in deltas])
+    out = (_P * k)()
+    _check(lib().tt_round_batched(ctx.handle, k, _handles(xs), dl, out), "tt_round_batched")
+    return [TT(ctx, _P(out[i])) for i in range(k)]
+
+
+def tt_orthogonalize(ctx, scheme, A, delta, policy="paper"):
+    m = len(A)
+    Q = (_P * m)()
+    R = (C.c_double * (m * m))()
+    nr = C.c_int()
+    _check(lib().tt_orthogonalize(ctx.handle, SCHEME[scheme], float(delta), POLICY[policy], m, _handles(A), Q, R,
+                                  C.byref(nr)), "tt_orthogonalize")
+    Rm = np.array(R[:]).reshape(m, m).T.copy()  # column-major -> R[j, i]
+    return [TT(ctx, _P(Q[i])) for i in range(m)], Rm, nr.value
+
+
+def loss_of_orthogonality(ctx, Q):
+    """||I - Q^T Q||_2 with (Q^T Q)(i,j) = <q_i, q_j> from GPU TT dots
+    (Section 3.4, eq. LOO); the m x m spectral norm is a host metric."""
+    m = len(Q)
+    G = np.zeros((m, m))
+    for i in range(m):
+        v = tt_dot_many(ctx, Q[i], Q[: i + 1])
+        G[i, : i + 1] = v
+        G[: i + 1, i] = v
+    return float(np.max(np.abs(np.linalg.eigvalsh(np.eye(m) - G))))

@@ -1,0 +1,271 @@
+"""GPU-vs-oracle parity through the C ABI (ctypes binding of libttgb.so).
+
+TT cores are unique only up to invertible gauge changes, so results are
+compared on gauge invariants: TT-ranks, the TT norm of the difference
+(computed by the oracle from the explicit difference TT), and the bond
+singular values.  FP64 path: 1e-12 relative.  FP32 / mixed paths: the
+rounding error against the FP64 input stays within (delta + 1e-6) ||x||.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from ttinputs import random_tt, random_tts, coefficients, rank_profile
+
+pytestmark = pytest.mark.gpu
+
+T = pytest.importorskip("paper_2211_08770_gb300.ttgb")
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    from paper_2211_08770_gb300 import build
+    build.build()
+    out = {p: T.Ctx(0, p) for p in ("fp64", "fp32", "mixed_tf32")}
+    yield out
+    for c in out.values():
+        c.close()
+
+
+def up(ctx, cores):
+    return T.tt_tensor_create(ctx, cores)
+
+
+def _rand(seed, n, ranks):
+    return random_tt(np.random.default_rng(seed), n, ranks)
+
+
+def _decaying(seed, n, terms=8):
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(terms):
+        vs = [rng.standard_normal(k) for k in n]
+        out.append([(2.0 ** -j) * vs[0].reshape(1, -1, 1)] + [v.reshape(1, -1, 1) for v in vs[1:]])
+    return O.tt_add([1.0] * terms, out)
+
+
+def _sum_case(seed, m, d, n, r):
+    xs = random_tts(seed, m, d, n, r)
+    al = coefficients(seed + 1, m)
+    return O.tt_add(list(al), xs)
+
+
+def _gauge_padded(seed):
+    rng = np.random.default_rng(seed)
+    n, ranks = [5, 6, 5, 6], [1, 2, 3, 2, 1]
+    x = random_tt(rng, n, ranks)
+    A, Ap = [np.ones((1, 1))], [np.ones((1, 1))]
+    for k in range(1, 4):
+        M = rng.standard_normal((ranks[k], ranks[k] + 3))
+        A.append(M)
+        Ap.append(np.linalg.pinv(M))
+    A.append(np.ones((1, 1)))
+    Ap.append(np.ones((1, 1)))
+    return [np.einsum("pa,aib,bq->piq", Ap[k], x[k], A[k + 1]) for k in range(4)]
+
+
+ROUND_CASES = {
+    "small_random_d4": (lambda: _rand(1, [8] * 4, [1, 4, 4, 4, 1]), 1e-8),
+    "sum_d6_n16": (lambda: _sum_case(2, 5, 6, 16, 6), 1e-6),
+    "decaying_03": (lambda: _decaying(3, [5, 4, 6, 3]), 0.3),
+    "decaying_005": (lambda: _decaying(3, [5, 4, 6, 3]), 0.05),
+    "decaying_1e3": (lambda: _decaying(4, [7, 9, 5, 6, 4]), 1e-3),
+    "redundant_sum": (lambda: O.tt_add([1.0, 1.0, -1.0], [_rand(5, [6, 5, 6, 5, 4], [1, 3, 4, 4, 3, 1])] * 3), 1e-12),
+    "gauge_padded": (lambda: _gauge_padded(6), 1e-12),
+    "ragged": (lambda: _rand(7, [3, 17, 5, 70, 2], [1, 3, 7, 11, 2, 1]), 1e-10),
+    "rank_one": (lambda: _rand(8, [4, 9, 3], [1, 1, 1, 1]), 1e-6),
+    "d2": (lambda: _decaying(9, [12, 10]), 1e-2),
+    "delta0": (lambda: _rand(10, [4, 4, 4, 4], [1, 3, 5, 3, 1]), 0.0),
+    "wide_first_core": (lambda: _sum_case(11, 4, 5, 3, 5), 1e-7),
+}
+
+
+def _check_fp64(got, ref, x):
+    assert O.tt_ranks(got) == O.tt_ranks(ref)
+    nx = O.tt_norm(x)
+    assert O.tt_diff_norm(got, ref) <= 1e-12 * nx
+    for sg, sr in zip(O.bond_singular_values(got), O.bond_singular_values(ref)):
+        m = min(len(sg), len(sr))
+        assert np.all(np.abs(sg[:m] - sr[:m]) <= 1e-12 * max(sr[0], 1e-300))
+
+
+@pytest.mark.parametrize("case", sorted(ROUND_CASES))
+def test_round_fp64_matches_oracle(ctxs, case):
+    make, delta = ROUND_CASES[case]
+    x = make()
+    ref = O.tt_round(x, delta)
+    y, err = T.tt_round(ctxs["fp64"], up(ctxs["fp64"], x), delta)
+    got = y.cores()
+    _check_fp64(got, ref, x)
+    assert err <= delta * (1 + 1e-9) + 1e-15
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed_tf32"])
+@pytest.mark.parametrize("case", ["small_random_d4", "sum_d6_n16", "decaying_03", "decaying_005", "decaying_1e3",
+                                  "ragged", "rank_one", "d2", "wide_first_core"])
+def test_round_reduced_precision_error_bound(ctxs, prec, case):
+    make, delta = ROUND_CASES[case]
+    delta = max(delta, 1e-6)
+    x = make()
+    y, _ = T.tt_round(ctxs[prec], up(ctxs[prec], x), delta)
+    got = y.cores()
+    nx = O.tt_norm(x)
+    assert O.tt_diff_norm(got, x) <= (delta + 1e-6) * nx
+    ref = O.tt_round(x, delta)
+    rg, rr = O.tt_ranks(got), O.tt_ranks(ref)
+    assert all(abs(a - b) <= 1 for a, b in zip(rg, rr)), (rg, rr)
+
+
+def test_round_mixed_exact_ranks_on_well_separated_spectrum(ctxs):
+    # random sums: every singular value is far from eps, so ranks are exact
+    x = _sum_case(12, 6, 6, 16, 5)
+    ref = O.tt_round(x, 1e-6)
+    for prec in ("fp32", "mixed_tf32"):
+        y, _ = T.tt_round(ctxs[prec], up(ctxs[prec], x), 1e-6)
+        assert y.ranks == O.tt_ranks(ref)
+
+
+def test_add_bit_exact_fp64(ctxs):
+    c = ctxs["fp64"]
+    xs = random_tts(13, 4, 5, 7, 3) + [_rand(14, [7] * 5, [1, 2, 5, 1, 4, 1])]
+    al = [0.5, -1.25, 3.0, 0.1, -2.0]
+    s = T.tt_add(c, al, [up(c, x) for x in xs]).cores()
+    ref = O.tt_add(al, xs)
+    assert O.tt_ranks(s) == O.tt_ranks(ref)
+    for a, b in zip(s, ref):
+        assert np.array_equal(a, b)
+
+
+def test_add_d1(ctxs):
+    c = ctxs["fp64"]
+    xs = [[np.arange(5.0).reshape(1, 5, 1)], [np.ones((1, 5, 1))]]
+    s = T.tt_add(c, [2.0, -1.0], [up(c, x) for x in xs]).cores()
+    assert np.allclose(s[0].ravel(), 2 * np.arange(5.0) - 1, atol=0)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_dot_and_norm_fp64(ctxs, seed):
+    c = ctxs["fp64"]
+    rng = np.random.default_rng(40 + seed)
+    d = 3 + seed
+    n = [int(v) for v in rng.integers(2, 9, size=d)]
+    _, rx = rank_profile(d, n, 5)
+    _, ry = rank_profile(d, n, 3)
+    x, y = random_tt(rng, n, rx), random_tt(rng, n, ry)
+    gx, gy = up(c, x), up(c, y)
+    ref = O.tt_dot(x, y)
+    scale = O.tt_norm(x) * O.tt_norm(y)
+    assert abs(T.tt_dot(c, gx, gy) - ref) <= 1e-12 * scale
+    assert abs(T.tt_norm(c, gx) - O.tt_norm(x)) <= 1e-12 * O.tt_norm(x)
+    many = T.tt_dot_many(c, gx, [gy, gx])
+    assert abs(many[1] - O.tt_dot(x, x)) <= 1e-12 * O.tt_norm(x) ** 2
+
+
+def test_dot_mixed(ctxs):
+    x = _rand(50, [6, 7, 8], [1, 4, 5, 1])
+    y = _rand(51, [6, 7, 8], [1, 3, 2, 1])
+    for prec in ("fp32", "mixed_tf32"):
+        c = ctxs[prec]
+        v = T.tt_dot(c, up(c, x), up(c, y))
+        assert abs(v - O.tt_dot(x, y)) <= 1e-5 * O.tt_norm(x) * O.tt_norm(y)
+
+
+def _small_inputs(m=10, seed=0):
+    xs = random_tts(seed, m, 4, 8, 4)
+    return [O.tt_scale(x, 1.0 / O.tt_norm(x)) for x in xs]
+
+
+def _compare_schemes(Qg, Rg, ng, Qo, Ro, no, tol):
+    assert ng == no
+    assert np.allclose(Rg, Ro, atol=tol * np.max(np.abs(Ro)))
+    for qg, qo in zip(Qg, Qo):
+        c = qg.cores()
+        assert O.tt_ranks(c) == O.tt_ranks(qo)
+        assert O.tt_diff_norm(c, qo) <= tol
+
+
+def test_mgs_small_workload_every_update_fp64(ctxs):
+    # order 4, mode 8, ranks 4, m = 10, delta = 1e-8, rounding after every update
+    c = ctxs["fp64"]
+    A = _small_inputs()
+    Qo, Ro, no = O.tt_mgs(A, 1e-8, "every_update")
+    Qg, Rg, ng = T.tt_orthogonalize(c, "mgs", [up(c, a) for a in A], 1e-8, "every_update")
+    _compare_schemes(Qg, Rg, ng, Qo, Ro, no, 1e-12)
+    # dense brute force on 8^4 entries
+    Ad = np.column_stack([O.tt_full(a).ravel() for a in A])
+    Qd = np.column_stack([O.tt_full(q.cores()).ravel() for q in Qg])
+    assert np.linalg.norm(Qd @ Rg - Ad) <= 1e-6 * np.linalg.norm(Ad)
+    assert abs(T.loss_of_orthogonality(c, Qg) - O.loss_of_orthogonality(Qo)) <= 1e-12
+
+
+@pytest.mark.parametrize("scheme", ["cgs", "mgs", "cgs2", "mgs2", "gram", "householder"])
+def test_schemes_fp64_match_oracle(ctxs, scheme):
+    c = ctxs["fp64"]
+    A = _small_inputs(m=6, seed=3)
+    Qo, Ro, no = O.orthogonalize(scheme, A, 1e-8)
+    Qg, Rg, ng = T.tt_orthogonalize(c, scheme, [up(c, a) for a in A], 1e-8)
+    _compare_schemes(Qg, Rg, ng, Qo, Ro, no, 1e-11)
+
+
+@pytest.mark.parametrize("scheme", ["mgs2", "cgs2", "householder", "gram"])
+def test_schemes_mixed_loo_and_accuracy(ctxs, scheme):
+    A = _small_inputs(m=6, seed=4)
+    Qo, Ro, no = O.orthogonalize(scheme, A, 1e-5)
+    loo_o = O.loss_of_orthogonality(Qo)
+    for prec in ("fp32", "mixed_tf32"):
+        c = ctxs[prec]
+        Qg, Rg, ng = T.tt_orthogonalize(c, scheme, [up(c, a) for a in A], 1e-5)
+        assert ng == no
+        loo = T.loss_of_orthogonality(c, Qg)
+        assert loo <= max(10 * loo_o, 1e-6) + 1e-5, (prec, loo, loo_o)
+        assert np.allclose(Rg, Ro, atol=1e-4)
+
+
+def test_errors(ctxs):
+    c = ctxs["fp64"]
+    x = up(c, _rand(60, [4, 5, 6], [1, 2, 2, 1]))
+    y = up(c, _rand(61, [4, 5, 7], [1, 2, 2, 1]))
+    with pytest.raises(T.TTError) as e:
+        T.tt_dot(c, x, y)
+    assert e.value.name == "TT_ERR_SHAPE"
+    with pytest.raises(T.TTError) as e:
+        T.tt_round(c, x, -1.0)
+    assert e.value.name == "TT_ERR_ARG"
+    with pytest.raises(T.TTError) as e:
+        T.tt_round(c, x, float("nan"))
+    assert e.value.name == "TT_ERR_ARG"
+    with pytest.raises(T.TTError) as e:
+        T.tt_add(c, [], [])
+    assert e.value.name == "TT_ERR_ARG"
+    a = _small_inputs(m=3, seed=7)
+    with pytest.raises(T.TTError) as e:
+        T.tt_orthogonalize(c, "gram", [up(c, a[0]), up(c, a[1]), up(c, a[0])], 1e-10)
+    assert e.value.name == "TT_ERR_NOT_SPD"
+    with pytest.raises(T.TTError) as e:
+        T.tt_orthogonalize(c, "mgs", [up(c, a[0]), up(c, O.tt_scale(a[1], 0.0))], 1e-10)
+    assert e.value.name == "TT_ERR_BREAKDOWN"
+
+
+def test_hbm_budget_admission(ctxs):
+    small = T.Ctx(0, "fp64", hbm_budget=64 * 1024)
+    with pytest.raises(T.TTError) as e:
+        T.tt_tensor_create(small, _rand(62, [64, 64, 64], [1, 32, 32, 1]))
+    assert e.value.name == "TT_ERR_OOM"
+    small.close()
+
+
+def test_full_size_sum_rounding_sampled(ctxs):
+    # the single-rounding workload at full size: 20 terms, d = 10, n = 64,
+    # ranks 20 (concatenated rank 400), delta = 1e-6
+    from ttinputs import cfg_round_sum
+    alpha, xs = cfg_round_sum(0)
+    x = O.tt_add(list(alpha), xs)
+    ref = O.tt_round(x, 1e-6)
+    for prec in ("fp64", "mixed_tf32"):
+        c = ctxs[prec]
+        g = T.tt_add(c, list(alpha), [up(c, v) for v in xs])
+        y, _ = T.tt_round(c, g, 1e-6)
+        got = y.cores()
+        assert O.tt_ranks(got) == O.tt_ranks(ref)
+        tol = 1e-12 if prec == "fp64" else 1e-6 + 1e-6
+        assert O.tt_diff_norm(got, ref) <= tol * O.tt_norm(x)
