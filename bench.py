@@ -238,7 +238,7 @@ def run_ours(args):
     def time_e2e(precision, steps):
         ctx = T.Ctx(local, precision, stream=stream.cuda_stream)
         es = 8 if precision == "fp64" else 4
-        h2d = sum(c.size for c in xs) * es
+        h2d = sum(c.size for x in xs for c in x) * es
         times, d2h = [], 0
         for i in range(steps + 1):
             torch.cuda.synchronize()

@@ -116,6 +116,9 @@ typedef struct {
  * Returns TT_ERR_CUDA if the device is absent or not sm_103. */
 tt_status tt_ctx_create(tt_ctx** ctx, int device, tt_precision prec,
                         void* cuda_stream, size_t hbm_budget);
+/* Releases the caller's reference.  Tensors still alive keep the context
+ * (and their memory) valid until they are freed; the context must not be
+ * used for new calls after tt_ctx_destroy. */
 void      tt_ctx_destroy(tt_ctx* ctx);
 tt_status tt_ctx_get_stats(const tt_ctx* ctx, tt_stats* out);
 void      tt_ctx_reset_stats(tt_ctx* ctx);
@@ -213,6 +216,21 @@ tt_status tt_orthogonalize(tt_ctx* ctx, tt_scheme scheme, double delta,
                            tt_round_policy policy, int m,
                            const tt_tensor* const* A, tt_tensor** Q,
                            double* R, int* n_rounds);
+
+/* ---- building block ---------------------------------------------------- */
+
+/* Gram step of the Cholesky QR passes of TT-round: G = X X^T for a device
+ * FP32 matrix X (n x K, row-major, leading dimension ldx >= K), written to
+ * the device FP32 matrix G (n x n, row-major, overwritten).  Only tiles on
+ * or below the diagonal are computed (128 x 128 tiles for the tensor-core
+ * kernel, 64 x 64 for the CUDA-core one); strictly-upper tiles stay zero.
+ * use_tensor_cores != 0 selects the tcgen05 kind::tf32 kernel (TMA-staged
+ * operands, FP32 accumulation in TMEM), else the CUDA-core FP32 kernel.
+ * TT_ERR_ARG when the tensor-core kernel cannot take the layout (X not
+ * 16-byte aligned or ldx*4 not a multiple of 16); TT_ERR_TIMEOUT when one of
+ * its bounded waits ran out. */
+tt_status tt_gram_f32(tt_ctx* ctx, int n, long K, const float* X, long ldx, float* G,
+                      int use_tensor_cores);
 
 /* Householder sign rule used by subsequent TT_HOUSEHOLDER calls. */
 tt_status tt_set_sign_rule(tt_ctx* ctx, tt_sign_rule rule);

@@ -77,6 +77,17 @@ Ctx::~Ctx() {
         cudaEventDestroy(r.b);
     }
     for (auto e : ev_pool) cudaEventDestroy(e);
+    if (tc_err) cudaFree(tc_err);
+}
+
+void check_tc_error(Ctx& c) {
+    int h = 0;
+    TT_CUDA(cudaMemcpyAsync(&h, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    if (h) {
+        TT_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
+        throw_status(TT_ERR_TIMEOUT, "a bounded wait inside a tensor-core kernel ran out");
+    }
 }
 
 ProfScope::ProfScope(Ctx& ctx, const char* name, double fl, double by) : c(ctx), flops(fl), bytes(by) {
@@ -130,13 +141,23 @@ tt_tensor* new_tensor(tt_ctx* ctx, int d, const int* n, const int* r) {
     t->bytes = off;
     t->owned = true;
     for (int k = 0; k < d; ++k) t->cores[k] = (char*)t->block + offs[k];
+    ctx->refs++;
     return t;
+}
+
+void drop_ctx_ref(tt_ctx* c) {
+    if (--c->refs == 0) {
+        cudaStreamSynchronize(c->stream);
+        delete c;
+    }
 }
 
 void free_tensor(tt_tensor* t) {
     if (!t) return;
-    if (t->owned && t->block) t->ctx->release(t->block, t->bytes);
+    tt_ctx* c = t->ctx;
+    if (t->owned && t->block) c->release(t->block, t->bytes);
     delete t;
+    drop_ctx_ref(c);
 }
 
 void check_same_modes(const tt_tensor* a, const tt_tensor* b) {
@@ -315,10 +336,17 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     c->stream = (cudaStream_t)stream;
     c->budget = hbm_budget;
     c->sm_count = prop.multiProcessorCount;
+    // TTGB_NO_TENSOR_CORES=1 keeps TT_MIXED_TF32 contexts on the CUDA-core Gram
+    const char* no_tc = getenv("TTGB_NO_TENSOR_CORES");
+    if (no_tc && no_tc[0] == '1') c->use_tc = false;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (cudaMalloc(&c->tc_err, sizeof(int)) != cudaSuccess || cudaMemset(c->tc_err, 0, sizeof(int)) != cudaSuccess) {
+        delete c;
+        throw_status(TT_ERR_CUDA, "could not allocate the device status word");
     }
     *out = c;
     TT_API_END
@@ -327,7 +355,7 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
 void tt_ctx_destroy(tt_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
-    delete ctx;
+    drop_ctx_ref(ctx);  // deleted now, or when its last tensor is freed
 }
 
 tt_status tt_ctx_get_stats(const tt_ctx* ctx, tt_stats* out) {
@@ -444,6 +472,7 @@ tt_status tt_tensor_wrap_device(tt_ctx* ctx, int d, const int* n, const int* r, 
             throw_status(TT_ERR_ARG, "NULL core");
         }
     t->owned = false;
+    ctx->refs++;
     *out = t;
     TT_API_END
 }
@@ -514,6 +543,19 @@ tt_status tt_dot_many(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tenso
     TT_API_BEGIN
     if (!ctx) throw_status(TT_ERR_ARG, "NULL argument");
     dot_many_internal(ctx, x, count, y, out);
+    TT_API_END
+}
+
+tt_status tt_gram_f32(tt_ctx* ctx, int n, long K, const float* X, long ldx, float* G, int use_tensor_cores) {
+    TT_API_BEGIN
+    if (!ctx || !X || !G || n < 1 || K < 1 || ldx < K) throw_status(TT_ERR_ARG, "bad arguments");
+    if (use_tensor_cores) {
+        if (!gram_rows_tc_tf32(*ctx, n, K, X, ldx, G)) throw_status(TT_ERR_ARG, "layout not supported by TMA");
+        check_tc_error(*ctx);
+    } else {
+        gram<float, float>(*ctx, true, n, K, X, ldx, G);
+        ctx->sync();
+    }
     TT_API_END
 }
 

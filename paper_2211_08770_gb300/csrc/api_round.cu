@@ -290,6 +290,7 @@ struct Rounder {
     }
 
     void check_all_status() {
+        if (tc) check_tc_error(*c);
         if (nst == 0) return;
         std::vector<CholStatus> hs(nst);
         TT_CUDA(cudaMemcpyAsync(hs.data(), st, nst * sizeof(CholStatus), cudaMemcpyDeviceToHost, c->stream));

@@ -117,6 +117,8 @@ void axpy(Ctx& c, long n, double alpha, const T* x, T* y);  // y += alpha x
 // tiles), split-K, FP32 accumulation in TMEM, atomically added into G (FP32,
 // zeroed first).  Returns false when the shape is not supported.
 bool gram_rows_tc_tf32(Ctx& c, int n, long K, const float* X, long ldx, float* G);
+// reads (and clears) the tensor-core timeout flag; throws TT_ERR_TIMEOUT if set
+void check_tc_error(Ctx& c);
 
 // ---------------------------------------------------------------- context
 struct ProfRec {
@@ -134,6 +136,10 @@ struct Ctx {
     tt_sign_rule sign_rule = TT_SIGN_STABLE;
     int sm_count = 0;
     bool use_tc = true;  // tensor-core Gram in TT_MIXED_TF32
+    int* tc_err = nullptr;  // device flag: a bounded wait of a tensor-core kernel ran out
+    // lifetime: one reference for the owner plus one per live tensor; the
+    // context is deleted when the last reference goes
+    long refs = 1;
 
     // event profiling of launches (off by default)
     bool prof = false;

@@ -1,11 +1,222 @@
-// tcgen05 (5th-generation tensor core) TF32 Gram kernel.
+// Gram matrix G = X X^T of the rows of an FP32 matrix X (n x K, row-major,
+// K contiguous) on the 5th-generation tensor cores (tcgen05, kind::tf32,
+// FP32 accumulation in TMEM): the Gram step of the Cholesky QR passes of the
+// right-to-left TT-rounding sweep.
+//
+// One CTA computes one 128 x 128 tile (tile_i >= tile_j: lower tiles only,
+// G is symmetric) over one chunk of K (split-K) and adds it atomically into
+// G.  Warp 0 issues TMA loads of 128 x 32 FP32 boxes (128-byte swizzle) into
+// a 5-stage ring; warp 1 allocates 128 TMEM columns and issues 4 MMAs of
+// 128 x 128 x 8 per stage; warps 2-5 read the accumulator back with
+// tcgen05.ld.  Every mbarrier wait is bounded; a timeout sets *err and the
+// CTA winds down (TMEM is always freed).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace ttgb {
 
+namespace {
+
+constexpr int TB = 128;           // tile rows (= MMA M = N)
+constexpr int TK = 32;            // fp32 per 128-byte swizzled row
+constexpr int STAGES = 5;
+constexpr int TILE_BYTES = TB * TK * 4;  // 16 KB
+constexpr uint32_t TMEM_COLS = 128;
+constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of SM cycles
+
+struct __align__(8) GramSmem {
+    uint64_t full[STAGES];
+    uint64_t empty[STAGES];
+    uint64_t done;
+    uint32_t tmem_base;
+};
+
+__global__ void __launch_bounds__(192, 1)
+gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int ntiles, long kchunk_steps,
+                 float* __restrict__ G, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned operand ring, control block after it
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* ring = base;  // STAGES x (A 16 KB, B 16 KB)
+    GramSmem* ctl = reinterpret_cast<GramSmem*>(ring + STAGES * 2 * TILE_BYTES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // decode (tile_i, tile_j) with tile_i >= tile_j, and the K split
+    const int ntri = ntiles * (ntiles + 1) / 2;
+    const int pair = blockIdx.x % ntri;
+    const long split = blockIdx.x / ntri;
+    int ti = 0;
+    while ((ti + 1) * (ti + 2) / 2 <= pair) ++ti;
+    const int tj = pair - ti * (ti + 1) / 2;
+    const bool diag = (ti == tj);
+    const long ksteps_total = (K + TK - 1) / TK;
+    const long ks0 = split * kchunk_steps;
+    const long ks1 = min(ksteps_total, ks0 + kchunk_steps);
+    const int nsteps = (int)max(0L, ks1 - ks0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&ctl->full[s], 1);
+            tc::mbar_init(&ctl->empty[s], 1);
+        }
+        tc::mbar_init(&ctl->done, 1);
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&ctl->tmem_base, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0 && nsteps > 0) {
+            tc::prefetch_tmap(&tmap);
+            const uint32_t bytes = diag ? TILE_BYTES : 2 * TILE_BYTES;
+            int issued = 0;
+            for (int it = 0; it < nsteps; ++it) {
+                const int s = it % STAGES;
+                const uint32_t ph = (it / STAGES) & 1;
+                if (!tc::mbar_wait_bounded(&ctl->empty[s], ph ^ 1, WAIT_LIMIT)) { ok = false; break; }
+                unsigned char* a = ring + s * 2 * TILE_BYTES;
+                tc::mbar_arrive_expect_tx(&ctl->full[s], bytes);
+                const int kx = (int)((ks0 + it) * TK);
+                tc::tma_load_2d(a, &tmap, &ctl->full[s], kx, ti * TB);
+                if (!diag) tc::tma_load_2d(a + TILE_BYTES, &tmap, &ctl->full[s], kx, tj * TB);
+                ++issued;
+            }
+            if (!ok) {
+                atomicExch(err, 1);
+                // let the copies already issued land before the CTA can exit
+                for (int it = max(0, issued - STAGES); it < issued; ++it)
+                    tc::mbar_wait_bounded(&ctl->full[it % STAGES], (it / STAGES) & 1, WAIT_LIMIT);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && nsteps > 0) {
+            constexpr uint32_t idesc = tc::idesc_tf32(TB, TB);
+            for (int it = 0; it < nsteps; ++it) {
+                const int s = it % STAGES;
+                const uint32_t ph = (it / STAGES) & 1;
+                if (!tc::mbar_wait_bounded(&ctl->full[s], ph, WAIT_LIMIT)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t a_addr = tc::smem_u32(ring + s * 2 * TILE_BYTES);
+                const uint32_t b_addr = diag ? a_addr : a_addr + TILE_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < TK / 8; ++kk) {
+                    const uint64_t ad = tc::sdesc_kmajor_sw128(a_addr + kk * 32);
+                    const uint64_t bd = tc::sdesc_kmajor_sw128(b_addr + kk * 32);
+                    tc::mma_tf32(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                }
+                tc::mma_commit(&ctl->empty[s]);
+            }
+            if (!ok) atomicExch(err, 1);
+            tc::mma_commit(&ctl->done);
+        }
+    } else if (nsteps > 0) {
+        // epilogue warps 2..5: TMEM lane quarter = warp % 4
+        const int q = warp & 3;
+        // warp-uniform decisions: tcgen05.ld needs the whole warp converged
+        const bool got = __all_sync(0xffffffffu, tc::mbar_wait_bounded(&ctl->done, 0, 2 * WAIT_LIMIT));
+        int e = 0;
+        if (lane == 0) e = *(volatile int*)err;
+        e = __shfl_sync(0xffffffffu, e, 0);
+        if (!got) {
+            if (lane == 0) atomicExch(err, 1);
+        } else if (e == 0) {
+            tc::tc_fence_after();
+            const int row = ti * TB + q * 32 + lane;
+            float v[32];
+#pragma unroll 1
+            for (int c = 0; c < TB / 32; ++c) {
+                __syncwarp();
+                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c * 32, v);
+                if (row < n) {
+                    const int col0 = tj * TB + c * 32;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = col0 + j;
+                        if (col < n) atomicAdd(&G[(long)row * n + col], v[j]);
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
 bool gram_rows_tc_tf32(Ctx& c, int n, long K, const float* X, long ldx, float* G) {
-    (void)c; (void)n; (void)K; (void)X; (void)ldx; (void)G;
-    return false;
+    if (n <= 0 || K <= 0) return false;
+    // TMA: 16-byte aligned base, row stride a multiple of 16 bytes
+    if (((uintptr_t)X & 15) != 0 || (ldx * 4) % 16 != 0 || ldx < K) return false;
+    if (K > (1L << 31) - 64 || n > (1 << 20)) return false;
+    auto encode = get_encode();
+    if (!encode) return false;
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
+    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)TB};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)X, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+
+    const int ntiles = (n + TB - 1) / TB;
+    const int ntri = ntiles * (ntiles + 1) / 2;
+    const long ksteps = (K + TK - 1) / TK;
+    long splits = std::max<long>(1, (long)c.sm_count / ntri);
+    splits = std::min<long>(splits, std::max<long>(1, ksteps / 8));
+    const long kchunk = (ksteps + splits - 1) / splits;
+    splits = (ksteps + kchunk - 1) / kchunk;
+    const long blocks = (long)ntri * splits;
+    if (blocks > 2147483647L) return false;
+
+    const size_t smem = 1024 + STAGES * 2 * TILE_BYTES + sizeof(GramSmem) + 64;
+    static bool attr = false;
+    if (!attr) {
+        TT_CUDA(cudaFuncSetAttribute(gram_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    int* err = c.tc_err;
+    TT_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n * n, c.stream));
+    ProfScope ps(c, "gram_tf32_tc", (double)n * (n + 1) * (double)K, 4.0 * (double)n * K + 4.0 * n * n);
+    gram_tf32_kernel<<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, K, ntiles, kchunk, G, err);
+    TT_LAUNCHED(c);
+    return true;
 }
 
 }  // namespace ttgb

@@ -73,6 +73,7 @@ _SIGS = {
     "tt_round_batched": (_I, [_P, _I, _PP, _PD, _PP]),
     "tt_orthogonalize": (_I, [_P, _I, _D, _I, _I, _PP, _PP, _PD, _PI]),
     "tt_set_sign_rule": (_I, [_P, _I]),
+    "tt_gram_f32": (_I, [_P, _I, C.c_long, _P, C.c_long, _P, _I]),
     "tt_status_str": (C.c_char_p, [_I]),
     "tt_last_error": (C.c_char_p, []),
 }
@@ -296,6 +297,12 @@ def tt_orthogonalize(ctx, scheme, A, delta, policy="paper"):
                                   C.byref(nr)), "tt_orthogonalize")
     Rm = np.array(R[:]).reshape(m, m).T.copy()  # column-major -> R[j, i]
     return [TT(ctx, _P(Q[i])) for i in range(m)], Rm, nr.value
+
+
+def tt_gram_f32(ctx, n, K, x_ptr, ldx, g_ptr, use_tensor_cores=True):
+    """G = X X^T for device FP32 pointers (see include/ttgb.h)."""
+    _check(lib().tt_gram_f32(ctx.handle, n, K, _P(x_ptr), ldx, _P(g_ptr), 1 if use_tensor_cores else 0),
+           "tt_gram_f32")
 
 
 def loss_of_orthogonality(ctx, Q):

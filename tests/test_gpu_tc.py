@@ -1,0 +1,79 @@
+"""tcgen05 TF32 Gram kernel (tt_gram_f32 through the C ABI) against an FP64
+Gram of the same FP32 matrix, and against the CUDA-core FP32 kernel.
+
+TF32 keeps 10 explicit mantissa bits, so each product carries a relative
+error below 2^-9; the bound used here, 4e-3 sqrt(G_ii G_jj), is that
+worst-case product error summed coherently (|<x_i, x_j>| <= ||x_i|| ||x_j||).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+T = pytest.importorskip("paper_2211_08770_gb300.ttgb")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2211_08770_gb300 import build
+    build.build()
+    c = T.Ctx(0, "mixed_tf32")
+    yield c
+    c.close()
+
+
+def _lower_tiles_mask(n, tile):
+    i = np.arange(n)[:, None] // tile
+    j = np.arange(n)[None, :] // tile
+    return i >= j
+
+
+@pytest.mark.parametrize("n,K", [(1, 32), (7, 64), (128, 256), (130, 1000), (200, 4096), (400, 25600), (513, 96)])
+def test_tc_gram_matches_fp64(ctx, n, K):
+    g = torch.Generator(device="cpu").manual_seed(n * 7919 + K)
+    Xh = torch.randn(n, K, generator=g, dtype=torch.float32)
+    X = Xh.cuda()
+    G = torch.full((n, n), float("nan"), device="cuda", dtype=torch.float32)
+    T.tt_gram_f32(ctx, n, K, X.data_ptr(), K, G.data_ptr(), True)
+    torch.cuda.synchronize()
+    Gd = G.cpu().numpy().astype(np.float64)
+    Xd = Xh.numpy().astype(np.float64)
+    ref = Xd @ Xd.T
+    mask = _lower_tiles_mask(n, 128)
+    dg = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    err = np.abs(Gd - ref)[mask] / dg[mask]
+    assert np.all(np.isfinite(Gd[mask]))
+    assert err.max() <= 4e-3, err.max()
+    # strictly-upper tiles are left at zero
+    assert np.all(Gd[~mask] == 0.0)
+    # the CUDA-core FP32 kernel on the same input
+    G2 = torch.zeros((n, n), device="cuda", dtype=torch.float32)
+    T.tt_gram_f32(ctx, n, K, X.data_ptr(), K, G2.data_ptr(), False)
+    torch.cuda.synchronize()
+    m64 = _lower_tiles_mask(n, 64)
+    e2 = (np.abs(G2.cpu().numpy().astype(np.float64) - ref)[m64] / dg[m64]).max()
+    assert e2 <= 1e-5
+
+
+def test_tc_gram_strided_rows(ctx):
+    n, K, ld = 96, 640, 1024
+    Xh = torch.randn(n, ld, dtype=torch.float32)
+    X = Xh.cuda()
+    G = torch.zeros((n, n), device="cuda", dtype=torch.float32)
+    T.tt_gram_f32(ctx, n, K, X.data_ptr(), ld, G.data_ptr(), True)
+    torch.cuda.synchronize()
+    Xd = Xh[:, :K].numpy().astype(np.float64)
+    ref = Xd @ Xd.T
+    dg = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    low = np.tril(np.ones((n, n), dtype=bool))
+    assert (np.abs(G.cpu().numpy() - ref)[low] / dg[low]).max() <= 4e-3
+
+
+def test_tc_gram_rejects_unaligned_stride(ctx):
+    n, K = 8, 30  # 30 * 4 bytes is not a multiple of 16
+    X = torch.randn(n, K, device="cuda", dtype=torch.float32)
+    G = torch.zeros((n, n), device="cuda", dtype=torch.float32)
+    with pytest.raises(T.TTError) as e:
+        T.tt_gram_f32(ctx, n, K, X.data_ptr(), K, G.data_ptr(), True)
+    assert e.value.name == "TT_ERR_ARG"
