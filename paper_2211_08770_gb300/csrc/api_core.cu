@@ -299,6 +299,50 @@ void dot_many_impl(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* 
     for (int j = 0; j < count; ++j) out[j] = (double)h[j];
 }
 
+// FP32-stored cores, FP64 accumulation: the cores are widened to FP64 in a
+// workspace and contracted with FP64 GEMMs, so the scalars that drive the
+// orthogonalization schemes (projections, norms) carry no FP32 summation error.
+void dot_many_f32_acc64(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out) {
+    size_t wa = 1, wv = 1, xe = 0, ye = 0;
+    for (int k = 0; k < x->d; ++k) xe += x->core_elems(k);
+    for (int j = 0; j < count; ++j) {
+        size_t a, e = 0;
+        wv = std::max(wv, dot_ws_elems(x, y[j], &a));
+        wa = std::max(wa, a);
+        for (int k = 0; k < y[j]->d; ++k) e += y[j]->core_elems(k);
+        ye = std::max(ye, e);
+    }
+    const size_t bytes = sizeof(double) * (wa + wv + count + 2 + xe + ye) + 1024;
+    char* ws = (char*)ctx->alloc(bytes);
+    double* A = (double*)ws;
+    double* V = A + wa;
+    double* res = V + wv;
+    double* xc = res + count + 2;
+    double* yc = xc + xe;
+    tt_tensor xd = *x, yd;
+    size_t off = 0;
+    for (int k = 0; k < x->d; ++k) {
+        convert<float, double>(*ctx, (long)x->core_elems(k), (const float*)x->cores[k], xc + off);
+        xd.cores[k] = xc + off;
+        off += x->core_elems(k);
+    }
+    for (int j = 0; j < count; ++j) {
+        yd = *y[j];
+        off = 0;
+        for (int k = 0; k < y[j]->d; ++k) {
+            convert<float, double>(*ctx, (long)y[j]->core_elems(k), (const float*)y[j]->cores[k], yc + off);
+            yd.cores[k] = yc + off;
+            off += y[j]->core_elems(k);
+        }
+        dot_chain<double>(ctx, &xd, &yd, A, V, res + j);
+    }
+    std::vector<double> h(count);
+    TT_CUDA(cudaMemcpyAsync(h.data(), res, sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->sync();
+    ctx->release(ws, bytes);
+    for (int j = 0; j < count; ++j) out[j] = h[j];
+}
+
 void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out) {
     check_tensor(ctx, x);
     if (count < 0 || (count > 0 && (!y || !out))) throw_status(TT_ERR_ARG, "tt_dot_many: bad arguments");
@@ -308,7 +352,7 @@ void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tens
     }
     if (count == 0) return;
     if (ctx->prec == TT_FP64) dot_many_impl<double>(ctx, x, count, y, out);
-    else dot_many_impl<float>(ctx, x, count, y, out);
+    else dot_many_f32_acc64(ctx, x, count, y, out);
 }
 
 }  // namespace ttgb

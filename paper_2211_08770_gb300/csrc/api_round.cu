@@ -127,14 +127,12 @@ struct Rounder {
         {
             gram_into(rows, true, a, K, X);
             CholStatus* s0 = next_st();
-            cholesky<T, T>(*c, a, G, Lf[0], 0.0, ug_fast, s0);
+            chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 0.0, ug_fast, s0);
             CholStatus h = read_st(s0);
             if (h.ndrop == 0 && h.min_ratio >= ratio_fast) {
-                trinv<T, T>(*c, a, Lf[0], Ti[0]);
                 apply(rows, a, K, X, Ti[0]);
                 gram_into(rows, true, a, K, X);
-                cholesky<T, T>(*c, a, G, Lf[1], 0.0, 8.0 * ug_fast * sq, next_st());
-                trinv<T, T>(*c, a, Lf[1], Ti[1]);
+                chol_inv<T, T>(*c, a, G, Lf[1], Ti[1], 0.0, 8.0 * ug_fast * sq, next_st());
                 apply(rows, a, K, X, Ti[1]);
                 gemm<T>(*c, false, false, a, a, a, T(1), Lf[0], a, Lf[1], a, T(0), Lp, a);
                 o.npass = 2;
@@ -145,13 +143,11 @@ struct Rounder {
         c->stats.fallback_orth++;
         o.shifted = true;
         gram_into(rows, false, a, K, X);
-        cholesky<T, T>(*c, a, G, Lf[0], 8.0 * ug_fb * sq, 0.0, next_st());
-        trinv<T, T>(*c, a, Lf[0], Ti[0]);
+        chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 8.0 * ug_fb * sq, 0.0, next_st());
         apply(rows, a, K, X, Ti[0]);
         for (int p = 1; p <= 2; ++p) {
             gram_into(rows, false, a, K, X);
-            cholesky<T, T>(*c, a, G, Lf[p], 0.0, drop_fb, next_st());
-            trinv<T, T>(*c, a, Lf[p], Ti[p]);
+            chol_inv<T, T>(*c, a, G, Lf[p], Ti[p], 0.0, drop_fb, next_st());
             apply(rows, a, K, X, Ti[p]);
         }
         gemm<T>(*c, false, false, a, a, a, T(1), Lf[0], a, Lf[1], a, T(0), Tmp, a);
@@ -259,8 +255,7 @@ struct Rounder {
                 const T* X = core[k];
                 gram<T, T>(*c, true, m, b, X, b, G);
                 CholStatus* s = next_st();
-                cholesky<T, T>(*c, m, G, Lf[0], 0.0, 8.0 * ug_fb * sqrt((double)m), s);
-                trinv<T, T>(*c, m, Lf[0], Ti[0]);
+                chol_inv<T, T>(*c, m, G, Lf[0], Ti[0], 0.0, 8.0 * ug_fb * sqrt((double)m), s);
                 double lb = sigma_lb(m, 1);
                 CholStatus hs0 = read_st(s);
                 const double noise = 16.0 * ug_fb * sqrt((double)m) * hs0.trace;
@@ -322,11 +317,17 @@ tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_es
     R.lr_sweep(eps);
     R.check_all_status();
     tt_tensor* y = R.emit();
-    try {
-        y->norm_hint = R.core_norm(x->d - 1);
-    } catch (...) {
-        free_tensor(y);
-        throw;
+    if (sizeof(T) == 8) {
+        // FP64: cores 1..d-1 are left-orthonormal to working accuracy, so
+        // ||x~|| = ||core_d||_F.  FP32 storage leaves an orthogonality defect
+        // of order 1e-6 there; those norms are recomputed on demand with FP64
+        // accumulation (norm_internal).
+        try {
+            y->norm_hint = R.core_norm(x->d - 1);
+        } catch (...) {
+            free_tensor(y);
+            throw;
+        }
     }
     if (err_est) *err_est = nrm > 0 ? sqrt(R.err2) / nrm : 0.0;
     return y;
@@ -357,7 +358,12 @@ double norm_internal(tt_ctx* ctx, const tt_tensor* x) {
     check_tensor(ctx, x);
     if (x->norm_hint >= 0.0) return x->norm_hint;
     if (ctx->prec == TT_FP64) return norm_t<double>(ctx, x);
-    return norm_t<float>(ctx, x);
+    // FP32 storage: sqrt(<x, x>) with FP64 accumulation over the stored cores
+    double v = 0.0;
+    const tt_tensor* ys[1] = {x};
+    dot_many_internal(ctx, x, 1, ys, &v);
+    if (!isfinite(v)) throw_status(TT_ERR_NONFINITE, "NaN or Inf in the tensor");
+    return sqrt(std::max(v, 0.0));
 }
 
 }  // namespace ttgb

@@ -128,8 +128,7 @@ void gram_scheme(Driver& D, int m, const tt_tensor* const* A, std::vector<Tensor
     double* dT = dL + mm;
     CholStatus* st = (CholStatus*)(dT + mm);
     TT_CUDA(cudaMemcpyAsync(dG, G.data(), mm * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    cholesky<double, double>(*c, m, dG, dL, 0.0, 0.0, st);
-    trinv<double, double>(*c, m, dL, dT);
+    chol_inv<double, double>(*c, m, dG, dL, dT, 0.0, 0.0, st);
     std::vector<double> L(mm), T(mm);
     CholStatus hs;
     TT_CUDA(cudaMemcpyAsync(L.data(), dL, mm * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

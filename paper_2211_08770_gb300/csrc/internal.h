@@ -64,6 +64,12 @@ template <class S, class C>
 void cholesky(Ctx& c, int n, const S* G, S* L, double shift_rel, double drop_rel,
               CholStatus* st_dev);
 
+// Blocked Cholesky with rank drop and the explicit inverse of the factor in
+// one single-CTA kernel: G + shift I = L L^T, T = L^{-1} (same conventions
+// as cholesky() and trinv()).
+template <class S, class C>
+void chol_inv(Ctx& c, int n, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st_dev);
+
 // T = L^{-1} for lower-triangular L with possibly zero (dropped) columns:
 // dropped indices give zero rows and columns of T.
 template <class S, class C>
