@@ -232,6 +232,17 @@ tt_status tt_orthogonalize(tt_ctx* ctx, tt_scheme scheme, double delta,
 tt_status tt_gram_f32(tt_ctx* ctx, int n, long K, const float* X, long ldx, float* G,
                       int use_tensor_cores);
 
+/* Factorization step of the Cholesky QR passes of TT-round:
+ * G + s I = L L^T with s = shift_rel * trace(G), and T = L^{-1}.  A pivot
+ * <= drop_rel * (max_j G_jj + s) marks its row of X as numerically dependent:
+ * the column of L and the row and column of T are set to zero (*ndrop counts
+ * them; host int, may be NULL).  G, L and T are device n x n row-major
+ * matrices of the context's storage type (FP64, or FP32 for the other
+ * precisions); only the lower triangle of G is read; L and T are lower
+ * triangular on return.  Synchronizes the stream. */
+tt_status tt_cholesky_inverse(tt_ctx* ctx, int n, const void* G, void* L, void* T,
+                              double shift_rel, double drop_rel, int* ndrop);
+
 /* Householder sign rule used by subsequent TT_HOUSEHOLDER calls. */
 tt_status tt_set_sign_rule(tt_ctx* ctx, tt_sign_rule rule);
 

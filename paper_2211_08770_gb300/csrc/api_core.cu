@@ -603,6 +603,30 @@ tt_status tt_gram_f32(tt_ctx* ctx, int n, long K, const float* X, long ldx, floa
     TT_API_END
 }
 
+tt_status tt_cholesky_inverse(tt_ctx* ctx, int n, const void* G, void* L, void* T, double shift_rel,
+                              double drop_rel, int* ndrop) {
+    TT_API_BEGIN
+    if (!ctx || !G || !L || !T || n < 1 || !(shift_rel >= 0.0) || !(drop_rel >= 0.0))
+        throw_status(TT_ERR_ARG, "bad arguments");
+    CholStatus* st = (CholStatus*)ctx->alloc(sizeof(CholStatus));
+    CholStatus h;
+    try {
+        if (ctx->prec == TT_FP64)
+            chol_inv<double, double>(*ctx, n, (const double*)G, (double*)L, (double*)T, shift_rel, drop_rel, st);
+        else
+            chol_inv<float, float>(*ctx, n, (const float*)G, (float*)L, (float*)T, shift_rel, drop_rel, st);
+        TT_CUDA(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+        ctx->sync();
+    } catch (...) {
+        ctx->release(st, sizeof(CholStatus));
+        throw;
+    }
+    ctx->release(st, sizeof(CholStatus));
+    if (h.nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in G");
+    if (ndrop) *ndrop = h.ndrop;
+    TT_API_END
+}
+
 const char* tt_status_str(tt_status s) {
     switch (s) {
         case TT_OK: return "TT_OK";

@@ -127,7 +127,10 @@ struct Rounder {
         {
             gram_into(rows, true, a, K, X);
             CholStatus* s0 = next_st();
-            chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 0.0, ug_fast, s0);
+            // drop only numerically-zero pivots here; health is judged by
+            // pivot / own diagonal, which Cholesky QR is invariant to
+            // (column or row scaling does not change it)
+            chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 0.0, drop_fb, s0);
             CholStatus h = read_st(s0);
             if (h.ndrop == 0 && h.min_ratio >= ratio_fast) {
                 apply(rows, a, K, X, Ti[0]);

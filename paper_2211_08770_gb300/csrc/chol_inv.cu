@@ -165,19 +165,29 @@ chol_inv_kernel(int n, const S* __restrict__ G, S* __restrict__ L, S* __restrict
             while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
             const int kk = t - ii * (ii + 1) / 2;
             const int I0 = (p + 1 + ii) * 32, K0 = (p + 1 + kk) * 32;
-            for (int j = 0; j < 32; ++j) {
-                W.Ks[j][lane] = (K0 + j < n && lane < jb) ? (C)L[(long)(K0 + j) * n + j0 + lane] : C(0);
-                W.Is[j][lane] = (I0 + j < n && lane < jb) ? (C)L[(long)(I0 + j) * n + j0 + lane] : C(0);
+            {
+                // Ks[k][j] = L[K0+j][j0+k] (lane j reads its row), Is[i][k] = L[I0+i][j0+k]
+                C kv[32], iv[32];
+                const bool kr = (K0 + lane < n);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) kv[k] = (kr && k < jb) ? (C)L[(long)(K0 + lane) * n + j0 + k] : C(0);
+#pragma unroll
+                for (int r = 0; r < 32; ++r)
+                    iv[r] = (I0 + r < n && lane < jb) ? (C)L[(long)(I0 + r) * n + j0 + lane] : C(0);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) W.Ks[k][lane] = kv[k];
+#pragma unroll
+                for (int r = 0; r < 32; ++r) W.Is[r][lane] = iv[r];
             }
             __syncwarp();
             C acc[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) acc[j] = C(0);
-#pragma unroll 4
+#pragma unroll 2
             for (int k = 0; k < 32; ++k) {
                 const C a = W.Is[lane][k];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc[j] = fma(a, W.Ks[j][k], acc[j]);
+                for (int j = 0; j < 32; ++j) acc[j] = fma(a, W.Ks[k][j], acc[j]);
             }
             const int row = I0 + lane;
             if (row < n) {
@@ -206,12 +216,21 @@ chol_inv_kernel(int n, const S* __restrict__ G, S* __restrict__ L, S* __restrict
             for (int K = J; K < I; ++K) {
                 const int K0 = K * 32;
                 // Ks[k][j] = T[K0+k][J0+j]; Is[i][k] = L[I0+i][K0+k]
-                for (int r = 0; r < 32; ++r) {
-                    W.Ks[r][lane] = (K0 + r < n && J0 + lane < n) ? (C)Tm[(long)(K0 + r) * n + J0 + lane] : C(0);
-                    W.Is[r][lane] = (I0 + r < n && K0 + lane < n) ? (C)L[(long)(I0 + r) * n + K0 + lane] : C(0);
+                {
+                    C kv[32], iv[32];
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) {
+                        kv[r] = (K0 + r < n && J0 + lane < n) ? (C)Tm[(long)(K0 + r) * n + J0 + lane] : C(0);
+                        iv[r] = (I0 + r < n && K0 + lane < n) ? (C)L[(long)(I0 + r) * n + K0 + lane] : C(0);
+                    }
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) {
+                        W.Ks[r][lane] = kv[r];
+                        W.Is[r][lane] = iv[r];
+                    }
                 }
                 __syncwarp();
-#pragma unroll 4
+#pragma unroll 2
                 for (int k = 0; k < 32; ++k) {
                     const C a = W.Is[lane][k];
 #pragma unroll

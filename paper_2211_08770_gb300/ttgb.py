@@ -74,6 +74,7 @@ _SIGS = {
     "tt_orthogonalize": (_I, [_P, _I, _D, _I, _I, _PP, _PP, _PD, _PI]),
     "tt_set_sign_rule": (_I, [_P, _I]),
     "tt_gram_f32": (_I, [_P, _I, C.c_long, _P, C.c_long, _P, _I]),
+    "tt_cholesky_inverse": (_I, [_P, _I, _P, _P, _P, _D, _D, _PI]),
     "tt_status_str": (C.c_char_p, [_I]),
     "tt_last_error": (C.c_char_p, []),
 }
@@ -303,6 +304,15 @@ def tt_gram_f32(ctx, n, K, x_ptr, ldx, g_ptr, use_tensor_cores=True):
     """G = X X^T for device FP32 pointers (see include/ttgb.h)."""
     _check(lib().tt_gram_f32(ctx.handle, n, K, _P(x_ptr), ldx, _P(g_ptr), 1 if use_tensor_cores else 0),
            "tt_gram_f32")
+
+
+def tt_cholesky_inverse(ctx, n, g_ptr, l_ptr, t_ptr, shift_rel=0.0, drop_rel=0.0):
+    """G + s I = L L^T, T = L^{-1} on device pointers (see include/ttgb.h);
+    returns the number of dropped pivots."""
+    nd = C.c_int()
+    _check(lib().tt_cholesky_inverse(ctx.handle, n, _P(g_ptr), _P(l_ptr), _P(t_ptr), float(shift_rel),
+                                     float(drop_rel), C.byref(nd)), "tt_cholesky_inverse")
+    return nd.value
 
 
 def loss_of_orthogonality(ctx, Q):

@@ -77,3 +77,56 @@ def test_tc_gram_rejects_unaligned_stride(ctx):
     with pytest.raises(T.TTError) as e:
         T.tt_gram_f32(ctx, n, K, X.data_ptr(), K, G.data_ptr(), True)
     assert e.value.name == "TT_ERR_ARG"
+
+
+def _spd(n, seed, kappa=1e2, dtype=np.float64):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.logspace(0, -np.log10(kappa), n)
+    return ((Q * ev) @ Q.T).astype(dtype)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_tf32"])
+@pytest.mark.parametrize("n", [1, 5, 31, 32, 33, 100, 257, 400])
+def test_cholesky_inverse_blocked(prec, n):
+    from paper_2211_08770_gb300 import build
+    build.build()
+    c = T.Ctx(0, prec)
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    G = _spd(n, n, 1e2)
+    Gd = torch.tensor(G, dtype=tdt, device="cuda")
+    L = torch.empty_like(Gd)
+    Ti = torch.empty_like(Gd)
+    nd = T.tt_cholesky_inverse(c, n, Gd.data_ptr(), L.data_ptr(), Ti.data_ptr())
+    assert nd == 0
+    Lh = L.cpu().numpy().astype(np.float64)
+    Th = Ti.cpu().numpy().astype(np.float64)
+    tol = 1e-13 if prec == "fp64" else 2e-5
+    assert np.allclose(np.triu(Lh, 1), 0) and np.allclose(np.triu(Th, 1), 0)
+    assert np.linalg.norm(Lh @ Lh.T - G) <= tol * np.linalg.norm(G) * np.sqrt(n)
+    assert np.linalg.norm(Th @ Lh - np.eye(n)) <= tol * 100 * np.sqrt(n)
+    c.close()
+
+
+def test_cholesky_inverse_drops_dependent_rows():
+    from paper_2211_08770_gb300 import build
+    build.build()
+    c = T.Ctx(0, "fp64")
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((70, 200))
+    X[40] = X[3] - 2 * X[7]          # exactly dependent rows
+    X[65] = X[10]
+    G = X @ X.T
+    Gd = torch.tensor(G, device="cuda")
+    L = torch.empty_like(Gd)
+    Ti = torch.empty_like(Gd)
+    nd = T.tt_cholesky_inverse(c, 70, Gd.data_ptr(), L.data_ptr(), Ti.data_ptr(), 0.0, 1e-12)
+    assert nd == 2
+    Lh, Th = L.cpu().numpy(), Ti.cpu().numpy()
+    assert np.all(Lh[:, 40] == 0) and np.all(Lh[:, 65] == 0)
+    assert np.all(Th[40] == 0) and np.all(Th[:, 65] == 0)
+    assert np.linalg.norm(Lh @ Lh.T - G) <= 1e-12 * np.linalg.norm(G)
+    keep = [i for i in range(70) if i not in (40, 65)]
+    Q = Th[keep] @ X
+    assert np.allclose(Q @ Q.T, np.eye(68), atol=1e-10)
+    c.close()
