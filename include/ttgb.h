@@ -232,6 +232,17 @@ tt_status tt_orthogonalize(tt_ctx* ctx, tt_scheme scheme, double delta,
 tt_status tt_gram_f32(tt_ctx* ctx, int n, long K, const float* X, long ldx, float* G,
                       int use_tensor_cores);
 
+/* Core-producing product of TT-round (apply Q = L^{-1} X, absorb
+ * core <- core L): C = A op(B) for device FP32 matrices, A M x K row-major
+ * (lda), op(B) = B^T with B N x K row-major when trans_b != 0, else B (K x N
+ * row-major, ldb); C M x N row-major (ldc), overwritten.  use_tensor_cores
+ * != 0 selects the tcgen05 split-TF32 kernel (A_hi B_hi + A_hi B_lo +
+ * A_lo B_hi, FP32 accumulation), else the CUDA-core FP32 kernel.  TT_ERR_ARG
+ * when the tensor-core kernel cannot take the layout (a pointer or leading
+ * dimension not 16-byte aligned). */
+tt_status tt_gemm_f32(tt_ctx* ctx, int trans_b, int M, int N, int K, const float* A, long lda,
+                      const float* B, long ldb, float* C, long ldc, int use_tensor_cores);
+
 /* Factorization step of the Cholesky QR passes of TT-round:
  * G + s I = L L^T with s = shift_rel * trace(G), and T = L^{-1}.  A pivot
  * <= drop_rel * (max_j G_jj + s) marks its row of X as numerically dependent:

@@ -383,6 +383,9 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     // TTGB_NO_TENSOR_CORES=1 keeps TT_MIXED_TF32 contexts on the CUDA-core Gram
     const char* no_tc = getenv("TTGB_NO_TENSOR_CORES");
     if (no_tc && no_tc[0] == '1') c->use_tc = false;
+    // TTGB_NO_TC_GEMM=1 keeps only the core-producing GEMMs on CUDA cores
+    const char* no_tg = getenv("TTGB_NO_TC_GEMM");
+    if (no_tg && no_tg[0] == '1') c->use_tc_gemm = false;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
@@ -598,6 +601,21 @@ tt_status tt_gram_f32(tt_ctx* ctx, int n, long K, const float* X, long ldx, floa
         check_tc_error(*ctx);
     } else {
         gram<float, float>(*ctx, true, n, K, X, ldx, G);
+        ctx->sync();
+    }
+    TT_API_END
+}
+
+tt_status tt_gemm_f32(tt_ctx* ctx, int trans_b, int M, int N, int K, const float* A, long lda, const float* B,
+                      long ldb, float* C, long ldc, int use_tensor_cores) {
+    TT_API_BEGIN
+    if (!ctx || !A || !B || !C || M < 1 || N < 1 || K < 1) throw_status(TT_ERR_ARG, "bad arguments");
+    if (use_tensor_cores) {
+        if (!gemm_tc3_tf32(*ctx, trans_b != 0, M, N, K, A, lda, B, ldb, C, ldc))
+            throw_status(TT_ERR_ARG, "layout not supported by the tensor-core kernel");
+        check_tc_error(*ctx);
+    } else {
+        gemm<float>(*ctx, false, trans_b != 0, M, N, K, 1.0f, A, lda, B, ldb, 0.0f, C, ldc);
         ctx->sync();
     }
     TT_API_END

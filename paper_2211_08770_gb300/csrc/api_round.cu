@@ -103,10 +103,21 @@ struct Rounder {
         gram<T, T>(*c, rows, a, K, X, rows ? K : a, G);
     }
 
+    // C = op(A) op(B): tensor-core split TF32 when the context allows it and
+    // the layout is TMA-aligned, else the CUDA-core kernel of the storage type
+    void mm(bool tA, bool tB, int M, int N, int K, const T* A, long lda, const T* B, long ldb, T* C, long ldc) {
+        if constexpr (sizeof(T) == 4) {
+            if (tc && c->use_tc_gemm && !tA &&
+                gemm_tc3_tf32(*c, tB, M, N, K, (const float*)A, lda, (const float*)B, ldb, (float*)C, ldc))
+                return;
+        }
+        gemm<T>(*c, tA, tB, M, N, K, T(1), A, lda, B, ldb, T(0), C, ldc);
+    }
+
     // X <- Ti X (rows) or X Ti^T (cols)
     void apply(bool rows, int a, long K, T*& X, const T* Tinv) {
-        if (rows) gemm<T>(*c, false, false, a, (int)K, a, T(1), Tinv, a, X, K, T(0), spare, K);
-        else gemm<T>(*c, false, true, (int)K, a, a, T(1), X, a, Tinv, a, T(0), spare, a);
+        if (rows) mm(false, false, a, (int)K, a, Tinv, a, X, K, spare, K);
+        else mm(false, true, (int)K, a, a, X, a, Tinv, a, spare, a);
         std::swap(X, spare);
     }
 
@@ -137,7 +148,7 @@ struct Rounder {
                 gram_into(rows, true, a, K, X);
                 chol_inv<T, T>(*c, a, G, Lf[1], Ti[1], 0.0, 8.0 * ug_fast * sq, next_st());
                 apply(rows, a, K, X, Ti[1]);
-                gemm<T>(*c, false, false, a, a, a, T(1), Lf[0], a, Lf[1], a, T(0), Lp, a);
+                mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Lp, a);
                 o.npass = 2;
                 return o;
             }
@@ -153,8 +164,8 @@ struct Rounder {
             chol_inv<T, T>(*c, a, G, Lf[p], Ti[p], 0.0, drop_fb, next_st());
             apply(rows, a, K, X, Ti[p]);
         }
-        gemm<T>(*c, false, false, a, a, a, T(1), Lf[0], a, Lf[1], a, T(0), Tmp, a);
-        gemm<T>(*c, false, false, a, a, a, T(1), Tmp, a, Lf[2], a, T(0), Lp, a);
+        mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Tmp, a);
+        mm(false, false, a, a, a, Tmp, a, Lf[2], a, Lp, a);
         o.npass = 3;
         return o;
     }
@@ -203,13 +214,13 @@ struct Rounder {
             const int M = r[k - 1] * n[k - 1];
             if (K <= a) {
                 // rank cap: X = I_K X, absorb X itself
-                gemm<T>(*c, false, false, M, (int)K, a, T(1), core[k - 1], a, core[k], K, T(0), spare, K);
+                mm(false, false, M, (int)K, a, core[k - 1], a, core[k], K, spare, K);
                 std::swap(core[k - 1], spare);
                 fill_identity<T>(*c, (int)K, core[k], K);
                 r[k] = (int)K;
             } else {
                 orth(true, a, K, core[k]);
-                gemm<T>(*c, false, false, M, a, a, T(1), core[k - 1], a, Lp, a, T(0), spare, a);
+                mm(false, false, M, a, a, core[k - 1], a, Lp, a, spare, a);
                 std::swap(core[k - 1], spare);
             }
         }
@@ -235,7 +246,8 @@ struct Rounder {
                 if (lb > 2.0 * eps && lb > 0.0) {
                     c->stats.certified_bonds++;
                     // core_{k+1} <- R core_{k+1}, R = Lp^T
-                    gemm<T>(*c, true, false, b, (int)NR, b, T(1), Lp, b, core[k + 1], NR, T(0), spare, NR);
+                    transpose<T>(*c, b, b, Lp, Tmp);
+                    mm(false, false, b, (int)NR, b, Tmp, b, core[k + 1], NR, spare, NR);
                     std::swap(core[k + 1], spare);
                     continue;
                 }
@@ -247,9 +259,9 @@ struct Rounder {
                 TT_CUDA(cudaMemcpyAsync(hs.data(), sig, b * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
                 c->sync();
                 const int rp = trunc_rank(hs, eps);
-                gemm<T>(*c, false, false, m, rp, b, T(1), core[k], b, Ub, b, T(0), spare, rp);
+                mm(false, false, m, rp, b, core[k], b, Ub, b, spare, rp);
                 std::swap(core[k], spare);
-                gemm<T>(*c, false, false, rp, (int)NR, b, T(1), SVt, b, core[k + 1], NR, T(0), spare, NR);
+                mm(false, false, rp, (int)NR, b, SVt, b, core[k + 1], NR, spare, NR);
                 std::swap(core[k + 1], spare);
                 r[k + 1] = rp;
             } else {
@@ -265,7 +277,7 @@ struct Rounder {
                 const double lb2 = lb * lb - noise;
                 if (lb > 0.0 && lb2 > 4.0 * eps * eps) {
                     c->stats.certified_bonds++;
-                    gemm<T>(*c, false, false, m, (int)NR, b, T(1), X, b, core[k + 1], NR, T(0), spare, NR);
+                    mm(false, false, m, (int)NR, b, X, b, core[k + 1], NR, spare, NR);
                     std::swap(core[k + 1], spare);
                     fill_identity<T>(*c, m, core[k], m);
                     r[k + 1] = m;
@@ -280,7 +292,7 @@ struct Rounder {
                 // core_k <- U[:, :rp] (m x rp)
                 TT_CUDA(cudaMemcpy2DAsync(core[k], rp * sizeof(T), Ub, m * sizeof(T), rp * sizeof(T), m,
                                           cudaMemcpyDeviceToDevice, c->stream));
-                gemm<T>(*c, false, false, rp, (int)NR, b, T(1), SVt, b, core[k + 1], NR, T(0), spare, NR);
+                mm(false, false, rp, (int)NR, b, SVt, b, core[k + 1], NR, spare, NR);
                 std::swap(core[k + 1], spare);
                 r[k + 1] = rp;
             }

@@ -123,6 +123,12 @@ void axpy(Ctx& c, long n, double alpha, const T* x, T* y);  // y += alpha x
 // tiles), split-K, FP32 accumulation in TMEM, atomically added into G (FP32,
 // zeroed first).  Returns false when the shape is not supported.
 bool gram_rows_tc_tf32(Ctx& c, int n, long K, const float* X, long ldx, float* G);
+// C (M x N, row-major, ldc) = A (M x K, row-major) op(B), op(B) = B^T with B
+// N x K row-major when bT, else B (K x N row-major); split-TF32 on tcgen05
+// (3 MMAs per k-step, FP32 accumulation).  Returns false (nothing launched)
+// when a pointer or leading dimension is not 16-byte aligned.
+bool gemm_tc3_tf32(Ctx& c, bool bT, int M, int N, int K, const float* A, long lda, const float* B, long ldb,
+                   float* C, long ldc);
 // reads (and clears) the tensor-core timeout flag; throws TT_ERR_TIMEOUT if set
 void check_tc_error(Ctx& c);
 
@@ -141,7 +147,8 @@ struct Ctx {
     tt_stats stats{};
     tt_sign_rule sign_rule = TT_SIGN_STABLE;
     int sm_count = 0;
-    bool use_tc = true;  // tensor-core Gram in TT_MIXED_TF32
+    bool use_tc = true;       // tensor-core Gram in TT_MIXED_TF32
+    bool use_tc_gemm = true;  // tensor-core split-TF32 apply / absorb GEMMs in TT_MIXED_TF32
     int* tc_err = nullptr;  // device flag: a bounded wait of a tensor-core kernel ran out
     // lifetime: one reference for the owner plus one per live tensor; the
     // context is deleted when the last reference goes

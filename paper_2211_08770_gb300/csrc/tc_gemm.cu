@@ -1,0 +1,304 @@
+// Split-TF32 GEMM on the 5th-generation tensor cores: C = A op(B) with FP32
+// operands, each split into round-to-nearest TF32 parts x = x_hi + x_lo and
+// multiplied as A_hi B_hi + A_hi B_lo + A_lo B_hi (kind::tf32, FP32
+// accumulation in TMEM).  These are the GEMMs of TT-round that produce core
+// values (apply Q = L^{-1} X and absorb core <- core L), where plain TF32
+// (10-bit mantissa) would perturb the represented tensor by ~1e-3.
+//
+// A is M x K row-major (K contiguous).  B is either N x K row-major
+// ("T": C = A B^T) or K x N row-major ("N": C = A B, N contiguous).  One CTA
+// computes a 128 x 128 tile of C: warp 0 streams raw FP32 tiles with TMA into
+// a 2-deep staging ring; warps 2-5 split them into TF32 hi/lo parts written
+// in the 128-byte-swizzled K-major layout the MMA reads (transposing B when it
+// is N-major) into a 2-deep operand ring; warp 1 issues the MMAs; warps 2-5
+// then read the accumulator from TMEM and store C.  Every wait is bounded.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace ttgb {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 32;
+constexpr int TILE = BM * BK * 4;  // 16 KB, one operand tile
+constexpr int NSTG = 2, NOP = 2;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr long long WAIT_LIMIT = 4000000000LL;
+
+struct __align__(8) GemmCtl {
+    uint64_t stg_full[NSTG], stg_empty[NSTG];
+    uint64_t op_full[NOP], op_empty[NOP];
+    uint64_t done;
+    uint32_t tmem_base;
+};
+
+__device__ __forceinline__ uint32_t rna_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void split4(const float4 v, float4& hi, float4& lo) {
+    const float h0 = __uint_as_float(rna_tf32(v.x)), h1 = __uint_as_float(rna_tf32(v.y));
+    const float h2 = __uint_as_float(rna_tf32(v.z)), h3 = __uint_as_float(rna_tf32(v.w));
+    hi = make_float4(h0, h1, h2, h3);
+    lo = make_float4(__uint_as_float(rna_tf32(v.x - h0)), __uint_as_float(rna_tf32(v.y - h1)),
+                     __uint_as_float(rna_tf32(v.z - h2)), __uint_as_float(rna_tf32(v.w - h3)));
+}
+
+// byte offset of the 16-byte chunk c4 of row r in a 128-byte-swizzled tile
+__device__ __forceinline__ int sw128(int r, int c4) { return r * 128 + ((c4 ^ (r & 7)) << 4); }
+
+template <bool BT>
+__global__ void __launch_bounds__(192, 1)
+gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
+                  int K, float* __restrict__ Cm, long ldc, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // operand ring first (1024-aligned tiles): [NOP][A_hi, A_lo, B_hi, B_lo]
+    unsigned char* opr = base;
+    unsigned char* stg = opr + NOP * 4 * TILE;  // [NSTG][A raw, B raw]
+    GemmCtl* ctl = reinterpret_cast<GemmCtl*>(stg + NSTG * 2 * TILE);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nk = (K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTG; ++s) {
+            tc::mbar_init(&ctl->stg_full[s], 1);
+            tc::mbar_init(&ctl->stg_empty[s], 4);
+        }
+        for (int s = 0; s < NOP; ++s) {
+            tc::mbar_init(&ctl->op_full[s], 4);
+            tc::mbar_init(&ctl->op_empty[s], 1);
+        }
+        tc::mbar_init(&ctl->done, 1);
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&ctl->tmem_base, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tc::prefetch_tmap(&mapA);
+            tc::prefetch_tmap(&mapB);
+            bool ok = true;
+            int issued = 0;
+            for (int it = 0; it < nk; ++it) {
+                const int s = it % NSTG;
+                if (!tc::mbar_wait_bounded(&ctl->stg_empty[s], ((it / NSTG) & 1) ^ 1, WAIT_LIMIT)) { ok = false; break; }
+                unsigned char* a = stg + s * 2 * TILE;
+                tc::mbar_arrive_expect_tx(&ctl->stg_full[s], 2 * TILE);
+                tc::tma_load_2d(a, &mapA, &ctl->stg_full[s], it * BK, m0);
+                if (BT) tc::tma_load_2d(a + TILE, &mapB, &ctl->stg_full[s], it * BK, n0);
+                else tc::tma_load_2d(a + TILE, &mapB, &ctl->stg_full[s], n0, it * BK);
+                ++issued;
+            }
+            if (!ok) {
+                atomicExch(err, 1);
+                for (int it = max(0, issued - NSTG); it < issued; ++it)
+                    tc::mbar_wait_bounded(&ctl->stg_full[it % NSTG], (it / NSTG) & 1, WAIT_LIMIT);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_tf32(BM, BN);
+            bool ok = true;
+            for (int it = 0; it < nk; ++it) {
+                const int o = it % NOP;
+                if (!tc::mbar_wait_bounded(&ctl->op_full[o], (it / NOP) & 1, WAIT_LIMIT)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t ahi = tc::smem_u32(opr + o * 4 * TILE);
+                const uint32_t alo = ahi + TILE, bhi = ahi + 2 * TILE, blo = ahi + 3 * TILE;
+#pragma unroll
+                for (int kk = 0; kk < BK / 8; ++kk) {
+                    const uint32_t off = kk * 32;
+                    const uint32_t acc0 = (it > 0 || kk > 0) ? 1u : 0u;
+                    tc::mma_tf32(tmem, tc::sdesc_kmajor_sw128(ahi + off), tc::sdesc_kmajor_sw128(bhi + off), idesc, acc0);
+                    tc::mma_tf32(tmem, tc::sdesc_kmajor_sw128(ahi + off), tc::sdesc_kmajor_sw128(blo + off), idesc, 1u);
+                    tc::mma_tf32(tmem, tc::sdesc_kmajor_sw128(alo + off), tc::sdesc_kmajor_sw128(bhi + off), idesc, 1u);
+                }
+                tc::mma_commit(&ctl->op_empty[o]);
+            }
+            if (!ok) atomicExch(err, 1);
+            tc::mma_commit(&ctl->done);
+        }
+    } else {
+        // converters (warps 2..5, 128 threads), then the epilogue
+        const int t = threadIdx.x - 64;
+        bool ok = true;
+        for (int it = 0; it < nk && ok; ++it) {
+            const int s = it % NSTG, o = it % NOP;
+            const bool g1 = tc::mbar_wait_bounded(&ctl->stg_full[s], (it / NSTG) & 1, WAIT_LIMIT);
+            const bool g2 = g1 && tc::mbar_wait_bounded(&ctl->op_empty[o], ((it / NOP) & 1) ^ 1, WAIT_LIMIT);
+            ok = __all_sync(0xffffffffu, g1 && g2);
+            if (!ok) break;
+            const unsigned char* sa = stg + s * 2 * TILE;
+            const unsigned char* sb = sa + TILE;
+            unsigned char* ahi = opr + o * 4 * TILE;
+            unsigned char* alo = ahi + TILE;
+            unsigned char* bhi = ahi + 2 * TILE;
+            unsigned char* blo = ahi + 3 * TILE;
+            // A (and B when K-major): staging [128 rows][32 k], 8 chunks of 4 per row
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int idx = q * 128 + t;
+                const int r = idx >> 3, c4 = idx & 7;
+                float4 v = *reinterpret_cast<const float4*>(sa + r * 128 + c4 * 16);
+                float4 h, l;
+                split4(v, h, l);
+                *reinterpret_cast<float4*>(ahi + sw128(r, c4)) = h;
+                *reinterpret_cast<float4*>(alo + sw128(r, c4)) = l;
+                if (BT) {
+                    v = *reinterpret_cast<const float4*>(sb + r * 128 + c4 * 16);
+                    split4(v, h, l);
+                    *reinterpret_cast<float4*>(bhi + sw128(r, c4)) = h;
+                    *reinterpret_cast<float4*>(blo + sw128(r, c4)) = l;
+                }
+            }
+            if (!BT) {
+                // B N-major: staging [32 k][128 n]; operand row n holds k = 0..31
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int idx = q * 128 + t;
+                    const int nn = idx & 127, c4 = idx >> 7;
+                    const float* col = reinterpret_cast<const float*>(sb) + (c4 * 4) * BN + nn;
+                    float4 v = make_float4(col[0], col[BN], col[2 * BN], col[3 * BN]);
+                    float4 h, l;
+                    split4(v, h, l);
+                    *reinterpret_cast<float4*>(bhi + sw128(nn, c4)) = h;
+                    *reinterpret_cast<float4*>(blo + sw128(nn, c4)) = l;
+                }
+            }
+            fence_proxy_async();  // generic-proxy writes -> visible to tcgen05.mma
+            __syncwarp();
+            if (lane == 0) {
+                tc::mbar_arrive(&ctl->op_full[o]);
+                tc::mbar_arrive(&ctl->stg_empty[s]);
+            }
+        }
+        if (!ok && lane == 0) atomicExch(err, 1);
+        // epilogue: TMEM lanes of this warp's quarter
+        const int q = warp & 3;
+        const bool got = __all_sync(0xffffffffu, ok && tc::mbar_wait_bounded(&ctl->done, 0, 2 * WAIT_LIMIT));
+        int e = 0;
+        if (lane == 0) e = *(volatile int*)err;
+        e = __shfl_sync(0xffffffffu, e, 0);
+        if (!got) {
+            if (lane == 0) atomicExch(err, 1);
+        } else if (e == 0) {
+            tc::tc_fence_after();
+            const int row = m0 + q * 32 + lane;
+            float v[32];
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                __syncwarp();
+                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c * 32, v);
+                const int col0 = n0 + c * 32;
+                if (row < M) {
+                    float* dst = Cm + (long)row * ldc + col0;
+                    if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (col0 + j < N) dst[j] = v[j];
+                    }
+                }
+            }
+        }
+    }
+    // the MMA issuer makes sure its MMAs have finished before TMEM is freed
+    if (warp == 1 && lane == 0) tc::mbar_wait_bounded(&ctl->done, 0, WAIT_LIMIT);
+    __syncwarp();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap* map, const float* ptr, long inner, long outer, long ld, int box_inner, int box_outer) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool gemm_tc3_tf32(Ctx& c, bool bT, int M, int N, int K, const float* A, long lda, const float* B, long ldb,
+                   float* C, long ldc) {
+    if (M <= 0 || N <= 0 || K <= 0) return false;
+    auto aligned = [](const void* p, long ld) { return ((uintptr_t)p & 15) == 0 && (ld * 4) % 16 == 0; };
+    if (!aligned(A, lda) || !aligned(B, ldb)) return false;
+    if (lda < K || (bT ? ldb < K : ldb < N) || ldc < N) return false;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, K, M, lda, BK, BM)) return false;
+    if (bT) {
+        if (!make_map(&mb, B, K, N, ldb, BK, BN)) return false;
+    } else {
+        if (!make_map(&mb, B, N, K, ldb, BN, BK)) return false;
+    }
+    const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    if (grid.y > 65535) return false;
+    const size_t smem = 1024 + NOP * 4 * TILE + NSTG * 2 * TILE + sizeof(GemmCtl) + 64;
+    static bool attr[2] = {false, false};
+    if (!attr[bT]) {
+        if (bT)
+            TT_CUDA(cudaFuncSetAttribute(gemm3_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else
+            TT_CUDA(cudaFuncSetAttribute(gemm3_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr[bT] = true;
+    }
+    ProfScope ps(c, "gemm_tf32x3_tc", 2.0 * M * (double)N * K, 4.0 * ((double)M * K + (double)K * N + (double)M * N));
+    if (bT)
+        gemm3_tf32_kernel<true><<<grid, 192, smem, c.stream>>>(ma, mb, M, N, K, C, ldc, c.tc_err);
+    else
+        gemm3_tf32_kernel<false><<<grid, 192, smem, c.stream>>>(ma, mb, M, N, K, C, ldc, c.tc_err);
+    TT_LAUNCHED(c);
+    return true;
+}
+
+}  // namespace ttgb

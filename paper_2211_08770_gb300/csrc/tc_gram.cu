@@ -152,6 +152,8 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int nt
             }
         }
     }
+    // the MMA issuer makes sure its MMAs have finished before TMEM is freed
+    if (warp == 1 && lane == 0 && nsteps > 0) tc::mbar_wait_bounded(&ctl->done, 0, WAIT_LIMIT);
     __syncwarp();
     tc::tc_fence_before();
     __syncthreads();

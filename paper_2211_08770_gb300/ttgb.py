@@ -75,6 +75,7 @@ _SIGS = {
     "tt_set_sign_rule": (_I, [_P, _I]),
     "tt_gram_f32": (_I, [_P, _I, C.c_long, _P, C.c_long, _P, _I]),
     "tt_cholesky_inverse": (_I, [_P, _I, _P, _P, _P, _D, _D, _PI]),
+    "tt_gemm_f32": (_I, [_P, _I, _I, _I, _I, _P, C.c_long, _P, C.c_long, _P, C.c_long, _I]),
     "tt_status_str": (C.c_char_p, [_I]),
     "tt_last_error": (C.c_char_p, []),
 }
@@ -304,6 +305,12 @@ def tt_gram_f32(ctx, n, K, x_ptr, ldx, g_ptr, use_tensor_cores=True):
     """G = X X^T for device FP32 pointers (see include/ttgb.h)."""
     _check(lib().tt_gram_f32(ctx.handle, n, K, _P(x_ptr), ldx, _P(g_ptr), 1 if use_tensor_cores else 0),
            "tt_gram_f32")
+
+
+def tt_gemm_f32(ctx, trans_b, M, N, K, a_ptr, lda, b_ptr, ldb, c_ptr, ldc, use_tensor_cores=True):
+    """C = A op(B) on device FP32 pointers (see include/ttgb.h)."""
+    _check(lib().tt_gemm_f32(ctx.handle, 1 if trans_b else 0, M, N, K, _P(a_ptr), lda, _P(b_ptr), ldb, _P(c_ptr),
+                             ldc, 1 if use_tensor_cores else 0), "tt_gemm_f32")
 
 
 def tt_cholesky_inverse(ctx, n, g_ptr, l_ptr, t_ptr, shift_rel=0.0, drop_rel=0.0):
