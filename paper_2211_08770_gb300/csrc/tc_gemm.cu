@@ -78,10 +78,10 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTG; ++s) {
             tc::mbar_init(&ctl->stg_full[s], 1);
-            tc::mbar_init(&ctl->stg_empty[s], 4);
+            tc::mbar_init(&ctl->stg_empty[s], 128);
         }
         for (int s = 0; s < NOP; ++s) {
-            tc::mbar_init(&ctl->op_full[s], 4);
+            tc::mbar_init(&ctl->op_full[s], 128);
             tc::mbar_init(&ctl->op_empty[s], 1);
         }
         tc::mbar_init(&ctl->done, 1);
@@ -188,12 +188,11 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                     *reinterpret_cast<float4*>(blo + sw128(nn, c4)) = l;
                 }
             }
-            fence_proxy_async();  // generic-proxy writes -> visible to tcgen05.mma
-            __syncwarp();
-            if (lane == 0) {
-                tc::mbar_arrive(&ctl->op_full[o]);
-                tc::mbar_arrive(&ctl->stg_empty[s]);
-            }
+            // every converter thread makes its own generic-proxy writes visible
+            // to the async proxy (tcgen05.mma) and arrives itself
+            fence_proxy_async();
+            tc::mbar_arrive(&ctl->op_full[o]);
+            tc::mbar_arrive(&ctl->stg_empty[s]);
         }
         if (!ok && lane == 0) atomicExch(err, 1);
         // epilogue: TMEM lanes of this warp's quarter
