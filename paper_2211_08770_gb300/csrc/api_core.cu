@@ -383,9 +383,11 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     // TTGB_NO_TENSOR_CORES=1 keeps TT_MIXED_TF32 contexts on the CUDA-core Gram
     const char* no_tc = getenv("TTGB_NO_TENSOR_CORES");
     if (no_tc && no_tc[0] == '1') c->use_tc = false;
-    // TTGB_NO_TC_GEMM=1 keeps only the core-producing GEMMs on CUDA cores
-    const char* no_tg = getenv("TTGB_NO_TC_GEMM");
-    if (no_tg && no_tg[0] == '1') c->use_tc_gemm = false;
+    // TTGB_TC_GEMM=1 moves the core-producing GEMMs to the split-TF32
+    // tensor-core kernel (three products; its chained error exceeds the
+    // FP32 CUDA-core kernel's, so it is opt-in)
+    const char* tg = getenv("TTGB_TC_GEMM");
+    if (tg && tg[0] == '1') c->use_tc_gemm = true;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;

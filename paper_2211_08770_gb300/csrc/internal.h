@@ -148,7 +148,7 @@ struct Ctx {
     tt_sign_rule sign_rule = TT_SIGN_STABLE;
     int sm_count = 0;
     bool use_tc = true;       // tensor-core Gram in TT_MIXED_TF32
-    bool use_tc_gemm = true;  // tensor-core split-TF32 apply / absorb GEMMs in TT_MIXED_TF32
+    bool use_tc_gemm = false;  // tensor-core split-TF32 apply / absorb GEMMs in TT_MIXED_TF32
     int* tc_err = nullptr;  // device flag: a bounded wait of a tensor-core kernel ran out
     // lifetime: one reference for the owner plus one per live tensor; the
     // context is deleted when the last reference goes
