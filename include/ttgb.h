@@ -257,6 +257,35 @@ tt_status tt_cholesky_inverse(tt_ctx* ctx, int n, const void* G, void* L, void* 
 /* Householder sign rule used by subsequent TT_HOUSEHOLDER calls. */
 tt_status tt_set_sign_rule(tt_ctx* ctx, tt_sign_rule rule);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
+/* <x, y> in FP64 without allocating any device memory, for callers that
+ * cannot call cudaMalloc: code that runs while a CUDA graph is being
+ * captured, hosts whose device memory is all handed to their own pool, or
+ * latency-critical loops that must avoid cudaMalloc's implicit
+ * synchronization.  The paper has no counterpart; this is the contraction of
+ * tt_dot (W_k = sum_i X_k(i)^T W_{k-1} Y_k(i)) with its work arrays in a
+ * static device array of 2^20 doubles (8 MiB) that every GPU loading the
+ * library holds until the process exits.
+ *
+ * Arguments: cuda_stream (cudaStream_t, NULL = legacy default stream) on the
+ * calling thread's current device; d, n[0..d-1], rx[0..d], ry[0..d] the
+ * shapes (host arrays, boundary ranks 1); x_cores[k], y_cores[k] device
+ * pointers (host arrays of them) to FP64 cores in the [r][n][r] layout;
+ * result_dev a device pointer receiving the one double.  The call is
+ * asynchronous on the stream: synchronize before reading result_dev.
+ * Creates no context, allocates nothing, does not synchronize.
+ *
+ * The work arrays need max_k rx[k+1] ry[k+1] + max_k rx[k] n[k] ry[k+1]
+ * doubles; larger shapes are rejected with TT_ERR_ARG (tt_last_error says
+ * by how much).  The first call on a device looks up the array's device
+ * address; make that first call before any stream capture.  All calls share
+ * the one array, which keeps the previous call's contents: calls that
+ * overlap on the GPU (different streams without ordering) race. */
+tt_status tt_dot_f64_noalloc(void* cuda_stream, int d, const int* n, const int* rx, const int* ry,
+                             const double* const* x_cores, const double* const* y_cores,
+                             double* result_dev);
+
 /* ---- diagnostics ------------------------------------------------------- */
 
 const char* tt_status_str(tt_status s);

@@ -76,6 +76,7 @@ _SIGS = {
     "tt_gram_f32": (_I, [_P, _I, C.c_long, _P, C.c_long, _P, _I]),
     "tt_cholesky_inverse": (_I, [_P, _I, _P, _P, _P, _D, _D, _PI]),
     "tt_gemm_f32": (_I, [_P, _I, _I, _I, _I, _P, C.c_long, _P, C.c_long, _P, C.c_long, _I]),
+    "tt_dot_f64_noalloc": (_I, [_P, _I, _PI, _PI, _PI, _PP, _PP, _P]),
     "tt_status_str": (C.c_char_p, [_I]),
     "tt_last_error": (C.c_char_p, []),
 }
@@ -305,6 +306,18 @@ def tt_gram_f32(ctx, n, K, x_ptr, ldx, g_ptr, use_tensor_cores=True):
     """G = X X^T for device FP32 pointers (see include/ttgb.h)."""
     _check(lib().tt_gram_f32(ctx.handle, n, K, _P(x_ptr), ldx, _P(g_ptr), 1 if use_tensor_cores else 0),
            "tt_gram_f32")
+
+
+def tt_dot_f64_noalloc(stream, n, rx, ry, x_ptrs, y_ptrs, result_ptr):
+    """<x, y> of FP64 device cores into the device double at result_ptr,
+    allocating nothing (see include/ttgb.h); asynchronous on `stream`."""
+    d = len(n)
+    nn = (C.c_int * d)(*n)
+    a = (C.c_int * (d + 1))(*rx)
+    b = (C.c_int * (d + 1))(*ry)
+    xs = (_P * d)(*x_ptrs)
+    ys = (_P * d)(*y_ptrs)
+    _check(lib().tt_dot_f64_noalloc(_P(stream or None), d, nn, a, b, xs, ys, _P(result_ptr)), "tt_dot_f64_noalloc")
 
 
 def tt_gemm_f32(ctx, trans_b, M, N, K, a_ptr, lda, b_ptr, ldb, c_ptr, ldc, use_tensor_cores=True):
