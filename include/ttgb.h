@@ -236,8 +236,10 @@ tt_status tt_gram_f32(tt_ctx* ctx, int n, long K, const float* X, long ldx, floa
  * core <- core L): C = A op(B) for device FP32 matrices, A M x K row-major
  * (lda), op(B) = B^T with B N x K row-major when trans_b != 0, else B (K x N
  * row-major, ldb); C M x N row-major (ldc), overwritten.  use_tensor_cores
- * != 0 selects the tcgen05 split-TF32 kernel (A_hi B_hi + A_hi B_lo +
- * A_lo B_hi, FP32 accumulation), else the CUDA-core FP32 kernel.  TT_ERR_ARG
+ * selects the kernel: 0 the CUDA-core FP32 kernel; 1 the tcgen05 kernel with
+ * each operand split into three round-to-nearest TF32 parts (hi + mid + lo,
+ * six products, FP32 accumulation: FP32-level accuracy); 2 the same with two
+ * parts (hi + lo, three products, ~2^-22 relative error per product).  TT_ERR_ARG
  * when the tensor-core kernel cannot take the layout (a pointer or leading
  * dimension not 16-byte aligned). */
 tt_status tt_gemm_f32(tt_ctx* ctx, int trans_b, int M, int N, int K, const float* A, long lda,

@@ -383,11 +383,11 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     // TTGB_NO_TENSOR_CORES=1 keeps TT_MIXED_TF32 contexts on the CUDA-core Gram
     const char* no_tc = getenv("TTGB_NO_TENSOR_CORES");
     if (no_tc && no_tc[0] == '1') c->use_tc = false;
-    // TTGB_TC_GEMM=1 moves the core-producing GEMMs to the split-TF32
-    // tensor-core kernel (three products; its chained error exceeds the
-    // FP32 CUDA-core kernel's, so it is opt-in)
+    // TTGB_TC_GEMM=0 keeps the core-producing GEMMs on CUDA cores; =2 selects
+    // the two-part split (3 products, faster, ~2^-22 per product)
     const char* tg = getenv("TTGB_TC_GEMM");
-    if (tg && tg[0] == '1') c->use_tc_gemm = true;
+    if (tg && tg[0] == '0') c->use_tc_gemm = false;
+    if (tg && tg[0] == '2') c->tc_gemm_split = 2;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
@@ -613,7 +613,8 @@ tt_status tt_gemm_f32(tt_ctx* ctx, int trans_b, int M, int N, int K, const float
     TT_API_BEGIN
     if (!ctx || !A || !B || !C || M < 1 || N < 1 || K < 1) throw_status(TT_ERR_ARG, "bad arguments");
     if (use_tensor_cores) {
-        if (!gemm_tc3_tf32(*ctx, trans_b != 0, M, N, K, A, lda, B, ldb, C, ldc))
+        if (use_tensor_cores != 1 && use_tensor_cores != 2) throw_status(TT_ERR_ARG, "use_tensor_cores must be 0, 1 or 2");
+        if (!gemm_tc3_tf32(*ctx, trans_b != 0, M, N, K, A, lda, B, ldb, C, ldc, use_tensor_cores == 1 ? 3 : 2))
             throw_status(TT_ERR_ARG, "layout not supported by the tensor-core kernel");
         check_tc_error(*ctx);
     } else {

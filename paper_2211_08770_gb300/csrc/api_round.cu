@@ -108,7 +108,8 @@ struct Rounder {
     void mm(bool tA, bool tB, int M, int N, int K, const T* A, long lda, const T* B, long ldb, T* C, long ldc) {
         if constexpr (sizeof(T) == 4) {
             if (tc && c->use_tc_gemm && !tA &&
-                gemm_tc3_tf32(*c, tB, M, N, K, (const float*)A, lda, (const float*)B, ldb, (float*)C, ldc))
+                gemm_tc3_tf32(*c, tB, M, N, K, (const float*)A, lda, (const float*)B, ldb, (float*)C, ldc,
+                              c->tc_gemm_split))
                 return;
         }
         gemm<T>(*c, tA, tB, M, N, K, T(1), A, lda, B, ldb, T(0), C, ldc);

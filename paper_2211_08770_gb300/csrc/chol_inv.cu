@@ -287,6 +287,8 @@ chol_inv_kernel(int n, const S* __restrict__ G, S* __restrict__ L, S* __restrict
 template <class S, class C>
 void chol_inv(Ctx& c, int n, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st) {
     if (n <= 0) return;
+    // panel in shared memory when it fits (n <= 512 FP32, n <= 256 FP64)
+    if (chol_inv_smem<S, C>(c, n, G, L, T, shift_rel, drop_rel, st)) return;
     constexpr int NT = sizeof(C) == 8 ? 256 : 512;
     const size_t smem = (NT / 32) * sizeof(WarpTiles<C>);
     static bool attr = false;

@@ -70,6 +70,11 @@ void cholesky(Ctx& c, int n, const S* G, S* L, double shift_rel, double drop_rel
 template <class S, class C>
 void chol_inv(Ctx& c, int n, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st_dev);
 
+// the same with the working panel in shared memory; false (nothing
+// launched) when n exceeds 512 (FP32) or 256 (FP64)
+template <class S, class C>
+bool chol_inv_smem(Ctx& c, int n, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st_dev);
+
 // T = L^{-1} for lower-triangular L with possibly zero (dropped) columns:
 // dropped indices give zero rows and columns of T.
 template <class S, class C>
@@ -125,10 +130,11 @@ void axpy(Ctx& c, long n, double alpha, const T* x, T* y);  // y += alpha x
 bool gram_rows_tc_tf32(Ctx& c, int n, long K, const float* X, long ldx, float* G);
 // C (M x N, row-major, ldc) = A (M x K, row-major) op(B), op(B) = B^T with B
 // N x K row-major when bT, else B (K x N row-major); split-TF32 on tcgen05
-// (3 MMAs per k-step, FP32 accumulation).  Returns false (nothing launched)
-// when a pointer or leading dimension is not 16-byte aligned.
+// with FP32 accumulation: nsplit = 3 (hi + mid + lo, 6 MMAs per k-step,
+// FP32-level products) or 2 (hi + lo, 3 MMAs).  Returns false (nothing
+// launched) when a pointer or leading dimension is not 16-byte aligned.
 bool gemm_tc3_tf32(Ctx& c, bool bT, int M, int N, int K, const float* A, long lda, const float* B, long ldb,
-                   float* C, long ldc);
+                   float* C, long ldc, int nsplit);
 // reads (and clears) the tensor-core timeout flag; throws TT_ERR_TIMEOUT if set
 void check_tc_error(Ctx& c);
 
@@ -148,7 +154,8 @@ struct Ctx {
     tt_sign_rule sign_rule = TT_SIGN_STABLE;
     int sm_count = 0;
     bool use_tc = true;       // tensor-core Gram in TT_MIXED_TF32
-    bool use_tc_gemm = false;  // tensor-core split-TF32 apply / absorb GEMMs in TT_MIXED_TF32
+    bool use_tc_gemm = true;  // tensor-core split-TF32 apply / absorb GEMMs in TT_MIXED_TF32
+    int tc_gemm_split = 3;    // 3: hi + mid + lo (6 products), 2: hi + lo (3 products)
     int* tc_err = nullptr;  // device flag: a bounded wait of a tensor-core kernel ran out
     // lifetime: one reference for the owner plus one per live tensor; the
     // context is deleted when the last reference goes

@@ -1,9 +1,11 @@
 // Split-TF32 GEMM on the 5th-generation tensor cores: C = A op(B) with FP32
-// operands, each split into round-to-nearest TF32 parts x = x_hi + x_lo and
-// multiplied as A_hi B_hi + A_hi B_lo + A_lo B_hi (kind::tf32, FP32
-// accumulation in TMEM).  These are the GEMMs of TT-round that produce core
-// values (apply Q = L^{-1} X and absorb core <- core L), where plain TF32
-// (10-bit mantissa) would perturb the represented tensor by ~1e-3.
+// operands, each split into round-to-nearest TF32 parts, kind::tf32 MMAs with
+// FP32 accumulation in TMEM.  Three parts x = hi + mid + lo and the six
+// products hh, hm, mh, hl, lh, mm leave only terms below 2^-33 |a||b| out
+// (FP32-level products); two parts x = hi + lo and the products hh, hl, lh
+// leave ~2^-22.  These are the GEMMs of TT-round that produce core values
+// (apply Q = L^{-1} X and absorb core <- core L), where plain TF32 (10-bit
+// mantissa) would perturb the represented tensor by ~1e-3.
 //
 // A is M x K row-major (K contiguous).  B is either N x K row-major
 // ("T": C = A B^T) or K x N row-major ("N": C = A B, N contiguous).  One CTA
@@ -28,13 +30,15 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 32;
 constexpr int TILE = BM * BK * 4;  // 16 KB, one operand tile
-constexpr int NSTG = 2, NOP = 2;
+constexpr int NSTG = 2;
 constexpr uint32_t TMEM_COLS = 128;
 constexpr long long WAIT_LIMIT = 4000000000LL;
 
+constexpr int NOP_MAX = 2;
+
 struct __align__(8) GemmCtl {
     uint64_t stg_full[NSTG], stg_empty[NSTG];
-    uint64_t op_full[NOP], op_empty[NOP];
+    uint64_t op_full[NOP_MAX], op_empty[NOP_MAX];
     uint64_t done;
     uint32_t tmem_base;
 };
@@ -49,6 +53,23 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// three-way split x = hi + mid + lo, each round-to-nearest TF32; the
+// remainder is below 2^-33 |x|
+__device__ __forceinline__ void split4x3(const float4 v, float4& hi, float4& mi, float4& lo) {
+    float h[4], m[4], l[4];
+    const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h[i] = __uint_as_float(rna_tf32(x[i]));
+        const float r = x[i] - h[i];
+        m[i] = __uint_as_float(rna_tf32(r));
+        l[i] = __uint_as_float(rna_tf32(r - m[i]));
+    }
+    hi = make_float4(h[0], h[1], h[2], h[3]);
+    mi = make_float4(m[0], m[1], m[2], m[3]);
+    lo = make_float4(l[0], l[1], l[2], l[3]);
+}
+
 __device__ __forceinline__ void split4(const float4 v, float4& hi, float4& lo) {
     const float h0 = __uint_as_float(rna_tf32(v.x)), h1 = __uint_as_float(rna_tf32(v.y));
     const float h2 = __uint_as_float(rna_tf32(v.z)), h3 = __uint_as_float(rna_tf32(v.w));
@@ -57,18 +78,39 @@ __device__ __forceinline__ void split4(const float4 v, float4& hi, float4& lo) {
                      __uint_as_float(rna_tf32(v.z - h2)), __uint_as_float(rna_tf32(v.w - h3)));
 }
 
+// writes the NS parts of v to the same offset of NS consecutive tiles
+template <int NS>
+__device__ __forceinline__ void store_parts(const float4 v, unsigned char* dst) {
+    if (NS == 3) {
+        float4 h, m, l;
+        split4x3(v, h, m, l);
+        *reinterpret_cast<float4*>(dst) = h;
+        *reinterpret_cast<float4*>(dst + TILE) = m;
+        *reinterpret_cast<float4*>(dst + 2 * TILE) = l;
+    } else {
+        float4 h, l;
+        split4(v, h, l);
+        *reinterpret_cast<float4*>(dst) = h;
+        *reinterpret_cast<float4*>(dst + TILE) = l;
+    }
+}
+
 // byte offset of the 16-byte chunk c4 of row r in a 128-byte-swizzled tile
 __device__ __forceinline__ int sw128(int r, int c4) { return r * 128 + ((c4 ^ (r & 7)) << 4); }
 
-template <bool BT>
+// NS = 2: x = hi + lo, products hi*hi + hi*lo + lo*hi (3 MMAs per k-step)
+// NS = 3: x = hi + mid + lo, products hh + hm + mh + hl + lh + mm (6 MMAs)
+template <bool BT, int NS>
 __global__ void __launch_bounds__(192, 1)
 gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
                   int K, float* __restrict__ Cm, long ldc, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    // operand ring first (1024-aligned tiles): [NOP][A_hi, A_lo, B_hi, B_lo]
+    // operand ring first (1024-aligned tiles): [NOP][A parts.., B parts..]
+    constexpr int NOP = (NS == 3) ? 1 : 2;
+    constexpr int OPT = 2 * NS;  // tiles per operand stage
     unsigned char* opr = base;
-    unsigned char* stg = opr + NOP * 4 * TILE;  // [NSTG][A raw, B raw]
+    unsigned char* stg = opr + NOP * OPT * TILE;  // [NSTG][A raw, B raw]
     GemmCtl* ctl = reinterpret_cast<GemmCtl*>(stg + NSTG * 2 * TILE);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -126,15 +168,24 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                 const int o = it % NOP;
                 if (!tc::mbar_wait_bounded(&ctl->op_full[o], (it / NOP) & 1, WAIT_LIMIT)) { ok = false; break; }
                 tc::tc_fence_after();
-                const uint32_t ahi = tc::smem_u32(opr + o * 4 * TILE);
-                const uint32_t alo = ahi + TILE, bhi = ahi + 2 * TILE, blo = ahi + 3 * TILE;
+                // A parts at tiles 0..NS-1, B parts at NS..2NS-1: 0 = hi, 1 = lo (NS = 2)
+                // or 0 = hi, 1 = mid, 2 = lo (NS = 3)
+                const uint32_t a0 = tc::smem_u32(opr + o * OPT * TILE);
+                const uint32_t b0 = a0 + NS * TILE;
 #pragma unroll
                 for (int kk = 0; kk < BK / 8; ++kk) {
                     const uint32_t off = kk * 32;
                     const uint32_t acc0 = (it > 0 || kk > 0) ? 1u : 0u;
-                    tc::mma_tf32(tmem, tc::sdesc_kmajor_sw128(ahi + off), tc::sdesc_kmajor_sw128(bhi + off), idesc, acc0);
-                    tc::mma_tf32(tmem, tc::sdesc_kmajor_sw128(ahi + off), tc::sdesc_kmajor_sw128(blo + off), idesc, 1u);
-                    tc::mma_tf32(tmem, tc::sdesc_kmajor_sw128(alo + off), tc::sdesc_kmajor_sw128(bhi + off), idesc, 1u);
+                    auto ad = [&](int part) { return tc::sdesc_kmajor_sw128(a0 + part * TILE + off); };
+                    auto bd = [&](int part) { return tc::sdesc_kmajor_sw128(b0 + part * TILE + off); };
+                    tc::mma_tf32(tmem, ad(0), bd(0), idesc, acc0);
+                    tc::mma_tf32(tmem, ad(0), bd(1), idesc, 1u);
+                    tc::mma_tf32(tmem, ad(1), bd(0), idesc, 1u);
+                    if (NS == 3) {
+                        tc::mma_tf32(tmem, ad(0), bd(2), idesc, 1u);
+                        tc::mma_tf32(tmem, ad(2), bd(0), idesc, 1u);
+                        tc::mma_tf32(tmem, ad(1), bd(1), idesc, 1u);
+                    }
                 }
                 tc::mma_commit(&ctl->op_empty[o]);
             }
@@ -153,26 +204,16 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             if (!ok) break;
             const unsigned char* sa = stg + s * 2 * TILE;
             const unsigned char* sb = sa + TILE;
-            unsigned char* ahi = opr + o * 4 * TILE;
-            unsigned char* alo = ahi + TILE;
-            unsigned char* bhi = ahi + 2 * TILE;
-            unsigned char* blo = ahi + 3 * TILE;
+            unsigned char* a0 = opr + o * OPT * TILE;
+            unsigned char* b0 = a0 + NS * TILE;
             // A (and B when K-major): staging [128 rows][32 k], 8 chunks of 4 per row
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int idx = q * 128 + t;
                 const int r = idx >> 3, c4 = idx & 7;
-                float4 v = *reinterpret_cast<const float4*>(sa + r * 128 + c4 * 16);
-                float4 h, l;
-                split4(v, h, l);
-                *reinterpret_cast<float4*>(ahi + sw128(r, c4)) = h;
-                *reinterpret_cast<float4*>(alo + sw128(r, c4)) = l;
-                if (BT) {
-                    v = *reinterpret_cast<const float4*>(sb + r * 128 + c4 * 16);
-                    split4(v, h, l);
-                    *reinterpret_cast<float4*>(bhi + sw128(r, c4)) = h;
-                    *reinterpret_cast<float4*>(blo + sw128(r, c4)) = l;
-                }
+                const int off = sw128(r, c4);
+                store_parts<NS>(*reinterpret_cast<const float4*>(sa + r * 128 + c4 * 16), a0 + off);
+                if (BT) store_parts<NS>(*reinterpret_cast<const float4*>(sb + r * 128 + c4 * 16), b0 + off);
             }
             if (!BT) {
                 // B N-major: staging [32 k][128 n]; operand row n holds k = 0..31
@@ -181,11 +222,7 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                     const int idx = q * 128 + t;
                     const int nn = idx & 127, c4 = idx >> 7;
                     const float* col = reinterpret_cast<const float*>(sb) + (c4 * 4) * BN + nn;
-                    float4 v = make_float4(col[0], col[BN], col[2 * BN], col[3 * BN]);
-                    float4 h, l;
-                    split4(v, h, l);
-                    *reinterpret_cast<float4*>(bhi + sw128(nn, c4)) = h;
-                    *reinterpret_cast<float4*>(blo + sw128(nn, c4)) = l;
+                    store_parts<NS>(make_float4(col[0], col[BN], col[2 * BN], col[3 * BN]), b0 + sw128(nn, c4));
                 }
             }
             // every converter thread makes its own generic-proxy writes visible
@@ -268,8 +305,8 @@ bool make_map(CUtensorMap* map, const float* ptr, long inner, long outer, long l
 }  // namespace
 
 bool gemm_tc3_tf32(Ctx& c, bool bT, int M, int N, int K, const float* A, long lda, const float* B, long ldb,
-                   float* C, long ldc) {
-    if (M <= 0 || N <= 0 || K <= 0) return false;
+                   float* C, long ldc, int nsplit) {
+    if (M <= 0 || N <= 0 || K <= 0 || (nsplit != 2 && nsplit != 3)) return false;
     auto aligned = [](const void* p, long ld) { return ((uintptr_t)p & 15) == 0 && (ld * 4) % 16 == 0; };
     if (!aligned(A, lda) || !aligned(B, ldb)) return false;
     if (lda < K || (bT ? ldb < K : ldb < N) || ldc < N) return false;
@@ -282,20 +319,27 @@ bool gemm_tc3_tf32(Ctx& c, bool bT, int M, int N, int K, const float* A, long ld
     }
     const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     if (grid.y > 65535) return false;
-    const size_t smem = 1024 + NOP * 4 * TILE + NSTG * 2 * TILE + sizeof(GemmCtl) + 64;
-    static bool attr[2] = {false, false};
-    if (!attr[bT]) {
-        if (bT)
-            TT_CUDA(cudaFuncSetAttribute(gemm3_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        else
-            TT_CUDA(cudaFuncSetAttribute(gemm3_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr[bT] = true;
+    const int nop = (nsplit == 3) ? 1 : 2;
+    const size_t smem = 1024 + (size_t)nop * 2 * nsplit * TILE + NSTG * 2 * TILE + sizeof(GemmCtl) + 64;
+    static bool attr[2][2] = {{false, false}, {false, false}};
+    const int si = nsplit - 2;
+#define TT_GEMM3_ATTR(BT_, NS_)                                                                              \
+    TT_CUDA(cudaFuncSetAttribute(gemm3_tf32_kernel<BT_, NS_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)smem))
+    if (!attr[bT][si]) {
+        if (bT && si) TT_GEMM3_ATTR(true, 3);
+        else if (bT) TT_GEMM3_ATTR(true, 2);
+        else if (si) TT_GEMM3_ATTR(false, 3);
+        else TT_GEMM3_ATTR(false, 2);
+        attr[bT][si] = true;
     }
-    ProfScope ps(c, "gemm_tf32x3_tc", 2.0 * M * (double)N * K, 4.0 * ((double)M * K + (double)K * N + (double)M * N));
-    if (bT)
-        gemm3_tf32_kernel<true><<<grid, 192, smem, c.stream>>>(ma, mb, M, N, K, C, ldc, c.tc_err);
-    else
-        gemm3_tf32_kernel<false><<<grid, 192, smem, c.stream>>>(ma, mb, M, N, K, C, ldc, c.tc_err);
+#undef TT_GEMM3_ATTR
+    ProfScope ps(c, nsplit == 3 ? "gemm_tf32x6_tc" : "gemm_tf32x3_tc", 2.0 * M * (double)N * K,
+                 4.0 * ((double)M * K + (double)K * N + (double)M * N));
+    if (bT && si) gemm3_tf32_kernel<true, 3><<<grid, 192, smem, c.stream>>>(ma, mb, M, N, K, C, ldc, c.tc_err);
+    else if (bT) gemm3_tf32_kernel<true, 2><<<grid, 192, smem, c.stream>>>(ma, mb, M, N, K, C, ldc, c.tc_err);
+    else if (si) gemm3_tf32_kernel<false, 3><<<grid, 192, smem, c.stream>>>(ma, mb, M, N, K, C, ldc, c.tc_err);
+    else gemm3_tf32_kernel<false, 2><<<grid, 192, smem, c.stream>>>(ma, mb, M, N, K, C, ldc, c.tc_err);
     TT_LAUNCHED(c);
     return true;
 }

@@ -322,8 +322,9 @@ def tt_dot_f64_noalloc(stream, n, rx, ry, x_ptrs, y_ptrs, result_ptr):
 
 def tt_gemm_f32(ctx, trans_b, M, N, K, a_ptr, lda, b_ptr, ldb, c_ptr, ldc, use_tensor_cores=True):
     """C = A op(B) on device FP32 pointers (see include/ttgb.h)."""
+    mode = int(use_tensor_cores) if not isinstance(use_tensor_cores, bool) else (1 if use_tensor_cores else 0)
     _check(lib().tt_gemm_f32(ctx.handle, 1 if trans_b else 0, M, N, K, _P(a_ptr), lda, _P(b_ptr), ldb, _P(c_ptr),
-                             ldc, 1 if use_tensor_cores else 0), "tt_gemm_f32")
+                             ldc, mode), "tt_gemm_f32")
 
 
 def tt_cholesky_inverse(ctx, n, g_ptr, l_ptr, t_ptr, shift_rel=0.0, drop_rel=0.0):
