@@ -31,7 +31,7 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 32;
 constexpr int TILE = BM * BK * 4;  // 16 KB, one operand tile
 constexpr int NSTG = 2;
-constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TMEM_COLS = 256;  // two 128-column accumulators
 constexpr long long WAIT_LIMIT = 4000000000LL;
 
 constexpr int NOP_MAX = 2;
@@ -39,6 +39,7 @@ constexpr int NOP_MAX = 2;
 struct __align__(8) GemmCtl {
     uint64_t stg_full[NSTG], stg_empty[NSTG];
     uint64_t op_full[NOP_MAX], op_empty[NOP_MAX];
+    uint64_t acc_full[2], acc_empty[2];
     uint64_t done;
     uint32_t tmem_base;
 };
@@ -126,6 +127,10 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             tc::mbar_init(&ctl->op_full[s], 128);
             tc::mbar_init(&ctl->op_empty[s], 1);
         }
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&ctl->acc_full[s], 1);
+            tc::mbar_init(&ctl->acc_empty[s], 128);
+        }
         tc::mbar_init(&ctl->done, 1);
         tc::fence_barrier_init();
     }
@@ -165,9 +170,12 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             constexpr uint32_t idesc = tc::idesc_tf32(BM, BN);
             bool ok = true;
             for (int it = 0; it < nk; ++it) {
-                const int o = it % NOP;
+                const int o = it % NOP, ab = it & 1;
+                // accumulator buffer ab must have been read back by the promoters
+                if (!tc::mbar_wait_bounded(&ctl->acc_empty[ab], ((it >> 1) & 1) ^ 1, WAIT_LIMIT)) { ok = false; break; }
                 if (!tc::mbar_wait_bounded(&ctl->op_full[o], (it / NOP) & 1, WAIT_LIMIT)) { ok = false; break; }
                 tc::tc_fence_after();
+                const uint32_t dacc = tmem + ab * 128;
                 // A parts at tiles 0..NS-1, B parts at NS..2NS-1: 0 = hi, 1 = lo (NS = 2)
                 // or 0 = hi, 1 = mid, 2 = lo (NS = 3)
                 const uint32_t a0 = tc::smem_u32(opr + o * OPT * TILE);
@@ -175,27 +183,53 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
 #pragma unroll
                 for (int kk = 0; kk < BK / 8; ++kk) {
                     const uint32_t off = kk * 32;
-                    const uint32_t acc0 = (it > 0 || kk > 0) ? 1u : 0u;
+                    // each k-step starts a fresh partial sum (promoted to FP32
+                    // registers by the converter warps)
+                    const uint32_t acc0 = (kk > 0) ? 1u : 0u;
                     auto ad = [&](int part) { return tc::sdesc_kmajor_sw128(a0 + part * TILE + off); };
                     auto bd = [&](int part) { return tc::sdesc_kmajor_sw128(b0 + part * TILE + off); };
-                    tc::mma_tf32(tmem, ad(0), bd(0), idesc, acc0);
-                    tc::mma_tf32(tmem, ad(0), bd(1), idesc, 1u);
-                    tc::mma_tf32(tmem, ad(1), bd(0), idesc, 1u);
+                    tc::mma_tf32(dacc, ad(0), bd(0), idesc, acc0);
+                    tc::mma_tf32(dacc, ad(0), bd(1), idesc, 1u);
+                    tc::mma_tf32(dacc, ad(1), bd(0), idesc, 1u);
                     if (NS == 3) {
-                        tc::mma_tf32(tmem, ad(0), bd(2), idesc, 1u);
-                        tc::mma_tf32(tmem, ad(2), bd(0), idesc, 1u);
-                        tc::mma_tf32(tmem, ad(1), bd(1), idesc, 1u);
+                        tc::mma_tf32(dacc, ad(0), bd(2), idesc, 1u);
+                        tc::mma_tf32(dacc, ad(2), bd(0), idesc, 1u);
+                        tc::mma_tf32(dacc, ad(1), bd(1), idesc, 1u);
                     }
                 }
                 tc::mma_commit(&ctl->op_empty[o]);
+                tc::mma_commit(&ctl->acc_full[ab]);
             }
             if (!ok) atomicExch(err, 1);
             tc::mma_commit(&ctl->done);
         }
     } else {
-        // converters (warps 2..5, 128 threads), then the epilogue
+        // converters / promoters (warps 2..5, 128 threads): split stage it
+        // into TF32 parts, then add the partial sum of k-step it-1 from TMEM
+        // into FP32 registers (round-to-nearest); finally store C
         const int t = threadIdx.x - 64;
+        const int q = warp & 3;  // TMEM lane quarter this warp may read
+        float acc[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) acc[j] = 0.f;
         bool ok = true;
+        auto promote = [&](int j) -> bool {
+            const int ab = j & 1;
+            const bool g = __all_sync(0xffffffffu, tc::mbar_wait_bounded(&ctl->acc_full[ab], (j >> 1) & 1, WAIT_LIMIT));
+            if (!g) return false;
+            tc::tc_fence_after();
+#pragma unroll
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                __syncwarp();
+                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + ab * 128 + c * 32, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&ctl->acc_empty[ab]);
+            return true;
+        };
         for (int it = 0; it < nk && ok; ++it) {
             const int s = it % NSTG, o = it % NOP;
             const bool g1 = tc::mbar_wait_bounded(&ctl->stg_full[s], (it / NSTG) & 1, WAIT_LIMIT);
@@ -208,8 +242,8 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             unsigned char* b0 = a0 + NS * TILE;
             // A (and B when K-major): staging [128 rows][32 k], 8 chunks of 4 per row
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int idx = q * 128 + t;
+            for (int qq = 0; qq < 8; ++qq) {
+                const int idx = qq * 128 + t;
                 const int r = idx >> 3, c4 = idx & 7;
                 const int off = sw128(r, c4);
                 store_parts<NS>(*reinterpret_cast<const float4*>(sa + r * 128 + c4 * 16), a0 + off);
@@ -218,8 +252,8 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             if (!BT) {
                 // B N-major: staging [32 k][128 n]; operand row n holds k = 0..31
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int idx = q * 128 + t;
+                for (int qq = 0; qq < 8; ++qq) {
+                    const int idx = qq * 128 + t;
                     const int nn = idx & 127, c4 = idx >> 7;
                     const float* col = reinterpret_cast<const float*>(sb) + (c4 * 4) * BN + nn;
                     store_parts<NS>(make_float4(col[0], col[BN], col[2 * BN], col[3 * BN]), b0 + sw128(nn, c4));
@@ -230,36 +264,25 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             fence_proxy_async();
             tc::mbar_arrive(&ctl->op_full[o]);
             tc::mbar_arrive(&ctl->stg_empty[s]);
+            if (it >= 1) ok = promote(it - 1);
         }
+        if (ok) ok = promote(nk - 1);
         if (!ok && lane == 0) atomicExch(err, 1);
-        // epilogue: TMEM lanes of this warp's quarter
-        const int q = warp & 3;
-        const bool got = __all_sync(0xffffffffu, ok && tc::mbar_wait_bounded(&ctl->done, 0, 2 * WAIT_LIMIT));
         int e = 0;
         if (lane == 0) e = *(volatile int*)err;
         e = __shfl_sync(0xffffffffu, e, 0);
-        if (!got) {
-            if (lane == 0) atomicExch(err, 1);
-        } else if (e == 0) {
-            tc::tc_fence_after();
+        if (ok && e == 0) {
             const int row = m0 + q * 32 + lane;
-            float v[32];
-#pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                __syncwarp();
-                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c * 32, v);
-                const int col0 = n0 + c * 32;
-                if (row < M) {
-                    float* dst = Cm + (long)row * ldc + col0;
-                    if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+            if (row < M) {
+                float* dst = Cm + (long)row * ldc + n0;
+                if (n0 + BN <= N && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                    } else {
+                    for (int j = 0; j < BN; j += 4)
+                        *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+                } else {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (col0 + j < N) dst[j] = v[j];
-                    }
+                    for (int j = 0; j < BN; ++j)
+                        if (n0 + j < N) dst[j] = acc[j];
                 }
             }
         }
