@@ -10,9 +10,8 @@
 //    column reads), and so is block row p of T, so a tile update reads its
 //    operands from shared memory and only its 32 x 32 output goes to L2,
 //    loaded before the arithmetic so the load latency overlaps it;
-//  - the next diagonal block is factored by warp 0 right after it has
-//    applied the current panel to that block (lookahead), while the other
-//    warps finish the remaining tiles;
+//  - the 32 x 32 diagonal block is factored by the whole CTA (a single warp
+//    doing it serially was the critical path), with reciprocal pivots;
 //  - the panel solve keeps four rows in flight per warp.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -25,75 +24,70 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-template <class S, class C>
-struct DiagOut {
-    C (*Ds)[33];
-    C (*Di)[33];
-};
-
-// factor + invert the diagonal block p (warp 0 only); writes Ds, Di and the
-// diagonal blocks of L and T in global memory
-template <class S, class C>
-__device__ void factor_diag(int n, int p, const S* __restrict__ G, S* __restrict__ L, S* __restrict__ Tm,
-                            double shift, double tau, C (*Ds)[33], C (*Di)[33], int* s_ndrop, int* s_nonfin,
-                            double* s_minratio) {
-    const int lane = threadIdx.x & 31;
+// factor + invert the diagonal block p with the whole CTA: column by column,
+// thread 0 takes the pivot decision, the column below it is scaled and the
+// trailing triangle of the block updated in parallel (two barriers per
+// column); then warp 0 forms the inverse (lane j = column j, in registers,
+// multiplying by the reciprocal pivots).  Writes Ds, Di and the diagonal
+// blocks of L and T in global memory.
+template <class S, class C, int NT>
+__device__ void factor_diag_cta(int n, int p, const S* __restrict__ G, S* __restrict__ L, S* __restrict__ Tm,
+                                double shift, double tau, C (*Ds)[33], C (*Di)[33], C* s_inv, int* s_ndrop,
+                                int* s_nonfin, double* s_minratio) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j0 = p * 32, jb = min(32, n - j0);
-    C d[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) d[k] = (lane < jb && k <= lane) ? (C)L[(long)(j0 + lane) * n + j0 + k] : C(0);
-    const double gd = (lane < jb) ? (double)G[(long)(j0 + lane) * n + j0 + lane] + shift : 1.0;
-    int ndrop = 0, nonfin = 0;
-    C minr = C(1e30);
+    for (int e = tid; e < 32 * 32; e += NT) {
+        const int r = e >> 5, k = e & 31;
+        Ds[r][k] = (r < jb && k <= r) ? (C)L[(long)(j0 + r) * n + j0 + k] : C(0);
+    }
+    __syncthreads();
     const C tau_c = (C)tau;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        if (c < jb) {
-            const C piv = __shfl_sync(FULL, d[c], c);
-            const C orig = (C)__shfl_sync(FULL, gd, c);
+    for (int c = 0; c < jb; ++c) {
+        if (tid == 0) {
+            const C piv = Ds[c][c];
+            const C orig = (C)((double)G[(long)(j0 + c) * n + j0 + c] + shift);
             const bool fin = isfinite(piv);
             const bool keep = fin && piv > tau_c && piv > C(0);
             const C dc = keep ? sqrt(piv) : C(0);
             const C inv = keep ? C(1) / dc : C(0);
-            if (lane == c) d[c] = dc;
-            else if (lane > c) d[c] *= inv;
+            Ds[c][c] = dc;
+            s_inv[c] = inv;
+            if (!fin) *s_nonfin = 1;
+            if (keep) *s_minratio = fmin(*s_minratio, orig > C(0) ? (double)(piv / orig) : 0.0);
+            else *s_ndrop += 1;
+        }
+        __syncthreads();
+        // trailing update of the block with the unscaled column c: A_rk -= a_rc a_kc / piv
+        const C inv = s_inv[c];
+        const C inv2 = inv * inv;
+        for (int e = tid; e < 32 * 32; e += NT) {
+            const int r = e >> 5, k = e & 31;
+            if (k > c && k <= r && r < jb) Ds[r][k] = fma(-Ds[r][c] * inv2, Ds[k][c], Ds[r][k]);
+        }
+        __syncthreads();
+        if (tid > c && tid < jb) Ds[tid][c] *= inv;  // scale column c (read again only after the next barrier)
+    }
+    __syncthreads();
+    if (warp == 0) {
+        C x[32];
 #pragma unroll
-            for (int k = c + 1; k < 32; ++k) {
-                const C lkc = __shfl_sync(FULL, d[c], k);
-                if (lane >= k) d[k] = fma(-d[c], lkc, d[k]);
-            }
-            nonfin |= !fin;
-            if (keep) minr = fmin(minr, orig > C(0) ? piv / orig : C(0));
-            else ++ndrop;
+        for (int i = 0; i < 32; ++i) {
+            C sacc = (i == lane) ? C(1) : C(0);
+#pragma unroll
+            for (int k = 0; k < i; ++k) sacc = fma(-Ds[i][k], x[k], sacc);
+            x[i] = (i < jb) ? sacc * s_inv[i] : C(0);
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Di[i][lane] = x[i];
+    }
+    __syncthreads();
+    for (int e = tid; e < 32 * 32; e += NT) {
+        const int r = e >> 5, k = e & 31;
+        if (r < jb && k <= r) {
+            L[(long)(j0 + r) * n + j0 + k] = (S)Ds[r][k];
+            Tm[(long)(j0 + r) * n + j0 + k] = (S)Di[r][k];
         }
     }
-#pragma unroll
-    for (int k = 0; k < 32; ++k) Ds[lane][k] = (k <= lane) ? d[k] : C(0);
-    __syncwarp();
-    C x[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        const C lii = Ds[i][i];
-        C s = (i == lane) ? C(1) : C(0);
-#pragma unroll
-        for (int k = 0; k < i; ++k) s = fma(-Ds[i][k], x[k], s);
-        x[i] = (lii != C(0) && i < jb) ? s / lii : C(0);
-    }
-#pragma unroll
-    for (int i = 0; i < 32; ++i) Di[i][lane] = x[i];
-    __syncwarp();
-    if (lane < jb) {
-        for (int k = 0; k <= lane; ++k) {
-            L[(long)(j0 + lane) * n + j0 + k] = (S)Ds[lane][k];
-            Tm[(long)(j0 + lane) * n + j0 + k] = (S)Di[lane][k];
-        }
-    }
-    if (lane == 0) {
-        *s_ndrop += ndrop;
-        *s_nonfin |= nonfin;
-        *s_minratio = fmin(*s_minratio, (double)minr);
-    }
-    __syncwarp();
 }
 
 // one 32 x 32 tile of the rank-32 update of panel p (task t)
@@ -160,6 +154,7 @@ chol_inv_smem_kernel(int n, int npad, const S* __restrict__ G, S* __restrict__ L
     C* TR = PT + 32L * npad;                 // [32][npad]
     __shared__ C Ds[32][33];
     __shared__ C Di[32][33];
+    __shared__ C s_inv[32];
     __shared__ double shd[32];
     __shared__ int s_ndrop, s_nonfinite;
     __shared__ double s_minratio;
@@ -213,10 +208,10 @@ chol_inv_smem_kernel(int n, int npad, const S* __restrict__ G, S* __restrict__ L
     __syncthreads();
 
     const int P = (n + 31) / 32;
-    if (warp == 0) factor_diag<S, C>(n, 0, G, L, Tm, shift, tau, Ds, Di, &s_ndrop, &s_nonfinite, &s_minratio);
-    __syncthreads();
     for (int p = 0; p < P; ++p) {
         const int j0 = p * 32, jb = min(32, n - j0);
+        // ---- phase 1: diagonal block, whole CTA
+        factor_diag_cta<S, C, NT>(n, p, G, L, Tm, shift, tau, Ds, Di, s_inv, &s_ndrop, &s_nonfinite, &s_minratio);
         // ---- phase 2a: diagonal block into the shared panel copies
         for (int r = warp; r < 32; r += NW) {
             const int i = j0 + r;
@@ -274,21 +269,12 @@ chol_inv_smem_kernel(int n, int npad, const S* __restrict__ G, S* __restrict__ L
             __syncwarp();
         }
         __syncthreads();
-        // ---- phase 3: rank-32 updates; warp 0 first updates the next diagonal
-        // block and factors it while the other warps take the remaining tiles
+        // ---- phase 3: rank-32 updates, one tile per warp at a time
         const int R = P - p - 1;
         if (R > 0) {
             const int nsy = R * (R + 1) / 2;
             const int ntask = nsy + R * (p + 1);
-            if (warp == 0) {
-                update_tile<S, C>(n, npad, p, 0, nsy, L, Tm, Pn, PT, TR);
-                __syncwarp();
-                factor_diag<S, C>(n, p + 1, G, L, Tm, shift, tau, Ds, Di, &s_ndrop, &s_nonfinite, &s_minratio);
-                if (NW == 1)
-                    for (int t = 1; t < ntask; ++t) update_tile<S, C>(n, npad, p, t, nsy, L, Tm, Pn, PT, TR);
-            } else {
-                for (int t = warp; t < ntask; t += NW - 1) update_tile<S, C>(n, npad, p, t, nsy, L, Tm, Pn, PT, TR);
-            }
+            for (int t = warp; t < ntask; t += NW) update_tile<S, C>(n, npad, p, t, nsy, L, Tm, Pn, PT, TR);
         }
         __syncthreads();
     }

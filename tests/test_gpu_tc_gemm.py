@@ -5,7 +5,8 @@ Two parts x = x_hi + x_lo (round-to-nearest TF32): each product keeps every
 term but lo*lo, so its error is below 3 * 2^-22 |a||b|; three parts
 (hi + mid + lo, six products) leave terms below 2^-33.  Sums add FP32
 accumulation error (~2^-24 sqrt(K) relative).  Bounds, relative to
-||a_i|| ||b_j|| at K <= 512: 2e-6 (two parts), 2e-7 (three parts).
+||a_i|| ||b_j|| at K <= 512: 2e-6 (two parts), 5e-7 (three parts; the FP32
+round-to-nearest sum of 32 products alone reaches ~3e-7).
 """
 import numpy as np
 import pytest
@@ -30,7 +31,7 @@ def _ref(A, B, trans_b):
     return Ad @ (Bd.T if trans_b else Bd)
 
 
-@pytest.mark.parametrize("parts,bound", [(3, 2e-7), (2, 2e-6)])
+@pytest.mark.parametrize("parts,bound", [(3, 5e-7), (2, 2e-6)])
 @pytest.mark.parametrize("trans_b", [True, False])
 @pytest.mark.parametrize("M,N,K", [(128, 128, 32), (400, 1000, 400), (64, 4096, 400), (25600, 400, 400),
                                    (130, 260, 36), (4, 8, 4), (1000, 64, 64)])
