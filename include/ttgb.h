@@ -224,8 +224,11 @@ tt_status tt_orthogonalize(tt_ctx* ctx, tt_scheme scheme, double delta,
  * the device FP32 matrix G (n x n, row-major, overwritten).  Only tiles on
  * or below the diagonal are computed (128 x 128 tiles for the tensor-core
  * kernel, 64 x 64 for the CUDA-core one); strictly-upper tiles stay zero.
- * use_tensor_cores != 0 selects the tcgen05 kind::tf32 kernel (TMA-staged
- * operands, FP32 accumulation in TMEM), else the CUDA-core FP32 kernel.
+ * use_tensor_cores = 1 selects the tcgen05 kind::tf32 kernel (TMA-staged
+ * operands, FP32 accumulation in TMEM), 0 the CUDA-core FP32 kernel.
+ * use_tensor_cores = 2 computes the column Gram G = X^T X instead, X being
+ * K x n row-major (ldx >= n): the Gram of a left unfolding, on tcgen05, the
+ * operands transposed into K-major tiles on chip.
  * TT_ERR_ARG when the tensor-core kernel cannot take the layout (X not
  * 16-byte aligned or ldx*4 not a multiple of 16); TT_ERR_TIMEOUT when one of
  * its bounded waits ran out. */

@@ -597,8 +597,13 @@ tt_status tt_dot_many(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tenso
 
 tt_status tt_gram_f32(tt_ctx* ctx, int n, long K, const float* X, long ldx, float* G, int use_tensor_cores) {
     TT_API_BEGIN
-    if (!ctx || !X || !G || n < 1 || K < 1 || ldx < K) throw_status(TT_ERR_ARG, "bad arguments");
-    if (use_tensor_cores) {
+    if (!ctx || !X || !G || n < 1 || K < 1 || ldx < (use_tensor_cores == 2 ? (long)n : K))
+        throw_status(TT_ERR_ARG, "bad arguments");
+    if (use_tensor_cores == 2) {
+        // column Gram: X is K x n row-major (ldx >= n), G = X^T X
+        if (!gram_cols_tc_tf32(*ctx, n, K, X, ldx, G)) throw_status(TT_ERR_ARG, "layout not supported by TMA");
+        check_tc_error(*ctx);
+    } else if (use_tensor_cores) {
         if (!gram_rows_tc_tf32(*ctx, n, K, X, ldx, G)) throw_status(TT_ERR_ARG, "layout not supported by TMA");
         check_tc_error(*ctx);
     } else {

@@ -96,8 +96,9 @@ struct Rounder {
 
     void gram_into(bool rows, bool fast, int a, long K, const T* X) {
         if constexpr (sizeof(T) == 4) {
-            if (fast && tc && rows) {
-                if (gram_rows_tc_tf32(*c, a, K, (const float*)X, K, (float*)G)) return;
+            if (fast && tc) {
+                if (rows && gram_rows_tc_tf32(*c, a, K, (const float*)X, K, (float*)G)) return;
+                if (!rows && gram_cols_tc_tf32(*c, a, K, (const float*)X, a, (float*)G)) return;
             }
         }
         gram<T, T>(*c, rows, a, K, X, rows ? K : a, G);

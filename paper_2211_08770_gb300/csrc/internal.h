@@ -128,6 +128,9 @@ void axpy(Ctx& c, long n, double alpha, const T* x, T* y);  // y += alpha x
 // tiles), split-K, FP32 accumulation in TMEM, atomically added into G (FP32,
 // zeroed first).  Returns false when the shape is not supported.
 bool gram_rows_tc_tf32(Ctx& c, int n, long K, const float* X, long ldx, float* G);
+// G = X^T X for X (m x n, row-major, ldx): the column Gram, same kernel family
+// (operands transposed into K-major tiles by converter warps).
+bool gram_cols_tc_tf32(Ctx& c, int n, long m, const float* X, long ldx, float* G);
 // C (M x N, row-major, ldc) = A (M x K, row-major) op(B), op(B) = B^T with B
 // N x K row-major when bT, else B (K x N row-major); split-TF32 on tcgen05
 // with FP32 accumulation: nsplit = 3 (hi + mid + lo, 6 MMAs per k-step,

@@ -164,6 +164,178 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int nt
     }
 }
 
+// ---------------------------------------------------------------------------
+// G = X^T X of the columns of X (m x n, row-major, n contiguous): the Gram
+// step of the left-to-right sweep, whose contraction runs over the rows of
+// the left unfolding.  TMA brings raw 32-row x 128-column FP32 boxes; the
+// converter warps round them to TF32 and write them transposed into the
+// K-major 128-byte-swizzled layout (column i of X becomes MMA row i), so the
+// MMA sees the same operand form as in the row Gram.
+constexpr int CSTG = 3, COP = 2;
+
+struct __align__(8) ColCtl {
+    uint64_t stg_full[CSTG], stg_empty[CSTG];
+    uint64_t op_full[COP], op_empty[COP];
+    uint64_t done;
+    uint32_t tmem_base;
+};
+
+__device__ __forceinline__ uint32_t rna_tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__global__ void __launch_bounds__(192, 1)
+gram_cols_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long m, int ntiles, long kchunk_steps,
+                      float* __restrict__ G, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* opr = base;                           // [COP][A, B] swizzled TF32 tiles
+    unsigned char* stg = opr + COP * 2 * TILE_BYTES;     // [CSTG][A raw, B raw]
+    ColCtl* ctl = reinterpret_cast<ColCtl*>(stg + CSTG * 2 * TILE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntri = ntiles * (ntiles + 1) / 2;
+    const int pair = blockIdx.x % ntri;
+    const long split = blockIdx.x / ntri;
+    int ti = 0;
+    while ((ti + 1) * (ti + 2) / 2 <= pair) ++ti;
+    const int tj = pair - ti * (ti + 1) / 2;
+    const bool diag = (ti == tj);
+    const long ksteps_total = (m + TK - 1) / TK;
+    const long ks0 = split * kchunk_steps;
+    const long ks1 = min(ksteps_total, ks0 + kchunk_steps);
+    const int nsteps = (int)max(0L, ks1 - ks0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CSTG; ++s) {
+            tc::mbar_init(&ctl->stg_full[s], 1);
+            tc::mbar_init(&ctl->stg_empty[s], 128);
+        }
+        for (int s = 0; s < COP; ++s) {
+            tc::mbar_init(&ctl->op_full[s], 128);
+            tc::mbar_init(&ctl->op_empty[s], 1);
+        }
+        tc::mbar_init(&ctl->done, 1);
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&ctl->tmem_base, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0 && nsteps > 0) {
+            tc::prefetch_tmap(&tmap);
+            const uint32_t bytes = diag ? TILE_BYTES : 2 * TILE_BYTES;
+            bool ok = true;
+            int issued = 0;
+            for (int it = 0; it < nsteps; ++it) {
+                const int s = it % CSTG;
+                if (!tc::mbar_wait_bounded(&ctl->stg_empty[s], ((it / CSTG) & 1) ^ 1, WAIT_LIMIT)) { ok = false; break; }
+                unsigned char* a = stg + s * 2 * TILE_BYTES;
+                tc::mbar_arrive_expect_tx(&ctl->stg_full[s], bytes);
+                const int ky = (int)((ks0 + it) * TK);
+                tc::tma_load_2d(a, &tmap, &ctl->stg_full[s], ti * TB, ky);
+                if (!diag) tc::tma_load_2d(a + TILE_BYTES, &tmap, &ctl->stg_full[s], tj * TB, ky);
+                ++issued;
+            }
+            if (!ok) {
+                atomicExch(err, 1);
+                for (int it = max(0, issued - CSTG); it < issued; ++it)
+                    tc::mbar_wait_bounded(&ctl->stg_full[it % CSTG], (it / CSTG) & 1, WAIT_LIMIT);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && nsteps > 0) {
+            constexpr uint32_t idesc = tc::idesc_tf32(TB, TB);
+            bool ok = true;
+            for (int it = 0; it < nsteps; ++it) {
+                const int o = it % COP;
+                if (!tc::mbar_wait_bounded(&ctl->op_full[o], (it / COP) & 1, WAIT_LIMIT)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t a_addr = tc::smem_u32(opr + o * 2 * TILE_BYTES);
+                const uint32_t b_addr = diag ? a_addr : a_addr + TILE_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < TK / 8; ++kk)
+                    tc::mma_tf32(tmem, tc::sdesc_kmajor_sw128(a_addr + kk * 32), tc::sdesc_kmajor_sw128(b_addr + kk * 32),
+                                 idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                tc::mma_commit(&ctl->op_empty[o]);
+            }
+            if (!ok) atomicExch(err, 1);
+            tc::mma_commit(&ctl->done);
+        }
+    } else if (nsteps > 0) {
+        const int t = threadIdx.x - 64;
+        bool ok = true;
+        for (int it = 0; it < nsteps && ok; ++it) {
+            const int s = it % CSTG, o = it % COP;
+            const bool g1 = tc::mbar_wait_bounded(&ctl->stg_full[s], (it / CSTG) & 1, WAIT_LIMIT);
+            const bool g2 = g1 && tc::mbar_wait_bounded(&ctl->op_empty[o], ((it / COP) & 1) ^ 1, WAIT_LIMIT);
+            ok = __all_sync(0xffffffffu, g1 && g2);
+            if (!ok) break;
+            const float* sA = reinterpret_cast<const float*>(stg + s * 2 * TILE_BYTES);  // [32 k][128 i]
+            unsigned char* dA = opr + o * 2 * TILE_BYTES;
+            const int ntile_op = diag ? 1 : 2;
+            for (int u = 0; u < ntile_op; ++u) {
+                const float* src = sA + u * (TILE_BYTES / 4);
+                unsigned char* dst = dA + u * TILE_BYTES;
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq) {
+                    const int idx = qq * 128 + t;
+                    const int ii = idx & 127, c4 = idx >> 7;
+                    const float* col = src + (c4 * 4) * TB + ii;
+                    const float4 v = make_float4(__uint_as_float(rna_tf32_bits(col[0])),
+                                                 __uint_as_float(rna_tf32_bits(col[TB])),
+                                                 __uint_as_float(rna_tf32_bits(col[2 * TB])),
+                                                 __uint_as_float(rna_tf32_bits(col[3 * TB])));
+                    *reinterpret_cast<float4*>(dst + ii * 128 + ((c4 ^ (ii & 7)) << 4)) = v;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc::mbar_arrive(&ctl->op_full[o]);
+            tc::mbar_arrive(&ctl->stg_empty[s]);
+        }
+        if (!ok && lane == 0) atomicExch(err, 1);
+        const int q = warp & 3;
+        const bool got = __all_sync(0xffffffffu, ok && tc::mbar_wait_bounded(&ctl->done, 0, 2 * WAIT_LIMIT));
+        int e = 0;
+        if (lane == 0) e = *(volatile int*)err;
+        e = __shfl_sync(0xffffffffu, e, 0);
+        if (!got) {
+            if (lane == 0) atomicExch(err, 1);
+        } else if (e == 0) {
+            tc::tc_fence_after();
+            const int row = ti * TB + q * 32 + lane;
+            float v[32];
+#pragma unroll 1
+            for (int c = 0; c < TB / 32; ++c) {
+                __syncwarp();
+                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c * 32, v);
+                if (row < n) {
+                    const int col0 = tj * TB + c * 32;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j < n) atomicAdd(&G[(long)row * n + col0 + j], v[j]);
+                }
+            }
+        }
+    }
+    if (warp == 1 && lane == 0 && nsteps > 0) tc::mbar_wait_bounded(&ctl->done, 0, WAIT_LIMIT);
+    __syncwarp();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -217,6 +389,47 @@ bool gram_rows_tc_tf32(Ctx& c, int n, long K, const float* X, long ldx, float* G
     TT_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n * n, c.stream));
     ProfScope ps(c, "gram_tf32_tc", (double)n * (n + 1) * (double)K, 4.0 * (double)n * K + 4.0 * n * n);
     gram_tf32_kernel<<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, K, ntiles, kchunk, G, err);
+    TT_LAUNCHED(c);
+    return true;
+}
+
+}  // namespace ttgb
+
+namespace ttgb {
+
+bool gram_cols_tc_tf32(Ctx& c, int n, long m, const float* X, long ldx, float* G) {
+    if (n <= 0 || m <= 0) return false;
+    if (((uintptr_t)X & 15) != 0 || (ldx * 4) % 16 != 0 || ldx < n) return false;
+    if (m > (1L << 31) - 64 || n > (1 << 20)) return false;
+    auto encode = get_encode();
+    if (!encode) return false;
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+    cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
+    cuuint32_t box[2] = {(cuuint32_t)TB, (cuuint32_t)TK};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)X, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    const int ntiles = (n + TB - 1) / TB;
+    const int ntri = ntiles * (ntiles + 1) / 2;
+    const long ksteps = (m + TK - 1) / TK;
+    long splits = std::max<long>(1, (long)c.sm_count / ntri);
+    splits = std::min<long>(splits, std::max<long>(1, ksteps / 8));
+    const long kchunk = (ksteps + splits - 1) / splits;
+    splits = (ksteps + kchunk - 1) / kchunk;
+    const long blocks = (long)ntri * splits;
+    if (blocks > 2147483647L) return false;
+    const size_t smem = 1024 + (COP + CSTG) * 2 * TILE_BYTES + sizeof(ColCtl) + 64;
+    static bool attr = false;
+    if (!attr) {
+        TT_CUDA(cudaFuncSetAttribute(gram_cols_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    TT_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n * n, c.stream));
+    ProfScope ps(c, "gram_tf32_tc", (double)n * (n + 1) * (double)m, 4.0 * (double)n * m + 4.0 * n * n);
+    gram_cols_tf32_kernel<<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, m, ntiles, kchunk, G, c.tc_err);
     TT_LAUNCHED(c);
     return true;
 }
