@@ -40,12 +40,14 @@ __device__ void factor_diag_cta(int n, int p, const S* __restrict__ G, S* __rest
         const int r = e >> 5, k = e & 31;
         Ds[r][k] = (r < jb && k <= r) ? (C)L[(long)(j0 + r) * n + j0 + k] : C(0);
     }
+    // original diagonal (for the pivot ratio), loaded once, off the column chain
+    if (tid < jb) Di[tid][0] = (C)((double)G[(long)(j0 + tid) * n + j0 + tid] + shift);
     __syncthreads();
     const C tau_c = (C)tau;
     for (int c = 0; c < jb; ++c) {
         if (tid == 0) {
             const C piv = Ds[c][c];
-            const C orig = (C)((double)G[(long)(j0 + c) * n + j0 + c] + shift);
+            const C orig = Di[c][0];
             const bool fin = isfinite(piv);
             const bool keep = fin && piv > tau_c && piv > C(0);
             const C dc = keep ? sqrt(piv) : C(0);
@@ -90,6 +92,30 @@ __device__ void factor_diag_cta(int n, int p, const S* __restrict__ G, S* __rest
     }
 }
 
+// 16-byte vector of the compute type, and acc[0..W) += a * v
+template <class C>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using T = float4;
+    static constexpr int W = 4;
+    __device__ __forceinline__ static void fma(float a, const float4 v, float* acc) {
+        acc[0] = fmaf(a, v.x, acc[0]);
+        acc[1] = fmaf(a, v.y, acc[1]);
+        acc[2] = fmaf(a, v.z, acc[2]);
+        acc[3] = fmaf(a, v.w, acc[3]);
+    }
+};
+template <>
+struct Vec16<double> {
+    using T = double2;
+    static constexpr int W = 2;
+    __device__ __forceinline__ static void fma(double a, const double2 v, double* acc) {
+        acc[0] = ::fma(a, v.x, acc[0]);
+        acc[1] = ::fma(a, v.y, acc[1]);
+    }
+};
+
 // one 32 x 32 tile of the rank-32 update of panel p (task t)
 template <class S, class C>
 __device__ void update_tile(int n, int npad, int p, int t, int nsy, S* __restrict__ L, S* __restrict__ Tm,
@@ -121,12 +147,16 @@ __device__ void update_tile(int n, int npad, int p, int t, int nsy, S* __restric
     for (int j = 0; j < 32; ++j) acc[j] = C(0);
     const C* rowp = Pn + (long)row * 33;
     const C* colp = (syrk ? PT : TR) + C0;
+    // the broadcast row colp[c * npad + 0..31] is 16-byte aligned (C0 and npad
+    // are multiples of 32): read it with 16-byte loads
+    using V = typename Vec16<C>::T;
+    constexpr int W = Vec16<C>::W;
 #pragma unroll 2
     for (int c = 0; c < 32; ++c) {
         const C a = rowp[c];
-        const C* b = colp + (long)c * npad;
+        const V* b = reinterpret_cast<const V*>(colp + (long)c * npad);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = fma(a, b[j], acc[j]);
+        for (int j = 0; j < 32 / W; ++j) Vec16<C>::fma(a, b[j], acc + j * W);
     }
     if (rv) {
 #pragma unroll

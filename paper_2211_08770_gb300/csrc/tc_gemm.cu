@@ -180,23 +180,31 @@ gemm3_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                 // or 0 = hi, 1 = mid, 2 = lo (NS = 3)
                 const uint32_t a0 = tc::smem_u32(opr + o * OPT * TILE);
                 const uint32_t b0 = a0 + NS * TILE;
+                // each k-step starts a fresh partial sum (promoted to FP32
+                // registers by the converter warps).  Products go in order of
+                // increasing magnitude, the hi*hi ones last, so that the
+                // accumulator's rounding acts on small partial sums for as
+                // long as possible.
+                auto ad = [&](int part, int kk) { return tc::sdesc_kmajor_sw128(a0 + part * TILE + kk * 32); };
+                auto bd = [&](int part, int kk) { return tc::sdesc_kmajor_sw128(b0 + part * TILE + kk * 32); };
+                uint32_t accf = 0u;
+                if (NS == 3) {
 #pragma unroll
-                for (int kk = 0; kk < BK / 8; ++kk) {
-                    const uint32_t off = kk * 32;
-                    // each k-step starts a fresh partial sum (promoted to FP32
-                    // registers by the converter warps)
-                    const uint32_t acc0 = (kk > 0) ? 1u : 0u;
-                    auto ad = [&](int part) { return tc::sdesc_kmajor_sw128(a0 + part * TILE + off); };
-                    auto bd = [&](int part) { return tc::sdesc_kmajor_sw128(b0 + part * TILE + off); };
-                    tc::mma_tf32(dacc, ad(0), bd(0), idesc, acc0);
-                    tc::mma_tf32(dacc, ad(0), bd(1), idesc, 1u);
-                    tc::mma_tf32(dacc, ad(1), bd(0), idesc, 1u);
-                    if (NS == 3) {
-                        tc::mma_tf32(dacc, ad(0), bd(2), idesc, 1u);
-                        tc::mma_tf32(dacc, ad(2), bd(0), idesc, 1u);
-                        tc::mma_tf32(dacc, ad(1), bd(1), idesc, 1u);
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        tc::mma_tf32(dacc, ad(1, kk), bd(1, kk), idesc, accf);  // mid * mid
+                        accf = 1u;
+                        tc::mma_tf32(dacc, ad(0, kk), bd(2, kk), idesc, 1u);    // hi * lo
+                        tc::mma_tf32(dacc, ad(2, kk), bd(0, kk), idesc, 1u);    // lo * hi
                     }
                 }
+#pragma unroll
+                for (int kk = 0; kk < BK / 8; ++kk) {
+                    tc::mma_tf32(dacc, ad(0, kk), bd(1, kk), idesc, accf);      // hi * mid (or lo)
+                    accf = 1u;
+                    tc::mma_tf32(dacc, ad(1, kk), bd(0, kk), idesc, 1u);        // mid (or lo) * hi
+                }
+#pragma unroll
+                for (int kk = 0; kk < BK / 8; ++kk) tc::mma_tf32(dacc, ad(0, kk), bd(0, kk), idesc, 1u);  // hi * hi
                 tc::mma_commit(&ctl->op_empty[o]);
                 tc::mma_commit(&ctl->acc_full[ab]);
             }
