@@ -20,5 +20,5 @@ from .tt import (  # noqa: F401
 )
 from .schemes import (  # noqa: F401
     SCHEMES, tt_cgs, tt_mgs, tt_cgs2, tt_mgs2, tt_gram, tt_householder,
-    tth_vec, apply_h_vec, loss_of_orthogonality, orthogonalize,
+    tth_vec, apply_h_vec, loss_of_orthogonality, orthogonalize, gs_step,
 )

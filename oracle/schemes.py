@@ -231,6 +231,35 @@ def tt_householder(A, delta, policy="paper", sign_rule="stable", return_u=False)
     return Q, R, cnt.n
 
 
+def gs_step(a, Q, delta, scheme="cgs2", policy="paper"):
+    """One outer iteration of Algorithms 1-4 for the vector a against the
+    orthonormal list Q (the step an Arnoldi-type caller issues per new
+    vector): the projection loop (once for CGS/MGS, twice for CGS2/MGS2),
+    rounding as the policy says, then normalisation.  Returns (q, col, n)
+    with col[j] = R(j, i) for j < i = len(Q) (both passes summed), col[i] =
+    ||p|| and n the number of roundings."""
+    modified = scheme in ("mgs", "mgs2")
+    passes = 2 if scheme in ("cgs2", "mgs2") else 1
+    i = len(Q)
+    col = np.zeros(i + 1)
+    cnt = _Counter(delta)
+    p_prev = a
+    for _ in range(passes):
+        p = p_prev
+        rk = np.zeros(i)
+        for j in range(i):
+            rk[j] = tt_dot(p if modified else p_prev, Q[j])
+            p = _axpy(p, -rk[j], Q[j])
+            if policy == "every_update":
+                p = cnt.round(p)
+        if policy == "paper" or i == 0:
+            p = cnt.round(p)
+        col[:i] += rk
+        p_prev = p
+    col[i], q = _normalize(p_prev)
+    return q, col, cnt.n
+
+
 def loss_of_orthogonality(Q):
     """||I - Q^T Q||_2 with (Q^T Q)(i,j) = <q_i, q_j> from TT dots
     (Section 3.4, eq. LOO; Section 4.1)."""

@@ -178,3 +178,54 @@ def test_tt_loo_orders_in_delta():
         assert loo[s] < 1e2 * delta, (s, loo[s])
     assert loo["mgs"] < 1e2 * delta * kappa
     assert loo["cgs"] > loo["mgs2"] and loo["gram"] > loo["mgs2"]
+
+
+@pytest.mark.parametrize("scheme", ["cgs", "mgs", "cgs2", "mgs2"])
+@pytest.mark.parametrize("policy", ["paper", "every_update"])
+def test_gs_step_iterated_is_the_scheme(scheme, policy):
+    # one outer iteration applied to a_1..a_m in turn is Algorithms 1-4
+    A = random_tts(31, 5, 4, 5, 2)
+    Q, R, n = O.orthogonalize(scheme, A, 1e-10, policy)
+    Qs, nsum = [], 0
+    for i, a in enumerate(A):
+        q, col, k = O.gs_step(a, Qs, 1e-10, scheme, policy)
+        assert np.array_equal(col, R[: i + 1, i])
+        for c1, c2 in zip(q, Q[i]):
+            assert np.array_equal(c1, c2)
+        Qs.append(q)
+        nsum += k
+    assert nsum == n
+
+
+@pytest.mark.parametrize("scheme", ["cgs", "mgs", "cgs2", "mgs2"])
+def test_gs_step_against_an_orthonormal_basis(scheme):
+    # exact orthonormal basis: the coefficients are the projections <a, q_j>,
+    # the new vector is a unit vector orthogonal to the basis (up to delta)
+    from ttinputs import orthonormal_basis
+    rng = np.random.default_rng(32)
+    n = [6, 5, 4, 4]
+    Q = orthonormal_basis(rng, n, 9, 3)
+    G = np.array([[O.tt_dot(a, b) for b in Q] for a in Q])
+    assert np.abs(G - np.eye(9)).max() < 1e-13
+    a = random_tt(rng, n, [1, 3, 4, 3, 1])
+    delta = 1e-10
+    q, col, k = O.gs_step(a, Q, delta, scheme)
+    proj = np.array([O.tt_dot(a, qj) for qj in Q])
+    na = O.tt_norm(a)
+    assert np.abs(col[:9] - proj).max() <= 1e-12 * na
+    assert k == (2 if scheme.endswith("2") else 1)
+    assert abs(O.tt_norm(q) - 1.0) < 1e-12
+    assert max(abs(O.tt_dot(q, qj)) for qj in Q) < 10 * delta * na / col[9]
+    # dense check: a = sum_j col_j q_j + col_9 q up to the rounding error
+    full = sum(c * O.tt_full(v) for c, v in zip(col, Q + [q]))
+    assert np.linalg.norm(full - O.tt_full(a)) <= 2 * delta * na
+
+
+def test_gs_step_first_vector():
+    a = random_tts(33, 1, 4, 5, 3)[0]
+    q, col, k = O.gs_step(a, [], 1e-3, "mgs2")
+    y = O.tt_round(O.tt_round(a, 1e-3), 1e-3)
+    assert k == 2 and col.shape == (1,)
+    assert col[0] == O.tt_norm(y)
+    for c1, c2 in zip(q, O.tt_scale(y, 1.0 / col[0])):
+        assert np.array_equal(c1, c2)

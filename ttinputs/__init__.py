@@ -117,3 +117,64 @@ def cfg_serving_request(rng, k_range=(1, 64), d_range=(6, 12), n_choices=(32, 64
     nn, ranks = rank_profile(d, n, r)
     return dict(k=k, d=d, n=n, r=r, delta=delta,
                 cores=random_tt(rng, nn, ranks, scale="unit-core"))
+
+
+def orthonormal_basis(rng, n, k, rb):
+    """k TT tensors with modes n (len(n) >= 3), orthonormal by construction:
+    q_(a,b) = u_a (x) v_b (x) w_(a,b), u_a and v_b columns of random
+    orthogonal matrices over modes 1 and 2 (k <= n_1 n_2), w a TT over modes
+    3..d of rank rb whose cores have orthonormal left unfoldings and whose
+    last core is a unit vector, so ||w|| = 1 and <q_i, q_j> = delta_ij.
+    TT ranks of each q: [1, 1, 1, rb, ..., rb, 1]."""
+    d = len(n)
+    if d < 3 or k > n[0] * n[1]:
+        raise ValueError("need d >= 3 and k <= n_1 n_2")
+    U = np.linalg.qr(rng.standard_normal((n[0], n[0])))[0]
+    V = np.linalg.qr(rng.standard_normal((n[1], n[1])))[0]
+    out = []
+    for j in range(k):
+        a, b = j % n[0], j // n[0]
+        cores = [U[:, a].reshape(1, n[0], 1), V[:, b].reshape(1, n[1], 1)]
+        _, ranks = rank_profile(d - 2, n[2:], rb)
+        for m in range(2, d):
+            rl, rr = ranks[m - 2], ranks[m - 1]
+            M = rng.standard_normal((rl * n[m], rr))
+            Qm = np.linalg.qr(M)[0] if m < d - 1 else M / np.linalg.norm(M)
+            cores.append(Qm.reshape(rl, n[m], rr))
+        out.append(cores)
+    return out
+
+
+def cfg_serving(seed=0, count=256, k_range=(1, 64), d_range=(6, 12), n_choices=(32, 64),
+                r_range=(10, 60), deltas=(1e-5, 1e-7), basis_rank=4, orth_fraction=0.5):
+    """The serving workload: resident bases, one per (d, n) pair, of
+    k_range[1] orthonormal vectors (orthonormal_basis, rank basis_rank), and
+    count requests: with probability orth_fraction an orthogonalization step
+    of a new rank-r tensor against the first k vectors of the basis of its
+    (d, n), else a rounding of a rank-r tensor with graded bonds (columns
+    of each core scaled over eight decades, so that delta truncates).  Returns (bases: {(d, n): cores list}, requests: list of dicts
+    with kind, d, n, r, k, delta, scheme, cores)."""
+    rng = np.random.default_rng(seed)
+    bases = {}
+    reqs = []
+    for _ in range(count):
+        q = cfg_serving_request(rng, k_range, d_range, n_choices, r_range, deltas)
+        key = (q["d"], q["n"])
+        if key not in bases:
+            bases[key] = orthonormal_basis(np.random.default_rng([seed, q["d"], q["n"]]),
+                                           [q["n"]] * q["d"], k_range[1], basis_rank)
+        if rng.random() < orth_fraction:
+            q["kind"] = "orth"
+            q["scheme"] = str(rng.choice(["cgs2", "mgs2"]))
+        else:
+            q["kind"] = "round"
+            # graded bonds: the j-th column of every core scaled by
+            # 10^(-8 j / r), so the bond singular values spread over about
+            # eight decades and the rounding at delta truncates them
+            for c in q["cores"][:-1]:
+                c *= 10.0 ** (-8.0 * np.arange(c.shape[2]) / max(c.shape[2], 1))
+            q["scheme"] = None
+            q["k"] = 0
+        reqs.append(q)
+    return bases, reqs
+
