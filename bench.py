@@ -299,6 +299,10 @@ def run_ours(args):
                             "steps": args.fp64_steps, "output_ranks": f["ranks"]}
         out["speedup_vs_fp64"] = value / fv
     out["e2e"] = time_e2e(prec, args.e2e_steps)
+    if args.batch_count > 0:
+        out["batched"] = time_batched(T, local, prec, args.batch_count, not args.no_fp64)
+    if args.serve_count > 0:
+        out["serve"] = time_serve(T, local, prec, args.serve_count, args.serve_rate, args.serve_workers)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline_sample(al, xs, budget_s=args.cpu_budget)
     if dist:
@@ -306,6 +310,82 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def time_batched(T, dev, prec, count, with_fp64):
+    """Batched rounding of `count` uneven instances (orders 4-12, modes
+    16-128, ranks 8-256, unit-scaled Gaussian cores, delta 1e-6): the lane
+    count is tuned on one warm pass per candidate, then one timed pass."""
+    import torch
+    from ttinputs import cfg_batched
+    xs = cfg_batched(0, count=count)
+    res = {"workload": "batched rounding, %d instances: d 4-12, n 16-128, r 8-256, delta 1e-6" % count,
+           "unit": "roundings/s", "count": count}
+
+    def run(precision, lanes_list):
+        ctx = T.Ctx(dev, precision)
+        hs = [T.tt_tensor_create(ctx, x) for x in xs]
+        torch.cuda.synchronize()
+        rates = {}
+        for lanes in lanes_list:
+            ctx.concurrency = lanes
+            t0 = time.perf_counter()
+            ys = T.tt_round_batched(ctx, hs, [DELTA] * count)
+            torch.cuda.synchronize()
+            rates[lanes] = count / (time.perf_counter() - t0)
+            for y in ys:
+                y.free()
+        best = max(rates, key=rates.get)
+        ctx.concurrency = best
+        ctx.reset_stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ys = T.tt_round_batched(ctx, hs, [DELTA] * count)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = ctx.stats()
+        for y in ys + hs:
+            y.free()
+        ctx.close()
+        return dict(value=count / dt, seconds=dt, lanes=best, tuning={str(k): round(v, 2) for k, v in rates.items()},
+                    gpu_launches=int(st["kernel_launches"]), host_syncs=int(st["host_syncs"]),
+                    peak_bytes=int(st["peak_bytes"]))
+
+    m = run(prec, (4, 8, 16, 32))
+    res.update(m)
+    if with_fp64:
+        f = run("fp64", (m["lanes"],))
+        res["fp64_value"] = f["value"]
+        res["speedup_vs_fp64"] = m["value"] / f["value"]
+    return res
+
+
+def time_serve(T, dev, prec, count, rate, workers):
+    """Poisson arrivals of roundings and CGS2/MGS2 outer iterations against
+    resident orthonormal bases (orders 6-12, modes 32/64, ranks 10-60, basis
+    size 1-64, delta 1e-5/1e-7)."""
+    from paper_2211_08770_gb300.serve import poisson_load
+    from ttinputs import cfg_serving
+    bases, reqs = cfg_serving(0, count=count)
+    ctx = T.Ctx(dev, prec)
+    srv = T.Server(ctx, workers=workers)
+    bids = {}
+    for key, B in bases.items():
+        hs = [T.tt_tensor_create(ctx, q) for q in B]
+        bids[key] = srv.add_basis(hs)
+        for h in hs:
+            h.free()
+    # warm the lanes (kernels, pools) with a few requests outside the measurement
+    poisson_load(srv, ctx, reqs[: min(8, count)], rate=rate, basis_ids=bids, seed=99)
+    out = poisson_load(srv, ctx, reqs, rate=rate, basis_ids=bids, seed=1)
+    st = srv.stats()
+    srv.close()
+    ctx.close()
+    out.update(workload="Poisson %.0f req/s: rounding or CGS2/MGS2 step vs resident basis; d 6-12, n 32/64, "
+                        "r 10-60, k 1-64, delta 1e-5/1e-7" % rate,
+               workers=workers, footprint_peak=int(st["footprint_peak"]), gpu_launches=int(st["kernel_launches"]),
+               roundings=int(st["roundings"]), errors=len(out["errors"]))
+    return out
 
 
 def _src_hash():
@@ -330,6 +410,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=128)
+    ap.add_argument("--serve-count", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=100.0)
+    ap.add_argument("--serve-workers", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

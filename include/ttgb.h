@@ -45,8 +45,9 @@ typedef enum {
     TT_ERR_NOT_SPD = 4,    /* TT-Gram: Cholesky of the Gram matrix failed */
     TT_ERR_BREAKDOWN = 5,  /* zero vector where a scheme normalises */
     TT_ERR_NONFINITE = 6,  /* NaN or Inf met in a result */
-    TT_ERR_TIMEOUT = 7,    /* a bounded device wait ran out */
-    TT_ERR_CUDA = 8        /* a CUDA runtime call failed */
+    TT_ERR_TIMEOUT = 7,    /* a bounded device wait ran out, or a server wait timed out */
+    TT_ERR_CUDA = 8,       /* a CUDA runtime call failed */
+    TT_ERR_CANCELLED = 9   /* a served request was cancelled before it started */
 } tt_status;
 
 /* Arithmetic of a context.
@@ -196,11 +197,29 @@ tt_status tt_norm(tt_ctx* ctx, const tt_tensor* x, double* out);
 tt_status tt_round(tt_ctx* ctx, const tt_tensor* x, double delta,
                    tt_tensor** out, double* err_est);
 
-/* Rounds count independent tensors, each at its own delta[i], reusing one
- * workspace and overlapping their work on the context's stream.  out[i] is
- * set for every i, or all are NULL on error. */
+/* Rounds count independent tensors, each at its own delta[i] (TT-round of
+ * Section 2.3 applied to every x[i]; the paper has no batched form).  The
+ * roundings run concurrently on the context's lanes (tt_ctx_set_concurrency):
+ * child contexts with their own non-blocking streams, each driven by one
+ * host thread (the calling thread drives lane 0), taking instances in
+ * decreasing order of estimated work.  Lanes start after the work queued so
+ * far on the context's stream and the stream continues after all of them,
+ * so the call is stream-ordered like tt_round.  Each out[i] equals what
+ * tt_round(ctx, x[i], delta[i]) returns (same kernels and decisions; lanes
+ * share no workspace).  Device bytes of every lane count against the
+ * context's HBM budget.  out[i] is set for every i, or all are NULL on
+ * error (the first error seen is returned; the other lanes stop taking new
+ * instances).  count = 0 is a no-op. */
 tt_status tt_round_batched(tt_ctx* ctx, int count, const tt_tensor* const* x,
                            const double* delta, tt_tensor** out);
+
+/* Number of lanes tt_round_batched uses (1 = sequential on the context's
+ * stream; default 8; at most TT_MAX_LANES).  Lanes are created on first use
+ * and live until the context is destroyed.  TT_ERR_ARG outside [1,
+ * TT_MAX_LANES]. */
+#define TT_MAX_LANES 64
+tt_status tt_ctx_set_concurrency(tt_ctx* ctx, int lanes);
+int       tt_ctx_get_concurrency(const tt_ctx* ctx);
 
 /* ---- orthogonalization (Section 3) ------------------------------------ */
 
@@ -290,6 +309,86 @@ tt_status tt_set_sign_rule(tt_ctx* ctx, tt_sign_rule rule);
 tt_status tt_dot_f64_noalloc(void* cuda_stream, int d, const int* n, const int* rx, const int* ry,
                              const double* const* x_cores, const double* const* y_cores,
                              double* result_dev);
+
+/* ---- request server ---------------------------------------------------- */
+
+/* A request loop over one context (the paper has no counterpart: it is the
+ * serving form of TT-round, Section 2.3, and of one outer iteration of the
+ * Gram-Schmidt schemes, Algorithms 1-4, as an Arnoldi-type caller issues
+ * them).  Requests of uneven order, mode size and rank are submitted at any
+ * time from any host thread and run concurrently on `workers` lanes (child
+ * contexts with their own non-blocking streams, one host thread each).
+ * Admission is by device footprint: every request carries an upper bound
+ * of the bytes it can hold at once (rounding workspace, output, the
+ * concatenated sums of an orthogonalization step); a request starts only
+ * while the admitted bounds sum to at most the footprint budget.  The
+ * oldest waiting request keeps its place: a later one may start first only
+ * if it fits beside the oldest one's bound.  Resident bases are copied to
+ * the device once (tt_server_add_basis) and shared by all requests.
+ *
+ * Inputs belong to the server's context and must stay alive and unchanged
+ * until their request is done; work queued on the context's stream before
+ * tt_server_submit is complete before the request starts.  A result is
+ * complete on the device when tt_server_wait returns it and belongs to the
+ * caller (tt_tensor_free).  The context must not be destroyed before the
+ * server.  Host faults are reported, never forced onto the GPU: a request
+ * whose bound exceeds the budget is refused at submit (TT_ERR_OOM), a
+ * queued one can be cancelled (TT_ERR_CANCELLED), a wait can time out
+ * (TT_ERR_TIMEOUT, the ticket stays valid). */
+typedef struct tt_server tt_server;
+
+typedef enum { TT_REQ_ROUND = 0, TT_REQ_ORTH_STEP = 1 } tt_request_kind;
+
+typedef struct {
+    uint64_t submitted, completed, failed, cancelled, refused;
+    uint64_t queued, running;          /* now */
+    uint64_t footprint_in_use;         /* sum of the bounds of running requests */
+    uint64_t footprint_peak;
+    uint64_t footprint_budget;
+    uint64_t roundings, kernel_launches, host_syncs;  /* work of completed requests */
+} tt_server_stats;
+
+/* workers in [1, TT_MAX_LANES]; footprint_budget in bytes (0: the
+ * context's HBM budget, or no limit if it has none). */
+tt_status tt_server_create(tt_ctx* ctx, int workers, size_t footprint_budget, tt_server** out);
+
+/* Copies k >= 1 orthonormal TT tensors of equal modes into a resident
+ * basis; *basis_id receives its handle.  The copies count against the
+ * context's HBM budget.  Orthonormality is the caller's promise (Algorithms
+ * 1-4 project on Q assuming Q^T Q = I). */
+tt_status tt_server_add_basis(tt_server* s, int k, const tt_tensor* const* q, int* basis_id);
+
+/* Queues a request and returns at once with *ticket.
+ * TT_REQ_ROUND: TT-round(x, delta); basis_id, k and scheme are ignored.
+ * TT_REQ_ORTH_STEP: one outer iteration of `scheme` (TT_CGS, TT_MGS, TT_CGS2
+ * or TT_MGS2, rounding once per pass as in the paper's listings) for x
+ * against the first k vectors of basis basis_id: the result is the new
+ * normalised basis vector and the coefficients R(0..k, k+1).
+ * TT_ERR_ARG / TT_ERR_SHAPE for bad arguments or modes that differ from the
+ * basis; TT_ERR_OOM when the request's footprint bound exceeds the budget. */
+tt_status tt_server_submit(tt_server* s, tt_request_kind kind, const tt_tensor* x, double delta, int basis_id,
+                           int k, tt_scheme scheme, uint64_t* ticket);
+
+/* Waits up to timeout_ms (< 0: no limit) for a request.  Returns the
+ * request's own status (its message in tt_last_error), or TT_ERR_TIMEOUT
+ * (ticket still valid), or TT_ERR_ARG for an unknown ticket.  Once a status
+ * other than TT_ERR_TIMEOUT is returned the ticket is consumed.  out (may
+ * be NULL: the result is then freed) receives the result; coef (may be
+ * NULL) up to coef_cap doubles R(0..k, k+1) of an orthogonalization step;
+ * times (may be NULL) 3 doubles: submit, start and finish instants in
+ * seconds of the host's monotonic clock (CLOCK_MONOTONIC). */
+tt_status tt_server_wait(tt_server* s, uint64_t ticket, int timeout_ms, tt_tensor** out, double* coef,
+                         int coef_cap, double* times);
+
+/* Removes a queued request (its wait then returns TT_ERR_CANCELLED).
+ * TT_ERR_ARG if the ticket is unknown or the request has started. */
+tt_status tt_server_cancel(tt_server* s, uint64_t ticket);
+
+tt_status tt_server_get_stats(tt_server* s, tt_server_stats* out);
+
+/* Cancels queued requests, waits for running ones, frees unclaimed results
+ * and the bases, and stops the workers. */
+void tt_server_destroy(tt_server* s);
 
 /* ---- diagnostics ------------------------------------------------------- */
 

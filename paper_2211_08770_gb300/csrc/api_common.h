@@ -29,6 +29,8 @@ tt_dtype storage_of(tt_precision p);
 void validate_shape(int d, const int* n, const int* r);
 tt_tensor* new_tensor(tt_ctx* ctx, int d, const int* n, const int* r);
 void free_tensor(tt_tensor* t);
+// drops one reference to a context (deleted with its last reference)
+void drop_ctx_ref(tt_ctx* c);
 tt_tensor* copy_tensor(tt_ctx* ctx, const tt_tensor* x);
 void check_same_modes(const tt_tensor* a, const tt_tensor* b);
 void check_tensor(tt_ctx* ctx, const tt_tensor* x);
@@ -37,6 +39,16 @@ tt_tensor* scale_internal(tt_ctx* ctx, const tt_tensor* x, double alpha);
 void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out);
 tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est);
 double norm_internal(tt_ctx* ctx, const tt_tensor* x);
+// moves a tensor made on a lane to its root (see get_lanes)
+void rehome(tt_tensor* t, Ctx& root);
+// One outer iteration of Algorithms 1-4 (scheme TT_CGS, TT_MGS, TT_CGS2 or
+// TT_MGS2) for a against the orthonormal Q[0..k-1]: returns the new basis
+// vector; col[0..k] receives R(0..k, k).
+tt_tensor* orth_step_internal(tt_ctx* ctx, tt_scheme scheme, double delta, tt_round_policy policy,
+                              const tt_tensor* a, int k, const tt_tensor* const* Q, double* col, int* nrounds);
+// device bytes a rounding of x may hold at once: workspace plus output
+size_t round_footprint(const tt_tensor* x, tt_precision prec);
+void round_batched_internal(tt_ctx* ctx, int count, const tt_tensor* const* x, const double* delta, tt_tensor** out);
 
 // RAII owner for tensors created inside drivers
 struct TensorGuard {

@@ -26,17 +26,23 @@ void set_last_error(const std::string& s) { g_last_error = s; }
 void* Ctx::alloc(size_t bytes) {
     if (bytes == 0) bytes = 256;
     bytes = (bytes + 255) & ~size_t(255);
-    if (budget && stats.bytes_in_use + bytes > budget)
-        throw_status(TT_ERR_OOM, "HBM budget exceeded (" + std::to_string(stats.bytes_in_use + bytes) + " > " +
-                                     std::to_string(budget) + " bytes)");
+    Ctx& a = root ? *root : *this;  // lanes draw on their root's budget
+    {
+        std::lock_guard<std::mutex> lk(a.acct_mu);
+        if (a.budget && a.stats.bytes_in_use + bytes > a.budget)
+            throw_status(TT_ERR_OOM, "HBM budget exceeded (" + std::to_string(a.stats.bytes_in_use + bytes) +
+                                         " > " + std::to_string(a.budget) + " bytes)");
+        a.stats.bytes_in_use += bytes;
+        a.stats.peak_bytes = std::max<uint64_t>(a.stats.peak_bytes, a.stats.bytes_in_use);
+    }
     void* p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, bytes, stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        std::lock_guard<std::mutex> lk(a.acct_mu);
+        a.stats.bytes_in_use -= std::min<uint64_t>(a.stats.bytes_in_use, bytes);
         throw_status(TT_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
-    stats.bytes_in_use += bytes;
-    stats.peak_bytes = std::max<uint64_t>(stats.peak_bytes, stats.bytes_in_use);
     return p;
 }
 
@@ -45,7 +51,9 @@ void Ctx::release(void* p, size_t bytes) {
     if (bytes == 0) bytes = 256;
     bytes = (bytes + 255) & ~size_t(255);
     cudaFreeAsync(p, stream);
-    stats.bytes_in_use -= std::min<uint64_t>(stats.bytes_in_use, bytes);
+    Ctx& a = root ? *root : *this;
+    std::lock_guard<std::mutex> lk(a.acct_mu);
+    a.stats.bytes_in_use -= std::min<uint64_t>(a.stats.bytes_in_use, bytes);
 }
 
 void Ctx::sync() {
@@ -72,6 +80,11 @@ cudaEvent_t Ctx::event() {
 }
 
 Ctx::~Ctx() {
+    for (Ctx* l : lanes) {
+        cudaStreamSynchronize(l->stream);
+        delete static_cast<tt_ctx*>(l);  // lanes are allocated as tt_ctx
+    }
+    if (owns_stream && stream) cudaStreamDestroy(stream);
     for (auto& r : recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -91,13 +104,16 @@ void check_tc_error(Ctx& c) {
 }
 
 ProfScope::ProfScope(Ctx& ctx, const char* name, double fl, double by) : c(ctx), flops(fl), bytes(by) {
-    if (!c.prof) return;
+    // only the outermost scope records: launches made inside another
+    // instrumented call (the GEMMs of the blocked Cholesky) count for it
+    if (c.prof_nest++ > 0 || !c.prof) return;
     fam = c.family(name);
     a = c.event();
     TT_CUDA(cudaEventRecord(a, c.stream));
 }
 
 ProfScope::~ProfScope() {
+    c.prof_nest--;
     if (!a) return;
     cudaEvent_t b = c.event();
     cudaEventRecord(b, c.stream);
@@ -168,7 +184,10 @@ void check_same_modes(const tt_tensor* a, const tt_tensor* b) {
 
 void check_tensor(tt_ctx* ctx, const tt_tensor* x) {
     if (!x) throw_status(TT_ERR_ARG, "NULL tensor");
-    if (x->ctx != ctx) throw_status(TT_ERR_ARG, "tensor belongs to another context");
+    // a lane may read its root's tensors (the caller orders the streams)
+    const Ctx* hx = x->ctx->root ? x->ctx->root : static_cast<const Ctx*>(x->ctx);
+    const Ctx* hc = ctx->root ? ctx->root : static_cast<const Ctx*>(ctx);
+    if (hx != hc) throw_status(TT_ERR_ARG, "tensor belongs to another context");
 }
 
 tt_tensor* copy_tensor(tt_ctx* ctx, const tt_tensor* x) {
@@ -383,11 +402,19 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     // TTGB_NO_TENSOR_CORES=1 keeps TT_MIXED_TF32 contexts on the CUDA-core Gram
     const char* no_tc = getenv("TTGB_NO_TENSOR_CORES");
     if (no_tc && no_tc[0] == '1') c->use_tc = false;
-    // TTGB_TC_GEMM=0 keeps the core-producing GEMMs on CUDA cores; =2 selects
-    // the two-part split (3 products, faster, ~2^-22 per product)
+    // TTGB_TC_GEMM=3 moves the core-producing GEMMs onto the tensor cores
+    // (three-part split, 6 products); =2 the two-part split (3 products,
+    // ~2^-22 per product); unset or 0 keeps them on CUDA cores
     const char* tg = getenv("TTGB_TC_GEMM");
-    if (tg && tg[0] == '0') c->use_tc_gemm = false;
-    if (tg && tg[0] == '2') c->tc_gemm_split = 2;
+    if (tg && tg[0] == '3') c->use_tc_gemm = true;
+    if (tg && tg[0] == '2') {
+        c->use_tc_gemm = true;
+        c->tc_gemm_split = 2;
+    }
+    // TTGB_CHOL_NB fixes the block size of the Cholesky factorizations (a
+    // multiple of 32; 0 or unset: chosen per order by timing)
+    const char* nb = getenv("TTGB_CHOL_NB");
+    if (nb) c->chol_nb = std::max(0, atoi(nb));
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
@@ -664,6 +691,7 @@ const char* tt_status_str(tt_status s) {
         case TT_ERR_NONFINITE: return "TT_ERR_NONFINITE";
         case TT_ERR_TIMEOUT: return "TT_ERR_TIMEOUT";
         case TT_ERR_CUDA: return "TT_ERR_CUDA";
+        case TT_ERR_CANCELLED: return "TT_ERR_CANCELLED";
     }
     return "TT_ERR_UNKNOWN";
 }

@@ -57,8 +57,7 @@ struct Rounder {
         auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
         const size_t core_b = al(cap * sizeof(T));
         const size_t small_b = al(rr * sizeof(T));
-        ws_bytes = (d + 1) * core_b + 11 * small_b + al(2 * rr * sizeof(double)) + al(rmax * sizeof(double)) +
-                   al(16 * sizeof(double)) + al(st_cap * sizeof(CholStatus));
+        ws_bytes = workspace_bytes(d, rmax, cap, sizeof(T));
         ws = (char*)ctx->alloc(ws_bytes);
         char* p = ws;
         core.resize(d);
@@ -80,6 +79,15 @@ struct Rounder {
                                     c->stream));
     }
     ~Rounder() { if (ws) c->release(ws, ws_bytes); }
+
+    // bytes of the workspace carved in the constructor (d + 1 core buffers,
+    // eleven r x r matrices, Jacobi work, singular values, scalars, statuses)
+    static size_t workspace_bytes(int d, int rmax, size_t cap, size_t es) {
+        auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+        const size_t rr = (size_t)rmax * rmax;
+        return (d + 1) * al(cap * es) + 11 * al(rr * es) + al(2 * rr * sizeof(double)) + al(rmax * sizeof(double)) +
+               al(16 * sizeof(double)) + al((16 * d + 16) * sizeof(CholStatus));
+    }
 
     CholStatus* next_st() {
         if (nst >= st_cap) throw_status(TT_ERR_ARG, "internal: status slots exhausted");
@@ -147,8 +155,12 @@ struct Rounder {
             CholStatus h = read_st(s0);
             if (h.ndrop == 0 && h.min_ratio >= ratio_fast) {
                 apply(rows, a, K, X, Ti[0]);
-                gram_into(rows, true, a, K, X);
-                chol_inv<T, T>(*c, a, G, Lf[1], Ti[1], 0.0, 8.0 * ug_fast * sq, next_st());
+                // the second pass in the storage precision: a TF32 Gram of
+                // the nearly orthonormal X would leave an orthogonality
+                // defect of about u_tf32 / sqrt(K), far above FP32 level
+                // for short unfoldings
+                gram_into(rows, false, a, K, X);
+                chol_inv<T, T>(*c, a, G, Lf[1], Ti[1], 0.0, drop_fb, next_st());
                 apply(rows, a, K, X, Ti[1]);
                 mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Lp, a);
                 o.npass = 2;
@@ -301,12 +313,19 @@ struct Rounder {
         }
     }
 
+    // one synchronization: the device wait flag (tensor-core and Jacobi
+    // kernels) and every factorization status of this rounding
     void check_all_status() {
-        if (tc) check_tc_error(*c);
-        if (nst == 0) return;
         std::vector<CholStatus> hs(nst);
-        TT_CUDA(cudaMemcpyAsync(hs.data(), st, nst * sizeof(CholStatus), cudaMemcpyDeviceToHost, c->stream));
+        int flag = 0;
+        TT_CUDA(cudaMemcpyAsync(&flag, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        if (nst)
+            TT_CUDA(cudaMemcpyAsync(hs.data(), st, nst * sizeof(CholStatus), cudaMemcpyDeviceToHost, c->stream));
         c->sync();
+        if (flag) {
+            TT_CUDA(cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream));
+            throw_status(TT_ERR_TIMEOUT, "a bounded device wait ran out");
+        }
         for (auto& h : hs)
             if (h.nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in a Gram matrix");
     }
@@ -364,6 +383,20 @@ double norm_t(tt_ctx* ctx, const tt_tensor* x) {
 
 }  // namespace
 
+size_t round_footprint(const tt_tensor* x, tt_precision prec) {
+    const size_t es = prec == TT_FP64 ? 8 : 4;
+    int rmax = 1;
+    size_t cap = 1, out = 0;
+    for (int k = 0; k <= x->d; ++k) rmax = std::max(rmax, x->r[k]);
+    for (int k = 0; k < x->d; ++k) {
+        cap = std::max(cap, x->core_elems(k));
+        out += (x->core_elems(k) * es + 255) & ~size_t(255);  // ranks never grow
+    }
+    const size_t ws = es == 8 ? Rounder<double>::workspace_bytes(x->d, rmax, cap, es)
+                              : Rounder<float>::workspace_bytes(x->d, rmax, cap, es);
+    return ws + out;
+}
+
 tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est) {
     check_tensor(ctx, x);
     if (!(delta >= 0.0) || !isfinite(delta)) throw_status(TT_ERR_ARG, "delta must be finite and >= 0");
@@ -401,21 +434,6 @@ tt_status tt_norm(tt_ctx* ctx, const tt_tensor* x, double* out) {
     TT_API_BEGIN
     if (!ctx || !out) throw_status(TT_ERR_ARG, "NULL argument");
     *out = norm_internal(ctx, x);
-    TT_API_END
-}
-
-tt_status tt_round_batched(tt_ctx* ctx, int count, const tt_tensor* const* x, const double* delta, tt_tensor** out) {
-    TT_API_BEGIN
-    if (!ctx || !out || count < 0 || (count > 0 && (!x || !delta))) throw_status(TT_ERR_ARG, "bad arguments");
-    for (int i = 0; i < count; ++i) out[i] = nullptr;
-    std::vector<tt_tensor*> res(count, nullptr);
-    try {
-        for (int i = 0; i < count; ++i) res[i] = round_internal(ctx, x[i], delta[i], nullptr);
-    } catch (...) {
-        for (auto* t : res) free_tensor(t);
-        throw;
-    }
-    for (int i = 0; i < count; ++i) out[i] = res[i];
     TT_API_END
 }
 

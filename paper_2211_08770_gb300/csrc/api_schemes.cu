@@ -56,54 +56,50 @@ tt_tensor* normalize(Driver& D, const tt_tensor* p, double* nrm_out) {
     return scale_internal(D.c, p, 1.0 / nrm);
 }
 
-// Algorithm 1 (modified = false) and Algorithm 2 (modified = true)
-void gs(Driver& D, int m, const tt_tensor* const* A, std::vector<TensorGuard>& Q, double* R, bool modified) {
-    for (int i = 0; i < m; ++i) {
+// One outer iteration of Algorithms 1-4: orthogonalizes a against the
+// orthonormal Q[0..i-1] and normalises it.  col[0..i-1] receives the
+// projection coefficients R(j, i) (the two passes summed when twice, as
+// R = R^(1) + R^(2) in Algorithms 3 and 4), col[i] the norm R(i, i).
+// Rounding follows the policy: TT_ROUND_PAPER rounds once per pass (and the
+// first vector, i = 0, is rounded in both policies); TT_ROUND_EVERY_UPDATE
+// after every axpy.
+tt_tensor* gs_step(Driver& D, const tt_tensor* a, int i, const tt_tensor* const* Q, double* col, bool modified,
+                   bool twice) {
+    for (int j = 0; j <= i; ++j) col[j] = 0.0;
+    Cur prev;
+    prev.p = a;
+    for (int k = 0; k < (twice ? 2 : 1); ++k) {
         Cur p;
-        p.p = A[i];
+        p.p = prev.p;
         for (int j = 0; j < i; ++j) {
-            const double rji = D.dot(modified ? p.p : A[i], Q[j].get());
-            R[j + (size_t)i * m] = rji;
-            p.set_owned(D.axpy(p.p, -rji, Q[j].get()));
+            const double rji = D.dot(modified ? p.p : prev.p, Q[j]);
+            col[j] += rji;
+            p.set_owned(D.axpy(p.p, -rji, Q[j]));
             if (D.pol == TT_ROUND_EVERY_UPDATE) p.set_owned(D.round(p.p));
         }
         if (D.pol == TT_ROUND_PAPER || i == 0) p.set_owned(D.round(p.p));
-        double nrm;
-        Q[i].reset(normalize(D, p.p, &nrm));
-        R[i + (size_t)i * m] = nrm;
+        // prev <- p (move ownership)
+        if (p.own.get()) {
+            prev.own = std::move(p.own);
+            prev.p = prev.own.get();
+        } else {
+            prev.p = p.p;
+        }
     }
+    double nrm;
+    tt_tensor* q = normalize(D, prev.p, &nrm);
+    col[i] = nrm;
+    return q;
 }
 
-// Algorithm 3 (modified = false) and Algorithm 4 (modified = true)
-void gs2(Driver& D, int m, const tt_tensor* const* A, std::vector<TensorGuard>& Q, double* R, bool modified) {
-    std::vector<double> R1((size_t)m * m, 0.0), R2((size_t)m * m, 0.0);
+// Algorithms 1-4 (modified: MGS variants; twice: the reorthogonalized ones)
+void gs(Driver& D, int m, const tt_tensor* const* A, std::vector<TensorGuard>& Q, double* R, bool modified,
+        bool twice) {
+    std::vector<const tt_tensor*> qp(m, nullptr);
     for (int i = 0; i < m; ++i) {
-        Cur prev;
-        prev.p = A[i];
-        for (int k = 0; k < 2; ++k) {
-            std::vector<double>& Rk = (k == 0) ? R1 : R2;
-            Cur p;
-            p.p = prev.p;
-            for (int j = 0; j < i; ++j) {
-                const double rji = D.dot(modified ? p.p : prev.p, Q[j].get());
-                Rk[j + (size_t)i * m] = rji;
-                p.set_owned(D.axpy(p.p, -rji, Q[j].get()));
-                if (D.pol == TT_ROUND_EVERY_UPDATE) p.set_owned(D.round(p.p));
-            }
-            if (D.pol == TT_ROUND_PAPER || i == 0) p.set_owned(D.round(p.p));
-            // prev <- p (move ownership)
-            if (p.own.get()) {
-                prev.own = std::move(p.own);
-                prev.p = prev.own.get();
-            } else {
-                prev.p = p.p;
-            }
-        }
-        double nrm;
-        Q[i].reset(normalize(D, prev.p, &nrm));
-        R2[i + (size_t)i * m] = nrm;
+        Q[i].reset(gs_step(D, A[i], i, qp.data(), R + (size_t)i * m, modified, twice));
+        qp[i] = Q[i].get();
     }
-    for (size_t e = 0; e < (size_t)m * m; ++e) R[e] = R1[e] + R2[e];
 }
 
 // Algorithm 5: Gram matrix from TT dots, Cholesky and explicit inverse on the
@@ -236,6 +232,17 @@ void householder(Driver& D, int m, const tt_tensor* const* A, std::vector<Tensor
 
 }  // namespace
 
+tt_tensor* orth_step_internal(tt_ctx* ctx, tt_scheme scheme, double delta, tt_round_policy policy,
+                              const tt_tensor* a, int k, const tt_tensor* const* Q, double* col, int* nrounds) {
+    if (scheme != TT_CGS && scheme != TT_MGS && scheme != TT_CGS2 && scheme != TT_MGS2)
+        throw_status(TT_ERR_ARG, "an orthogonalization step takes TT_CGS, TT_MGS, TT_CGS2 or TT_MGS2");
+    Driver D{ctx, delta, policy, 0};
+    tt_tensor* q = gs_step(D, a, k, Q, col, scheme == TT_MGS || scheme == TT_MGS2,
+                           scheme == TT_CGS2 || scheme == TT_MGS2);
+    if (nrounds) *nrounds = D.nrounds;
+    return q;
+}
+
 }  // namespace ttgb
 
 using namespace ttgb;
@@ -255,10 +262,10 @@ extern "C" tt_status tt_orthogonalize(tt_ctx* ctx, tt_scheme scheme, double delt
     std::vector<TensorGuard> Qg(m);
     std::vector<double> Rh((size_t)m * m, 0.0);
     switch (scheme) {
-        case TT_CGS: gs(D, m, A, Qg, Rh.data(), false); break;
-        case TT_MGS: gs(D, m, A, Qg, Rh.data(), true); break;
-        case TT_CGS2: gs2(D, m, A, Qg, Rh.data(), false); break;
-        case TT_MGS2: gs2(D, m, A, Qg, Rh.data(), true); break;
+        case TT_CGS: gs(D, m, A, Qg, Rh.data(), false, false); break;
+        case TT_MGS: gs(D, m, A, Qg, Rh.data(), true, false); break;
+        case TT_CGS2: gs(D, m, A, Qg, Rh.data(), false, true); break;
+        case TT_MGS2: gs(D, m, A, Qg, Rh.data(), true, true); break;
         case TT_GRAM: gram_scheme(D, m, A, Qg, Rh.data()); break;
         case TT_HOUSEHOLDER: householder(D, m, A, Qg, Rh.data()); break;
         default: throw_status(TT_ERR_ARG, "bad scheme");

@@ -1,0 +1,610 @@
+// Cholesky factorization with rank drop and explicit inverse of the factor:
+// G + s I = L L^T, T = L^{-1}, the small r x r step of Cholesky QR in both
+// sweeps of TT-round (Section 2.3; the Cholesky QR reading of the
+// orthogonalization step).
+//
+// Order n <= 256 (FP32) or 160 (FP64): one CTA holds the whole lower
+// triangle in shared memory as 32 x 32 tiles and never touches global memory
+// between loading G and storing L and T, so no step waits on L2 latency:
+//  - right-looking Cholesky by 32-column panels: warp 0 factors and inverts
+//    the diagonal tile in registers (shuffles, no CTA barrier per column);
+//    the tiles below are solved against the tile inverse; the trailing
+//    update is spread over the warps, with warp 0 updating and factoring
+//    the next diagonal tile first (lookahead), so the serial chain of
+//    diagonal factorizations overlaps the bulk of the flops;
+//  - in-place blocked triangular inversion from the last block column to
+//    the first: T_{>J,J} = -T_{>J,>J} L_{>J,J} T_JJ.
+// Tiles are stored without padding with a 16-byte-chunk XOR swizzle, so a
+// lane reads its own tile row with 16-byte loads and every warp reads the
+// shared operand row by 16-byte broadcasts; each 32 x 32 x 32 tile product
+// is one warp, lane r owning output row r in registers.
+//
+// Larger orders are factored blockwise (block size NB <= the one-CTA limit)
+// with the same kernel on diagonal blocks and the CUDA-core GEMM for the
+// panels, trailing updates and off-diagonal inverse blocks, which spreads
+// the O(n^3) work over the GPU.  NB is chosen per (precision, order) by
+// timing the candidates on the first call (autotuned), unless fixed.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+#include "internal.h"
+
+namespace ttgb {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <class C>
+struct TileT;
+template <>
+struct TileT<float> {
+    using V = float4;
+    static constexpr int W = 4;     // elements per 16-byte chunk
+    static constexpr int NCH = 8;   // chunks per 32-element row
+    static constexpr int PMAX = 8;  // n <= 256
+    __device__ __forceinline__ static void fma(float a, const float4 v, float* acc) {
+        acc[0] = fmaf(a, v.x, acc[0]);
+        acc[1] = fmaf(a, v.y, acc[1]);
+        acc[2] = fmaf(a, v.z, acc[2]);
+        acc[3] = fmaf(a, v.w, acc[3]);
+    }
+    __device__ __forceinline__ static void unpack(const float4 v, float* x) {
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+    __device__ __forceinline__ static float4 pack(const float* x) { return make_float4(x[0], x[1], x[2], x[3]); }
+};
+template <>
+struct TileT<double> {
+    using V = double2;
+    static constexpr int W = 2;
+    static constexpr int NCH = 16;
+    static constexpr int PMAX = 5;  // n <= 160
+    __device__ __forceinline__ static void fma(double a, const double2 v, double* acc) {
+        acc[0] = ::fma(a, v.x, acc[0]);
+        acc[1] = ::fma(a, v.y, acc[1]);
+    }
+    __device__ __forceinline__ static void unpack(const double2 v, double* x) {
+        x[0] = v.x; x[1] = v.y;
+    }
+    __device__ __forceinline__ static double2 pack(const double* x) { return make_double2(x[0], x[1]); }
+};
+
+// element (r, c) of a swizzled 32 x 32 tile: chunk c / W of row r sits in
+// slot (c / W) ^ (r mod NCH)
+template <class C>
+__device__ __forceinline__ int tix(int r, int c) {
+    using TT = TileT<C>;
+    return r * 32 + ((((c / TT::W) ^ (r & (TT::NCH - 1)))) * TT::W) + (c % TT::W);
+}
+
+// lane-owned row r of a tile <-> 32 registers
+template <class C>
+__device__ __forceinline__ void load_row(C (&x)[32], const C* tile, int r) {
+    using TT = TileT<C>;
+    const typename TT::V* p = reinterpret_cast<const typename TT::V*>(tile + r * 32);
+#pragma unroll
+    for (int j = 0; j < TT::NCH; ++j) TT::unpack(p[j ^ (r & (TT::NCH - 1))], x + j * TT::W);
+}
+template <class C>
+__device__ __forceinline__ void store_row(C* tile, int r, const C (&x)[32]) {
+    using TT = TileT<C>;
+    typename TT::V* p = reinterpret_cast<typename TT::V*>(tile + r * 32);
+#pragma unroll
+    for (int j = 0; j < TT::NCH; ++j) p[j ^ (r & (TT::NCH - 1))] = TT::pack(x + j * TT::W);
+}
+// lane r's row x stored as column r of the tile (element (k, r) = x[k])
+template <class C>
+__device__ __forceinline__ void store_col(C* tile, int r, const C (&x)[32]) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) tile[tix<C>(k, r)] = x[k];
+}
+
+// acc[c] += sum_k a[k] B(k, c): B read by broadcast rows
+template <class C>
+__device__ __forceinline__ void tile_fma(C (&acc)[32], const C (&a)[32], const C* B) {
+    using TT = TileT<C>;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const typename TT::V* row = reinterpret_cast<const typename TT::V*>(B + k * 32);
+#pragma unroll
+        for (int j = 0; j < TT::NCH; ++j) TT::fma(a[k], row[j ^ (k & (TT::NCH - 1))], acc + j * TT::W);
+    }
+}
+
+__device__ __forceinline__ int tri(int I, int J) { return I * (I + 1) / 2 + J; }  // slot of lower tile (I, J)
+
+struct FactorState {
+    int ndrop, nonfin;
+    double minratio;
+};
+
+// Warp 0: factor the diagonal tile q in place (rank drop below tau), write
+// the transposed inverse to DiT and the inverse to TD (natural layout).
+template <class C>
+__device__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, const double* od, double tau, FactorState& fs) {
+    const int lane = threadIdx.x & 31;
+    C* tile = Lt + (long)tri(q, q) * 1024;
+    C a[32];
+    load_row<C>(a, tile, lane);
+    C invs[32];
+    const C tau_c = (C)tau;
+    C mypiv = C(0);   // lane c keeps pivot c: the status is formed after the loop,
+    bool mykeep = true;  // off the pivot chain
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const C piv = __shfl_sync(FULL, a[c], c);
+        const bool keep = isfinite(piv) && piv > tau_c && piv > C(0);
+        const C d = keep ? sqrt(piv) : C(0);
+        const C inv = keep ? C(1) / d : C(0);
+        invs[c] = inv;
+        if (lane == c) {
+            mypiv = piv;
+            mykeep = keep;
+        }
+        const C l = (lane > c) ? a[c] * inv : C(0);
+        a[c] = (lane == c) ? d : l;
+#pragma unroll
+        for (int k = c + 1; k < 32; ++k) a[k] = fma(-l, __shfl_sync(FULL, l, k), a[k]);
+    }
+    store_row<C>(tile, lane, a);
+    {
+        const int j = q * 32 + lane;
+        const bool valid = j < n;
+        const unsigned nonfin = __ballot_sync(FULL, valid && !isfinite(mypiv));
+        const unsigned drop = __ballot_sync(FULL, valid && !mykeep);
+        double ratio = (valid && mykeep) ? (od[j] > 0.0 ? (double)mypiv / od[j] : 0.0) : 1e300;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ratio = fmin(ratio, __shfl_xor_sync(FULL, ratio, o));
+        if (lane == 0) {
+            if (nonfin) fs.nonfin = 1;
+            fs.ndrop += __popc(drop);
+            fs.minratio = fmin(fs.minratio, ratio);
+        }
+    }
+    // inverse: lane c solves column c, x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii
+    C x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        C s = (i == lane) ? C(1) : C(0);
+#pragma unroll
+        for (int k = 0; k < i; ++k) s = fma(-__shfl_sync(FULL, a[k], i), x[k], s);
+        x[i] = s * invs[i];
+    }
+    store_row<C>(DiT, lane, x);                // DiT row c = column c of T_qq
+    store_col<C>(TD + (long)q * 1024, lane, x);  // TD natural: (i, c) = x_i of lane c
+    __syncwarp();
+}
+
+// Arguments of one factorization.  Standalone (ext == nullptr): the shift is
+// shift_rel trace(G), the drop threshold drop_rel (max_j G_jj + shift); both
+// applied here and the status written.  Block of a larger factorization
+// (ext != nullptr): G already carries the shift, ext[0] = shift and ext[1]
+// = drop threshold, od_src is the original diagonal of the whole matrix at
+// this block, and the status is merged atomically.
+template <class S>
+struct TileArgs {
+    int n;
+    const S* G;
+    long ldg;
+    S* L;
+    long ldl;
+    S* T;
+    long ldt;
+    const S* od_src;  // original diagonal: od_src[i * od_stride]
+    long od_stride;
+    double shift_rel, drop_rel;
+    const double* ext;
+    CholStatus* st;
+};
+
+__device__ __forceinline__ void atomic_min_nonneg(double* addr, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMin(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+template <class S, class C, int NT>
+__global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char ct_smem[];
+    __shared__ double od[TileT<C>::PMAX * 32];
+    __shared__ double red[2 * NW];
+    const int n = A.n;
+    const int P = (n + 31) / 32;
+    const int ntile = P * (P + 1) / 2;
+    C* Lt = reinterpret_cast<C*>(ct_smem);   // ntile tiles
+    C* PT = Lt + (long)ntile * 1024;         // P - 1 tiles (panel transposed / trtri rows)
+    C* DiT = PT + (long)(P - 1) * 1024;      // 1 tile
+    C* TD = DiT + 1024;                      // P tiles (diagonal inverses)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // ---- shift and drop threshold
+    double shift, tau, addshift, tr = 0.0, mx = 0.0;
+    if (A.ext) {
+        shift = A.ext[0];
+        tau = A.ext[1];
+        addshift = 0.0;
+    } else {
+        for (int i = tid; i < n; i += NT) {
+            const double g = (double)A.G[(long)i * A.ldg + i];
+            tr += g;
+            mx = fmax(mx, g);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tr += __shfl_xor_sync(FULL, tr, o);
+            mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
+        }
+        if (lane == 0) {
+            red[warp] = tr;
+            red[NW + warp] = mx;
+        }
+        __syncthreads();
+        tr = 0.0;
+        mx = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            tr += red[w];
+            mx = fmax(mx, red[NW + w]);
+        }
+        shift = A.shift_rel * tr;
+        tau = A.drop_rel * (mx + shift);
+        addshift = shift;
+    }
+    for (int i = tid; i < P * 32; i += NT) od[i] = (i < n) ? (double)A.od_src[(long)i * A.od_stride] + shift : 1.0;
+
+    // ---- load the lower tiles of G (+ shift on the diagonal); padding = identity
+    for (int t = warp; t < ntile * 32; t += NW) {
+        const int slot = t >> 5, r = t & 31;
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= slot) ++I;
+        const int J = slot - I * (I + 1) / 2;
+        const int gi = I * 32 + r, gj = J * 32 + lane;
+        C v;
+        if (gi < n && gj < n) {
+            v = (I == J && lane > r) ? C(0) : (C)A.G[(long)gi * A.ldg + gj];
+            if (gi == gj) v = (C)((double)v + addshift);
+        } else {
+            v = (gi == gj) ? C(1) : C(0);
+        }
+        Lt[(long)slot * 1024 + tix<C>(r, lane)] = v;
+    }
+    __syncthreads();
+
+    FactorState fs{0, 0, 1e300};
+    // ---- Cholesky, right-looking by panels, diagonal factor one panel ahead
+    if (warp == 0) factor_diag<C>(n, 0, Lt, DiT, TD, od, tau, fs);
+    __syncthreads();
+    for (int p = 0; p < P; ++p) {
+        const int R = P - 1 - p;
+        // panel solve: L_Ip = A_Ip T_pp^T, natural copy in place and transposed copy in PT
+        for (int I = p + 1 + warp; I < P; I += NW) {
+            C* tile = Lt + (long)tri(I, p) * 1024;
+            C a[32], acc[32];
+            load_row<C>(a, tile, lane);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = C(0);
+            tile_fma<C>(acc, a, DiT);
+            store_row<C>(tile, lane, acc);
+            store_col<C>(PT + (long)(I - p - 1) * 1024, lane, acc);
+        }
+        __syncthreads();
+        if (R == 0) break;
+        // trailing update A_IK -= L_Ip L_Kp^T for p < K <= I; warp 0 first
+        // takes (p+1, p+1) and factors it, the other warps the rest
+        const int ntask = R * (R + 1) / 2;
+        if (warp == 0) {
+            C* tile = Lt + (long)tri(p + 1, p + 1) * 1024;
+            C a[32], acc[32];
+            load_row<C>(acc, tile, lane);
+            load_row<C>(a, Lt + (long)tri(p + 1, p) * 1024, lane);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) a[k] = -a[k];
+            tile_fma<C>(acc, a, PT);
+            store_row<C>(tile, lane, acc);
+            __syncwarp();
+            factor_diag<C>(n, p + 1, Lt, DiT + 0, TD, od, tau, fs);
+        }
+        // tasks 1..ntask-1 in (I, K) order over I = p+1.., K = p+1..I; task 0 is (p+1, p+1)
+        for (int t = 1 + (NW > 1 ? warp - 1 : 0); t < ntask; t += (NW > 1 ? NW - 1 : 1)) {
+            if (NW > 1 && warp == 0) break;
+            int ii = 0;
+            while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+            const int kk = t - ii * (ii + 1) / 2;
+            const int I = p + 1 + ii, K = p + 1 + kk;
+            C* tile = Lt + (long)tri(I, K) * 1024;
+            C a[32], acc[32];
+            load_row<C>(acc, tile, lane);
+            load_row<C>(a, Lt + (long)tri(I, p) * 1024, lane);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) a[k] = -a[k];
+            tile_fma<C>(acc, a, PT + (long)(K - p - 1) * 1024);
+            store_row<C>(tile, lane, acc);
+        }
+        __syncthreads();
+    }
+
+    // ---- L out (lower tiles; the strictly upper part of the block zeroed)
+    for (int t = warp; t < P * P * 32; t += NW) {
+        const int I = (t >> 5) / P, J = (t >> 5) % P, r = t & 31;
+        const int gi = I * 32 + r, gj = J * 32 + lane;
+        if (gi < n && gj < n) {
+            C v = C(0);
+            if (I > J || (I == J && lane <= r)) v = Lt[(long)tri(I, J) * 1024 + tix<C>(r, lane)];
+            A.L[(long)gi * A.ldl + gj] = (S)v;
+        }
+    }
+    __syncthreads();
+
+    // ---- in-place inversion, last block column first
+    for (int J = P - 1; J >= 0; --J) {
+        if (J < P - 1) {
+            // Y_I = sum_{K=J+1..I} T_IK L_KJ into PT slot I - J - 1
+            for (int I = J + 1 + warp; I < P; I += NW) {
+                C acc[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[j] = C(0);
+                for (int K = J + 1; K <= I; ++K) {
+                    C a[32];
+                    load_row<C>(a, Lt + (long)tri(I, K) * 1024, lane);
+                    tile_fma<C>(acc, a, Lt + (long)tri(K, J) * 1024);
+                }
+                store_row<C>(PT + (long)(I - J - 1) * 1024, lane, acc);
+            }
+            __syncthreads();
+            // T_IJ = -Y_I T_JJ over L_IJ
+            for (int I = J + 1 + warp; I < P; I += NW) {
+                C a[32], acc[32];
+                load_row<C>(a, PT + (long)(I - J - 1) * 1024, lane);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    a[k] = -a[k];
+                    acc[k] = C(0);
+                }
+                tile_fma<C>(acc, a, TD + (long)J * 1024);
+                store_row<C>(Lt + (long)tri(I, J) * 1024, lane, acc);
+            }
+        }
+        // the diagonal block of T
+        for (int e = tid; e < 1024; e += NT) Lt[(long)tri(J, J) * 1024 + e] = TD[(long)J * 1024 + e];
+        __syncthreads();
+    }
+
+    // ---- T out
+    for (int t = warp; t < P * P * 32; t += NW) {
+        const int I = (t >> 5) / P, J = (t >> 5) % P, r = t & 31;
+        const int gi = I * 32 + r, gj = J * 32 + lane;
+        if (gi < n && gj < n) {
+            C v = C(0);
+            if (I > J || (I == J && lane <= r)) v = Lt[(long)tri(I, J) * 1024 + tix<C>(r, lane)];
+            A.T[(long)gi * A.ldt + gj] = (S)v;
+        }
+    }
+    if (tid == 0) {
+        if (A.ext) {
+            if (fs.ndrop) atomicAdd(&A.st->ndrop, fs.ndrop);
+            if (fs.nonfin) atomicOr(&A.st->nonfinite, 1);
+            atomic_min_nonneg(&A.st->min_ratio, fs.minratio);
+        } else {
+            A.st->ndrop = fs.ndrop;
+            A.st->nonfinite = fs.nonfin;
+            A.st->min_ratio = fs.minratio > 1e299 ? 0.0 : fs.minratio;
+            A.st->trace = tr;
+            A.st->max_diag = mx;
+        }
+    }
+}
+
+// Blocked driver pieces: shift, threshold and status of the whole matrix;
+// working copy L = lower(G) + shift I; strictly upper part of L zeroed.
+template <class S>
+__global__ void chol_prologue_kernel(int n, const S* __restrict__ G, double shift_rel, double drop_rel,
+                                     double* __restrict__ ext, CholStatus* __restrict__ st) {
+    __shared__ double rt[32], rm[32];
+    double tr = 0.0, mx = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double g = (double)G[(long)i * n + i];
+        tr += g;
+        mx = fmax(mx, g);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tr += __shfl_xor_sync(FULL, tr, o);
+        mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rt[threadIdx.x >> 5] = tr;
+        rm[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tr = 0.0;
+        mx = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            tr += rt[w];
+            mx = fmax(mx, rm[w]);
+        }
+        const double shift = shift_rel * tr;
+        ext[0] = shift;
+        ext[1] = drop_rel * (mx + shift);
+        st->ndrop = 0;
+        st->nonfinite = 0;
+        st->min_ratio = 1e300;
+        st->trace = tr;
+        st->max_diag = mx;
+    }
+}
+
+template <class S>
+__global__ void chol_copy_lower_kernel(int n, const S* __restrict__ G, const double* __restrict__ ext,
+                                       S* __restrict__ L, S* __restrict__ T) {
+    const long total = (long)n * n;
+    const double shift = ext[0];
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long i = e / n, j = e % n;
+        S v = S(0);
+        if (j <= i) v = (i == j) ? (S)((double)G[e] + shift) : G[e];
+        L[e] = v;
+        T[e] = S(0);
+    }
+}
+
+template <class S>
+__global__ void chol_finish_kernel(int n, S* __restrict__ L, CholStatus* __restrict__ st) {
+    const long total = (long)n * n;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long i = e / n, j = e % n;
+        if (j > i) L[e] = S(0);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st->min_ratio > 1e299) st->min_ratio = 0.0;
+}
+
+template <class S, class C>
+constexpr int tile_nt() {
+    return 256;
+}
+
+template <class S, class C>
+size_t tile_smem(int n) {
+    const int P = (n + 31) / 32;
+    return sizeof(C) * 1024 * (size_t)(P * (P + 1) / 2 + (P - 1) + 1 + P);
+}
+
+template <class S, class C>
+void launch_tile(Ctx& c, const TileArgs<S>& a) {
+    constexpr int NT = tile_nt<S, C>();
+    const int nmax = TileT<C>::PMAX * 32;
+    static std::atomic<bool> attr{false};
+    set_smem_once(attr, chol_tile_kernel<S, C, NT>, (int)tile_smem<S, C>(nmax));
+    chol_tile_kernel<S, C, NT><<<1, NT, tile_smem<S, C>(a.n), c.stream>>>(a);
+    TT_LAUNCHED(c);
+}
+
+template <class S, class C>
+void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st) {
+    const int m = (n + nb - 1) / nb;
+    const size_t wbytes = sizeof(S) * (size_t)n * nb + 2 * sizeof(double) + 256;
+    char* ws = (char*)c.alloc(wbytes);
+    struct Rel {
+        Ctx& c;
+        void* p;
+        size_t b;
+        ~Rel() { c.release(p, b); }
+    } rel{c, ws, wbytes};
+    double* ext = (double*)ws;
+    S* W = (S*)(ws + 256);
+    chol_prologue_kernel<S><<<1, 256, 0, c.stream>>>(n, G, shift_rel, drop_rel, ext, st);
+    TT_LAUNCHED(c);
+    const int cb = std::min(4 * c.sm_count, (int)(((long)n * n + 255) / 256));
+    chol_copy_lower_kernel<S><<<std::max(cb, 1), 256, 0, c.stream>>>(n, G, ext, L, T);
+    TT_LAUNCHED(c);
+    const long ld = n;
+    for (int j = 0; j < m; ++j) {
+        const int j0 = j * nb, b = std::min(nb, n - j0), j1 = j0 + b, M = n - j1;
+        TileArgs<S> a{b, L + j0 * (ld + 1), ld, L + j0 * (ld + 1), ld, T + j0 * (ld + 1), ld,
+                      G + j0 * (ld + 1), ld + 1, 0.0, 0.0, ext, st};
+        launch_tile<S, C>(c, a);
+        if (M == 0) break;
+        // panel L_{>j,j} = A_{>j,j} T_jj^T (via W), then the trailing update
+        gemm<S>(c, false, true, M, b, b, S(1), L + j1 * ld + j0, ld, T + j0 * (ld + 1), ld, S(0), W, b);
+        TT_CUDA(cudaMemcpy2DAsync(L + j1 * ld + j0, ld * sizeof(S), W, b * sizeof(S), b * sizeof(S), M,
+                                  cudaMemcpyDeviceToDevice, c.stream));
+        gemm<S>(c, false, true, M, M, b, S(-1), W, b, W, b, S(1), L + j1 * (ld + 1), ld);
+    }
+    // off-diagonal inverse blocks, last block column first:
+    // T_{>j,j} = -T_{>j,>j} (L_{>j,j} T_jj)
+    for (int j = m - 2; j >= 0; --j) {
+        const int j0 = j * nb, b = std::min(nb, n - j0), j1 = j0 + b, M = n - j1;
+        gemm<S>(c, false, false, M, b, b, S(1), L + j1 * ld + j0, ld, T + j0 * (ld + 1), ld, S(0), W, b);
+        gemm<S>(c, false, false, M, b, M, S(-1), T + j1 * (ld + 1), ld, W, b, S(0), T + j1 * ld + j0, ld);
+    }
+    chol_finish_kernel<S><<<std::max(cb, 1), 256, 0, c.stream>>>(n, L, st);
+    TT_LAUNCHED(c);
+}
+
+// per (compute type, order rounded up to 32) block size chosen by timing
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tuned;
+
+int tuned_nb(int es, int n) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find({es, (n + 31) / 32});
+    return it == g_tuned.end() ? 0 : it->second;
+}
+
+}  // namespace
+
+
+template <class S, class C>
+int chol_tile_max() {
+    return TileT<C>::PMAX * 32;
+}
+
+template <class S, class C>
+void chol_inv_nb(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st) {
+    const int nmax = chol_tile_max<S, C>();
+    if (nb >= n && n <= nmax) {
+        TileArgs<S> a{n, G, n, L, n, T, n, G, (long)n + 1, shift_rel, drop_rel, nullptr, st};
+        launch_tile<S, C>(c, a);
+    } else {
+        blocked<S, C>(c, n, std::max(32, std::min(nb, nmax)), G, L, T, shift_rel, drop_rel, st);
+    }
+}
+
+template <class S, class C>
+void chol_inv(Ctx& c, int n, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st) {
+    if (n <= 0) return;
+    const int nmax = chol_tile_max<S, C>();
+    ProfScope ps(c, "chol_inv", 2.0 * (double)n * n * n / 3.0, 3.0 * sizeof(S) * n * n);
+    int nb = c.chol_nb ? c.chol_nb : tuned_nb(sizeof(C), n);
+    if (!nb) {
+        // candidates: the one-CTA kernel when it fits, and blocked sizes
+        // below n; each timed once on this call's own input (the inputs are
+        // read-only, the last run leaves the outputs)
+        std::vector<int> cand;
+        if (n <= nmax) cand.push_back(n);
+        const int opts32[] = {128, 192, 256};
+        const int opts64[] = {64, 96, 128, 160};
+        const int* o = sizeof(C) == 4 ? opts32 : opts64;
+        const int no = sizeof(C) == 4 ? 3 : 4;
+        for (int i = 0; i < no; ++i)
+            if (o[i] < n && o[i] <= nmax) cand.push_back(o[i]);
+        if (cand.size() == 1) {
+            nb = cand.front();
+        } else {
+            cudaEvent_t e0 = c.event(), e1 = c.event();
+            float best = 1e30f;
+            for (int rep = 0; rep < 2; ++rep)  // first pass warms up
+                for (int v : cand) {
+                    TT_CUDA(cudaEventRecord(e0, c.stream));
+                    chol_inv_nb<S, C>(c, n, v, G, L, T, shift_rel, drop_rel, st);
+                    TT_CUDA(cudaEventRecord(e1, c.stream));
+                    TT_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    TT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (rep == 1 && ms < best) {
+                        best = ms;
+                        nb = v;
+                    }
+                }
+            c.ev_pool.push_back(e0);
+            c.ev_pool.push_back(e1);
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[{(int)sizeof(C), (n + 31) / 32}] = nb;
+        }
+    }
+    chol_inv_nb<S, C>(c, n, nb, G, L, T, shift_rel, drop_rel, st);
+}
+
+template void chol_inv<double, double>(Ctx&, int, const double*, double*, double*, double, double, CholStatus*);
+template void chol_inv<float, float>(Ctx&, int, const float*, float*, float*, double, double, CholStatus*);
+template void chol_inv_nb<double, double>(Ctx&, int, int, const double*, double*, double*, double, double,
+                                          CholStatus*);
+template void chol_inv_nb<float, float>(Ctx&, int, int, const float*, float*, float*, double, double, CholStatus*);
+template int chol_tile_max<double, double>();
+template int chol_tile_max<float, float>();
+
+}  // namespace ttgb

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -31,6 +33,21 @@ struct Error {
         if (e__ != cudaSuccess) ::ttgb::throw_cuda(e__, "kernel launch", __FILE__, __LINE__); \
     } while (0)
 
+// Raises a kernel's dynamic shared-memory limit once per process; safe when
+// several host threads (batched rounding, serving workers) launch at once.
+// It is set for the device current at the first call (one device per
+// process: multi-GPU runs are independent replicas).
+template <class F>
+void set_smem_once(std::atomic<bool>& flag, F* func, int bytes) {
+    if (flag.load(std::memory_order_acquire)) return;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (flag.load(std::memory_order_relaxed)) return;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) throw_cuda(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+    flag.store(true, std::memory_order_release);
+}
+
 // ---------------------------------------------------------------- kernels
 // Small-matrix factorization status written by the Cholesky kernel.
 struct CholStatus {
@@ -57,28 +74,21 @@ void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, lo
 template <class T, class S>
 void gram(Ctx& c, bool rows, int n, long K, const T* X, long ldx, S* G);
 
-// Cholesky G + shift I = L L^T (lower), single CTA, compute type C.
-// shift = shift_rel * trace(G).  Pivots <= drop_rel * max_diag are dropped
-// (column of L set to 0).  L is n x n row-major (upper part zeroed).
-template <class S, class C>
-void cholesky(Ctx& c, int n, const S* G, S* L, double shift_rel, double drop_rel,
-              CholStatus* st_dev);
-
-// Blocked Cholesky with rank drop and the explicit inverse of the factor in
-// one single-CTA kernel: G + shift I = L L^T, T = L^{-1} (same conventions
-// as cholesky() and trinv()).
+// Cholesky factorization with rank drop and the explicit inverse of the
+// factor: G + shift I = L L^T, T = L^{-1}, all n x n row-major (lower
+// triangles; upper parts written as zeros), compute type C.
+// shift = shift_rel * trace(G).  Pivots <= drop_rel * (max_j G_jj + shift)
+// are dropped: the column of L and the row and column of T are zero.
+// One CTA with everything in shared memory for n <= chol_tile_max(), else
+// blockwise with block size Ctx::chol_nb, or autotuned per order.
 template <class S, class C>
 void chol_inv(Ctx& c, int n, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st_dev);
-
-// the same with the working panel in shared memory; false (nothing
-// launched) when n exceeds 512 (FP32) or 256 (FP64)
+// the same with a given block size (nb >= n: the one-CTA kernel)
 template <class S, class C>
-bool chol_inv_smem(Ctx& c, int n, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st_dev);
-
-// T = L^{-1} for lower-triangular L with possibly zero (dropped) columns:
-// dropped indices give zero rows and columns of T.
+void chol_inv_nb(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, double drop_rel,
+                 CholStatus* st_dev);
 template <class S, class C>
-void trinv(Ctx& c, int n, const S* L, S* T);
+int chol_tile_max();
 
 // One-sided Jacobi SVD of the rows of R (p x b, row-major, p <= b):
 // R = U diag(sigma) V^T.  Outputs U (p x p, row-major, columns sorted by
@@ -157,15 +167,30 @@ struct Ctx {
     tt_sign_rule sign_rule = TT_SIGN_STABLE;
     int sm_count = 0;
     bool use_tc = true;       // tensor-core Gram in TT_MIXED_TF32
-    bool use_tc_gemm = true;  // tensor-core split-TF32 apply / absorb GEMMs in TT_MIXED_TF32
+    // tensor-core split-TF32 apply / absorb GEMMs in TT_MIXED_TF32 (opt-in:
+    // the tensor cores' FP32 accumulation truncates, and the apply Q = L^{-1} X
+    // cancels heavily, so a full rounding lands near 2.5e-6 relative error at
+    // delta = 1e-6 against 1.06e-6 with the CUDA-core FP32 GEMM)
+    bool use_tc_gemm = false;
     int tc_gemm_split = 3;    // 3: hi + mid + lo (6 products), 2: hi + lo (3 products)
     int* tc_err = nullptr;  // device flag: a bounded wait of a tensor-core kernel ran out
     // lifetime: one reference for the owner plus one per live tensor; the
     // context is deleted when the last reference goes
-    long refs = 1;
+    std::atomic<long> refs{1};
+
+    // Lanes: child contexts with their own non-blocking streams that run
+    // independent roundings concurrently (batched rounding, serving).  A
+    // lane's device bytes are charged to its root's budget and counters.
+    Ctx* root = nullptr;          // non-null for a lane
+    bool owns_stream = false;     // lanes create (and destroy) their stream
+    std::mutex acct_mu;           // guards stats.bytes_in_use / peak_bytes of a root
+    std::vector<Ctx*> lanes;      // lanes owned by this root (created on demand)
+    int max_lanes = 8;            // concurrency of tt_round_batched
+    int chol_nb = 0;              // block size of chol_inv (0: autotuned per order)
 
     // event profiling of launches (off by default)
     bool prof = false;
+    int prof_nest = 0;            // open ProfScopes: only the outermost records
     std::vector<std::string> fam_names;
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> ev_pool;
@@ -177,6 +202,13 @@ struct Ctx {
     cudaEvent_t event();
     ~Ctx();
 };
+
+// Returns the root's lanes [0, count), creating missing ones (stream,
+// status word, settings copied from the root).
+std::vector<Ctx*> get_lanes(Ctx& root, int count);
+// Adds a lane's counters (all but the byte counters, kept by the root) and
+// event-profile records into the root, then clears them on the lane.
+void merge_lane(Ctx& root, Ctx& lane);
 
 // Records CUDA events on the context stream around the launches made while
 // it is alive, when profiling is on.

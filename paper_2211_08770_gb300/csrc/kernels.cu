@@ -240,309 +240,6 @@ void inv_and_identity_defect(Ctx& c, int n, const S* L, const S* T, double* out)
     TT_LAUNCHED(c);
 }
 
-// -------------------------------------------------------------- Cholesky
-// Right-looking, column by column, one CTA.  The working matrix lives in
-// shared memory when it fits, else in L (global, L2-resident).
-namespace {
-
-template <class S, class C, bool SMEM>
-__global__ void __launch_bounds__(1024)
-chol_kernel(int n, const S* __restrict__ G, S* __restrict__ L, double shift_rel,
-            double drop_rel, CholStatus* st) {
-    extern __shared__ __align__(16) unsigned char chol_smem[];
-    __shared__ double shd[32];
-    __shared__ C s_d;
-    __shared__ int s_ndrop, s_nonfinite;
-    __shared__ double s_minratio;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    double tr = 0.0, mx = 0.0;
-    for (int i = tid; i < n; i += nt) {
-        const double g = (double)G[(long)i * n + i];
-        tr += g;
-        mx = fmax(mx, g);
-    }
-    tr = block_sum(tr, shd);
-    // block max
-    {
-        double v = mx;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if ((tid & 31) == 0) shd[tid >> 5] = v;
-        __syncthreads();
-        if (tid == 0) {
-            double m = 0.0;
-            for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, shd[w]);
-            shd[0] = m;
-            s_ndrop = 0;
-            s_nonfinite = 0;
-            s_minratio = 1e300;
-        }
-        __syncthreads();
-        mx = shd[0];
-        __syncthreads();
-    }
-    const double shift = shift_rel * tr;
-    const double tau = drop_rel * (mx + shift);
-    C* A = SMEM ? reinterpret_cast<C*>(chol_smem) : nullptr;
-    const long nn = (long)n * n;
-    for (long e = tid; e < nn; e += nt) {
-        const long i = e / n, k = e % n;
-        C v = C(0);
-        if (k <= i) v = (C)G[e] + (i == k ? (C)shift : C(0));
-        if (SMEM) A[e] = v; else L[e] = (S)v;
-    }
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-        if (tid == 0) {
-            const C p = SMEM ? A[(long)j * n + j] : (C)L[(long)j * n + j];
-            const double orig = (double)G[(long)j * n + j] + shift;
-            C d = C(0);
-            if (!isfinite((double)p)) {
-                s_nonfinite = 1;
-            } else if ((double)p > tau && p > C(0)) {
-                d = sqrt(p);
-                s_minratio = fmin(s_minratio, orig > 0.0 ? (double)p / orig : 0.0);
-            } else {
-                s_ndrop++;
-            }
-            s_d = d;
-            if (SMEM) A[(long)j * n + j] = d; else L[(long)j * n + j] = (S)d;
-        }
-        __syncthreads();
-        const C d = s_d;
-        if (d == C(0)) {
-            for (int i = j + 1 + tid; i < n; i += nt) {
-                if (SMEM) A[(long)i * n + j] = C(0); else L[(long)i * n + j] = S(0);
-            }
-            __syncthreads();
-            continue;
-        }
-        const C inv = C(1) / d;
-        for (int i = j + 1 + tid; i < n; i += nt) {
-            if (SMEM) A[(long)i * n + j] *= inv;
-            else L[(long)i * n + j] = (S)((C)L[(long)i * n + j] * inv);
-        }
-        __syncthreads();
-        const int rem = n - j - 1;
-        const long rr = (long)rem * rem;
-        for (long e = tid; e < rr; e += nt) {
-            const int i = j + 1 + (int)(e / rem), k = j + 1 + (int)(e % rem);
-            if (k > i) continue;
-            if (SMEM) {
-                A[(long)i * n + k] -= A[(long)i * n + j] * A[(long)k * n + j];
-            } else {
-                L[(long)i * n + k] = (S)((C)L[(long)i * n + k] - (C)L[(long)i * n + j] * (C)L[(long)k * n + j]);
-            }
-        }
-        __syncthreads();
-    }
-    if (SMEM) {
-        for (long e = tid; e < nn; e += nt) L[e] = (S)A[e];
-    }
-    if (tid == 0) {
-        st->ndrop = s_ndrop;
-        st->nonfinite = s_nonfinite;
-        st->min_ratio = s_minratio > 1e299 ? 0.0 : s_minratio;
-        st->trace = tr;
-        st->max_diag = mx;
-    }
-}
-
-}  // namespace
-
-template <class S, class C>
-void cholesky(Ctx& c, int n, const S* G, S* L, double shift_rel, double drop_rel, CholStatus* st) {
-    if (n <= 0) return;
-    const size_t smem = (size_t)n * n * sizeof(C);
-    const int threads = n <= 64 ? 256 : 1024;
-    ProfScope ps(c, "cholesky", (double)n * n * n / 3.0, 2.0 * sizeof(S) * n * n);
-    if (smem <= 160 * 1024) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            TT_CUDA(cudaFuncSetAttribute(chol_kernel<S, C, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-            attr_set = true;
-        }
-        chol_kernel<S, C, true><<<1, threads, smem, c.stream>>>(n, G, L, shift_rel, drop_rel, st);
-    } else {
-        chol_kernel<S, C, false><<<1, threads, 0, c.stream>>>(n, G, L, shift_rel, drop_rel, st);
-    }
-    TT_LAUNCHED(c);
-}
-
-// --------------------------------------------------- triangular inverse
-namespace {
-
-template <class S, class C>
-__global__ void __launch_bounds__(256) trinv_kernel(int n, const S* __restrict__ L, S* __restrict__ T) {
-    extern __shared__ __align__(16) unsigned char trinv_smem[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int j = blockIdx.x * (blockDim.x >> 5) + w;
-    if (j >= n) return;  // whole warp leaves; no block barrier below
-    C* x = reinterpret_cast<C*>(trinv_smem) + (long)w * n;
-    const C djj = (C)L[(long)j * n + j];
-    if (djj == C(0)) {
-        for (int i = lane; i < n; i += 32) T[(long)i * n + j] = S(0);
-        return;
-    }
-    for (int i = lane; i < j; i += 32) T[(long)i * n + j] = S(0);
-    if (lane == 0) x[j] = C(1) / djj;
-    __syncwarp();
-    for (int i = j + 1; i < n; ++i) {
-        const C dii = (C)L[(long)i * n + i];
-        C s = C(0);
-        for (int k = j + lane; k < i; k += 32) s = fma((C)L[(long)i * n + k], x[k], s);
-        s = warp_sum(s);
-        if (lane == 0) x[i] = (dii == C(0)) ? C(0) : -s / dii;
-        __syncwarp();
-    }
-    for (int i = j + lane; i < n; i += 32) T[(long)i * n + j] = (S)x[i];
-}
-
-}  // namespace
-
-template <class S, class C>
-void trinv(Ctx& c, int n, const S* L, S* T) {
-    if (n <= 0) return;
-    const int warps = 8;
-    const size_t smem = (size_t)warps * n * sizeof(C);
-    if (smem > 48 * 1024) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            TT_CUDA(cudaFuncSetAttribute(trinv_kernel<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024));
-            attr_set = true;
-        }
-        if (smem > 200 * 1024) throw_status(TT_ERR_ARG, "trinv: n too large");
-    }
-    ProfScope ps(c, "trinv", (double)n * n * n / 3.0, 2.0 * sizeof(S) * n * n);
-    trinv_kernel<S, C><<<(n + warps - 1) / warps, warps * 32, smem, c.stream>>>(n, L, T);
-    TT_LAUNCHED(c);
-}
-
-// ------------------------------------------------ one-sided Jacobi SVD
-// Rows of W (p x b) are orthogonalized by plane rotations in round-robin
-// order, one warp per pair; U accumulates the rotations (rows of Ut are the
-// columns of U).  FP64 arithmetic.  p <= 1024.
-namespace {
-
-__global__ void __launch_bounds__(1024)
-jacobi_kernel(int p, int b, double* __restrict__ W, double* __restrict__ Ut, int max_sweeps, double tol) {
-    __shared__ int s_rot;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int pp = p + (p & 1);
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        if (threadIdx.x == 0) s_rot = 0;
-        __syncthreads();
-        for (int s = 0; s < pp - 1; ++s) {
-            for (int k = w; k < pp / 2; k += nw) {
-                int i, j;
-                if (k == 0) { i = s; j = pp - 1; }
-                else { i = (s + k) % (pp - 1); j = (s - k + pp - 1) % (pp - 1); }
-                if (i >= p || j >= p) continue;
-                double* wi = W + (long)i * b;
-                double* wj = W + (long)j * b;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int t = lane; t < b; t += 32) {
-                    const double x = wi[t], y = wj[t];
-                    al = fma(x, x, al);
-                    be = fma(y, y, be);
-                    ga = fma(x, y, ga);
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) continue;
-                const double zeta = (be - al) / (2.0 * ga);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-                for (int q = lane; q < b; q += 32) {
-                    const double x = wi[q], y = wj[q];
-                    wi[q] = cs * x - sn * y;
-                    wj[q] = sn * x + cs * y;
-                }
-                double* ui = Ut + (long)i * p;
-                double* uj = Ut + (long)j * p;
-                for (int q = lane; q < p; q += 32) {
-                    const double x = ui[q], y = uj[q];
-                    ui[q] = cs * x - sn * y;
-                    uj[q] = sn * x + cs * y;
-                }
-                if (lane == 0) s_rot = 1;
-            }
-            __syncthreads();
-        }
-        const int rot = s_rot;
-        __syncthreads();
-        if (!rot) break;
-    }
-}
-
-template <class S>
-__global__ void __launch_bounds__(1024)
-jacobi_prep_kernel(int p, int b, const S* __restrict__ R, double* __restrict__ W, double* __restrict__ Ut) {
-    const long pb = (long)p * b, ppp = (long)p * p;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < pb; e += (long)gridDim.x * blockDim.x)
-        W[e] = (double)R[e];
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < ppp; e += (long)gridDim.x * blockDim.x)
-        Ut[e] = (e / p == e % p) ? 1.0 : 0.0;
-}
-
-template <class S>
-__global__ void __launch_bounds__(1024)
-jacobi_finish_kernel(int p, int b, const double* __restrict__ W, const double* __restrict__ Ut,
-                     S* __restrict__ U, S* __restrict__ SVt, double* __restrict__ sigma) {
-    extern __shared__ __align__(16) unsigned char jf_smem[];
-    double* sig = reinterpret_cast<double*>(jf_smem);
-    int* perm = reinterpret_cast<int*>(sig + p);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = w; i < p; i += nw) {
-        double s = 0.0;
-        for (int t = lane; t < b; t += 32) s = fma(W[(long)i * b + t], W[(long)i * b + t], s);
-        s = warp_sum(s);
-        if (lane == 0) sig[i] = sqrt(s);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < p; i += blockDim.x) {
-        int rank = 0;
-        const double si = sig[i];
-        for (int j = 0; j < p; ++j) rank += (sig[j] > si) || (sig[j] == si && j < i);
-        perm[rank] = i;
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < p; r += blockDim.x) sigma[r] = sig[perm[r]];
-    const long pb = (long)p * b;
-    for (long e = threadIdx.x; e < pb; e += blockDim.x) {
-        const long r = e / b, t = e % b;
-        SVt[e] = (S)W[(long)perm[r] * b + t];
-    }
-    const long ppp = (long)p * p;
-    for (long e = threadIdx.x; e < ppp; e += blockDim.x) {
-        const long i = e / p, r = e % p;  // U[i][r] = Ut[perm[r]][i]
-        U[e] = (S)Ut[(long)perm[r] * p + i];
-    }
-}
-
-}  // namespace
-
-template <class S>
-void jacobi_svd(Ctx& c, int p, int b, const S* R, S* U, S* SVt, double* sigma, S* work) {
-    if (p <= 0) return;
-    if (p > 1024 || p > b) throw_status(TT_ERR_ARG, "jacobi_svd: need p <= min(b, 1024)");
-    double* W = reinterpret_cast<double*>(work);
-    double* Ut = W + (long)p * b;
-    ProfScope ps(c, "jacobi_svd", 0.0, sizeof(S) * (2.0 * p * b + 2.0 * p * p));
-    jacobi_prep_kernel<S><<<std::max(1, std::min(2 * c.sm_count, (int)(((long)p * b + 1023) / 1024))), 1024, 0,
-                            c.stream>>>(p, b, R, W, Ut);
-    TT_LAUNCHED(c);
-    const int threads = std::min(1024, std::max(32, ((p + 1) / 2) * 32));
-    jacobi_kernel<<<1, threads, 0, c.stream>>>(p, b, W, Ut, 40, 1e-15);
-    TT_LAUNCHED(c);
-    const size_t smem = (size_t)p * (sizeof(double) + sizeof(int));
-    jacobi_finish_kernel<S><<<1, 1024, smem, c.stream>>>(p, b, W, Ut, U, SVt, sigma);
-    TT_LAUNCHED(c);
-}
-
 // ---------------------------------------------------------- elementwise
 namespace {
 
@@ -665,16 +362,11 @@ void axpy(Ctx& c, long n, double alpha, const T* x, T* y) {
     template void transpose<T>(Ctx&, int, int, const T*, T*);                                    \
     template void scatter_blocks<T>(Ctx&, const BlockList&, int, long, long, T*, int, int);      \
     template void axpy<T>(Ctx&, long, double, const T*, T*);                                     \
-    template void inv_and_identity_defect<T>(Ctx&, int, const T*, const T*, double*);            \
-    template void jacobi_svd<T>(Ctx&, int, int, const T*, T*, T*, double*, T*);
+    template void inv_and_identity_defect<T>(Ctx&, int, const T*, const T*, double*);
 TT_INST_T(float)
 TT_INST_T(double)
 template void gram<double, double>(Ctx&, bool, int, long, const double*, long, double*);
 template void gram<float, float>(Ctx&, bool, int, long, const float*, long, float*);
-template void cholesky<double, double>(Ctx&, int, const double*, double*, double, double, CholStatus*);
-template void cholesky<float, float>(Ctx&, int, const float*, float*, double, double, CholStatus*);
-template void trinv<double, double>(Ctx&, int, const double*, double*);
-template void trinv<float, float>(Ctx&, int, const float*, float*);
 template void convert<double, float>(Ctx&, long, const double*, float*);
 template void convert<float, double>(Ctx&, long, const float*, double*);
 

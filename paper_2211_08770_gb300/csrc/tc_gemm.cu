@@ -352,19 +352,12 @@ bool gemm_tc3_tf32(Ctx& c, bool bT, int M, int N, int K, const float* A, long ld
     if (grid.y > 65535) return false;
     const int nop = (nsplit == 3) ? 1 : 2;
     const size_t smem = 1024 + (size_t)nop * 2 * nsplit * TILE + NSTG * 2 * TILE + sizeof(GemmCtl) + 64;
-    static bool attr[2][2] = {{false, false}, {false, false}};
+    static std::atomic<bool> attr[2][2];
     const int si = nsplit - 2;
-#define TT_GEMM3_ATTR(BT_, NS_)                                                                              \
-    TT_CUDA(cudaFuncSetAttribute(gemm3_tf32_kernel<BT_, NS_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)smem))
-    if (!attr[bT][si]) {
-        if (bT && si) TT_GEMM3_ATTR(true, 3);
-        else if (bT) TT_GEMM3_ATTR(true, 2);
-        else if (si) TT_GEMM3_ATTR(false, 3);
-        else TT_GEMM3_ATTR(false, 2);
-        attr[bT][si] = true;
-    }
-#undef TT_GEMM3_ATTR
+    if (bT && si) set_smem_once(attr[1][1], gemm3_tf32_kernel<true, 3>, (int)smem);
+    else if (bT) set_smem_once(attr[1][0], gemm3_tf32_kernel<true, 2>, (int)smem);
+    else if (si) set_smem_once(attr[0][1], gemm3_tf32_kernel<false, 3>, (int)smem);
+    else set_smem_once(attr[0][0], gemm3_tf32_kernel<false, 2>, (int)smem);
     ProfScope ps(c, nsplit == 3 ? "gemm_tf32x6_tc" : "gemm_tf32x3_tc", 2.0 * M * (double)N * K,
                  4.0 * ((double)M * K + (double)K * N + (double)M * N));
     if (bT && si) gemm3_tf32_kernel<true, 3><<<grid, 192, smem, c.stream>>>(ma, mb, M, N, K, C, ldc, c.tc_err);

@@ -380,11 +380,8 @@ bool gram_rows_tc_tf32(Ctx& c, int n, long K, const float* X, long ldx, float* G
     if (blocks > 2147483647L) return false;
 
     const size_t smem = 1024 + STAGES * 2 * TILE_BYTES + sizeof(GramSmem) + 64;
-    static bool attr = false;
-    if (!attr) {
-        TT_CUDA(cudaFuncSetAttribute(gram_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<bool> attr{false};
+    set_smem_once(attr, gram_tf32_kernel, (int)smem);
     int* err = c.tc_err;
     TT_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n * n, c.stream));
     ProfScope ps(c, "gram_tf32_tc", (double)n * (n + 1) * (double)K, 4.0 * (double)n * K + 4.0 * n * n);
@@ -422,11 +419,8 @@ bool gram_cols_tc_tf32(Ctx& c, int n, long m, const float* X, long ldx, float* G
     const long blocks = (long)ntri * splits;
     if (blocks > 2147483647L) return false;
     const size_t smem = 1024 + (COP + CSTG) * 2 * TILE_BYTES + sizeof(ColCtl) + 64;
-    static bool attr = false;
-    if (!attr) {
-        TT_CUDA(cudaFuncSetAttribute(gram_cols_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<bool> attr{false};
+    set_smem_once(attr, gram_cols_tf32_kernel, (int)smem);
     TT_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n * n, c.stream));
     ProfScope ps(c, "gram_tf32_tc", (double)n * (n + 1) * (double)m, 4.0 * (double)n * m + 4.0 * n * n);
     gram_cols_tf32_kernel<<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, m, ntiles, kchunk, G, c.tc_err);

@@ -16,7 +16,8 @@ from . import build as _build
 
 TT_OK = 0
 STATUS = {0: "TT_OK", 1: "TT_ERR_ARG", 2: "TT_ERR_SHAPE", 3: "TT_ERR_OOM", 4: "TT_ERR_NOT_SPD",
-          5: "TT_ERR_BREAKDOWN", 6: "TT_ERR_NONFINITE", 7: "TT_ERR_TIMEOUT", 8: "TT_ERR_CUDA"}
+          5: "TT_ERR_BREAKDOWN", 6: "TT_ERR_NONFINITE", 7: "TT_ERR_TIMEOUT", 8: "TT_ERR_CUDA",
+          9: "TT_ERR_CANCELLED"}
 PRECISION = {"fp64": 0, "mixed_tf32": 1, "fp32": 2}
 SCHEME = {"cgs": 0, "mgs": 1, "cgs2": 2, "mgs2": 3, "gram": 4, "householder": 5}
 POLICY = {"paper": 0, "every_update": 1}
@@ -71,12 +72,21 @@ _SIGS = {
     "tt_norm": (_I, [_P, _P, _PD]),
     "tt_round": (_I, [_P, _P, _D, C.POINTER(_P), _PD]),
     "tt_round_batched": (_I, [_P, _I, _PP, _PD, _PP]),
+    "tt_ctx_set_concurrency": (_I, [_P, _I]),
+    "tt_ctx_get_concurrency": (_I, [_P]),
     "tt_orthogonalize": (_I, [_P, _I, _D, _I, _I, _PP, _PP, _PD, _PI]),
     "tt_set_sign_rule": (_I, [_P, _I]),
     "tt_gram_f32": (_I, [_P, _I, C.c_long, _P, C.c_long, _P, _I]),
     "tt_cholesky_inverse": (_I, [_P, _I, _P, _P, _P, _D, _D, _PI]),
     "tt_gemm_f32": (_I, [_P, _I, _I, _I, _I, _P, C.c_long, _P, C.c_long, _P, C.c_long, _I]),
     "tt_dot_f64_noalloc": (_I, [_P, _I, _PI, _PI, _PI, _PP, _PP, _P]),
+    "tt_server_create": (_I, [_P, _I, C.c_size_t, C.POINTER(_P)]),
+    "tt_server_add_basis": (_I, [_P, _I, _PP, _PI]),
+    "tt_server_submit": (_I, [_P, _I, _P, _D, _I, _I, _I, C.POINTER(C.c_uint64)]),
+    "tt_server_wait": (_I, [_P, C.c_uint64, _I, C.POINTER(_P), _PD, _I, _PD]),
+    "tt_server_cancel": (_I, [_P, C.c_uint64]),
+    "tt_server_get_stats": (_I, [_P, C.c_void_p]),
+    "tt_server_destroy": (None, [_P]),
     "tt_status_str": (C.c_char_p, [_I]),
     "tt_last_error": (C.c_char_p, []),
 }
@@ -158,6 +168,15 @@ class Ctx:
 
     def set_sign_rule(self, rule):
         _check(lib().tt_set_sign_rule(self._h, SIGN[rule]), "tt_set_sign_rule")
+
+    @property
+    def concurrency(self):
+        """Lanes used by tt_round_batched."""
+        return int(lib().tt_ctx_get_concurrency(self._h))
+
+    @concurrency.setter
+    def concurrency(self, lanes):
+        _check(lib().tt_ctx_set_concurrency(self._h, int(lanes)), "tt_ctx_set_concurrency")
 
     def close(self):
         if self._h:
@@ -302,10 +321,13 @@ def tt_orthogonalize(ctx, scheme, A, delta, policy="paper"):
     return [TT(ctx, _P(Q[i])) for i in range(m)], Rm, nr.value
 
 
-def tt_gram_f32(ctx, n, K, x_ptr, ldx, g_ptr, use_tensor_cores=True):
-    """G = X X^T for device FP32 pointers (see include/ttgb.h)."""
-    _check(lib().tt_gram_f32(ctx.handle, n, K, _P(x_ptr), ldx, _P(g_ptr), 1 if use_tensor_cores else 0),
-           "tt_gram_f32")
+def tt_gram_f32(ctx, n, K, x_ptr, ldx, g_ptr, use_tensor_cores=1):
+    """G = X X^T for device FP32 pointers (see include/ttgb.h); mode 0
+    CUDA cores, 1 tensor cores, 2 the column Gram X^T X on tensor cores."""
+    mode = int(use_tensor_cores)
+    if mode not in (0, 1, 2):
+        raise ValueError("use_tensor_cores must be 0, 1 or 2")
+    _check(lib().tt_gram_f32(ctx.handle, n, K, _P(x_ptr), ldx, _P(g_ptr), mode), "tt_gram_f32")
 
 
 def tt_dot_f64_noalloc(stream, n, rx, ry, x_ptrs, y_ptrs, result_ptr):
@@ -346,3 +368,75 @@ def loss_of_orthogonality(ctx, Q):
         G[i, : i + 1] = v
         G[: i + 1, i] = v
     return float(np.max(np.abs(np.linalg.eigvalsh(np.eye(m) - G))))
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in (
+        "submitted", "completed", "failed", "cancelled", "refused", "queued", "running",
+        "footprint_in_use", "footprint_peak", "footprint_budget", "roundings", "kernel_launches", "host_syncs")]
+
+
+class Server:
+    """A tt_server over ctx: requests run concurrently on `workers` lanes,
+    admitted by device footprint (bytes, 0 = the context's budget)."""
+
+    def __init__(self, ctx, workers=8, footprint_budget=0):
+        self.ctx = ctx
+        self._h = _P()
+        _check(lib().tt_server_create(ctx.handle, int(workers), int(footprint_budget), C.byref(self._h)),
+               "tt_server_create")
+        self._basis_k = {}
+        self._inputs = {}  # ticket -> input TT, kept alive until its wait returns
+
+    def add_basis(self, tensors):
+        """Copies orthonormal TT tensors (TT objects) into a resident basis; returns its id."""
+        bid = C.c_int()
+        _check(lib().tt_server_add_basis(self._h, len(tensors), _handles(tensors), C.byref(bid)),
+               "tt_server_add_basis")
+        self._basis_k[bid.value] = len(tensors)
+        return bid.value
+
+    def submit_round(self, x, delta):
+        t = C.c_uint64()
+        _check(lib().tt_server_submit(self._h, 0, x.handle, float(delta), -1, 0, 0, C.byref(t)), "tt_server_submit")
+        self._inputs[t.value] = x
+        return t.value
+
+    def submit_orth(self, x, basis_id, k, scheme, delta):
+        t = C.c_uint64()
+        _check(lib().tt_server_submit(self._h, 1, x.handle, float(delta), int(basis_id), int(k), SCHEME[scheme],
+                                      C.byref(t)), "tt_server_submit")
+        self._inputs[t.value] = x
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1, coef_cap=0):
+        """(TT result, coefficients (list), (t_submit, t_start, t_done))."""
+        h = _P()
+        cf = (C.c_double * max(coef_cap, 1))()
+        tm = (C.c_double * 3)()
+        st = lib().tt_server_wait(self._h, C.c_uint64(ticket), int(timeout_ms), C.byref(h), cf, int(coef_cap), tm)
+        if st != TT_OK and STATUS.get(st) == "TT_ERR_TIMEOUT":
+            _check(st, "tt_server_wait")  # the request is still pending: keep its input
+        self._inputs.pop(ticket, None)
+        _check(st, "tt_server_wait")
+        return TT(self.ctx, h), [cf[i] for i in range(coef_cap)], (tm[0], tm[1], tm[2])
+
+    def cancel(self, ticket):
+        _check(lib().tt_server_cancel(self._h, C.c_uint64(ticket)), "tt_server_cancel")
+
+    def stats(self):
+        s = _ServerStats()
+        _check(lib().tt_server_get_stats(self._h, C.byref(s)), "tt_server_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in _ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().tt_server_destroy(self._h)
+            self._h = _P()
+        self._inputs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

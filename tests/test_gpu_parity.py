@@ -64,7 +64,18 @@ def _gauge_padded(seed):
     return [np.einsum("pa,aib,bq->piq", Ap[k], x[k], A[k + 1]) for k in range(4)]
 
 
+def _graded(seed, n, ranks):
+    # bond singular values spread over about eight decades: the truncation
+    # SVDs run on every bond (ranks above 32 take the multi-CTA Jacobi)
+    x = _rand(seed, n, ranks)
+    for c in x[:-1]:
+        c *= 10.0 ** (-8.0 * np.arange(c.shape[2]) / c.shape[2])
+    return x
+
+
 ROUND_CASES = {
+    "graded_r48": (lambda: _graded(12, [12] * 5, [1, 12, 48, 48, 12, 1]), 1e-5),
+    "graded_r200": (lambda: _graded(13, [16] * 4, [1, 16, 200, 16, 1]), 1e-6),
     "small_random_d4": (lambda: _rand(1, [8] * 4, [1, 4, 4, 4, 1]), 1e-8),
     "sum_d6_n16": (lambda: _sum_case(2, 5, 6, 16, 6), 1e-6),
     "decaying_03": (lambda: _decaying(3, [5, 4, 6, 3]), 0.3),
@@ -217,7 +228,12 @@ def test_schemes_mixed_loo_and_accuracy(ctxs, scheme):
         Qg, Rg, ng = T.tt_orthogonalize(c, scheme, [up(c, a) for a in A], 1e-5)
         assert ng == no
         loo = T.loss_of_orthogonality(c, Qg)
-        assert loo <= max(10 * loo_o, 1e-6) + 1e-5, (prec, loo, loo_o)
+        # Section 3.4: LOO = O(delta) for the stable schemes.  A reduced-
+        # precision rounding may keep one singular value fewer or more than
+        # the oracle next to the threshold (ranks within one), which moves a
+        # rounded vector by up to delta ||x|| (the TT-round contract), so the
+        # slack is a small multiple of delta, not delta itself
+        assert loo <= max(10 * loo_o, 1e-6) + 2 * 1e-5, (prec, loo, loo_o)
         assert np.allclose(Rg, Ro, atol=1e-4)
 
 

@@ -87,10 +87,15 @@ def _spd(n, seed, kappa=1e2, dtype=np.float64):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed_tf32"])
-@pytest.mark.parametrize("n", [1, 5, 31, 32, 33, 100, 257, 400])
-def test_cholesky_inverse_blocked(prec, n):
+@pytest.mark.parametrize("n,nb", [(1, 0), (5, 0), (31, 0), (32, 0), (33, 0), (100, 0), (160, 0), (161, 0), (255, 0),
+                                  (256, 0), (257, 0), (400, 0), (600, 0), (100, 32), (257, 64), (400, 128),
+                                  (400, 96)])
+def test_cholesky_inverse_blocked(prec, n, nb, monkeypatch):
+    # nb = 0: the block size the library picks (one CTA up to 256 / 160,
+    # autotuned blocks above); nb > 0 forces blocks of that size
     from paper_2211_08770_gb300 import build
     build.build()
+    monkeypatch.setenv("TTGB_CHOL_NB", str(nb))
     c = T.Ctx(0, prec)
     tdt = torch.float64 if prec == "fp64" else torch.float32
     G = _spd(n, n, 1e2)
@@ -108,25 +113,27 @@ def test_cholesky_inverse_blocked(prec, n):
     c.close()
 
 
-def test_cholesky_inverse_drops_dependent_rows():
+@pytest.mark.parametrize("n,nb,dep", [(70, 0, (40, 65)), (70, 32, (40, 65)), (300, 64, (40, 65, 150, 299))])
+def test_cholesky_inverse_drops_dependent_rows(n, nb, dep, monkeypatch):
     from paper_2211_08770_gb300 import build
     build.build()
+    monkeypatch.setenv("TTGB_CHOL_NB", str(nb))
     c = T.Ctx(0, "fp64")
     rng = np.random.default_rng(3)
-    X = rng.standard_normal((70, 200))
-    X[40] = X[3] - 2 * X[7]          # exactly dependent rows
-    X[65] = X[10]
+    X = rng.standard_normal((n, 2 * n + 60))
+    for i, d in enumerate(dep):       # exactly dependent rows
+        X[d] = X[3 + i] - 2 * X[7 + i] if i % 2 == 0 else X[10 + i]
     G = X @ X.T
     Gd = torch.tensor(G, device="cuda")
     L = torch.empty_like(Gd)
     Ti = torch.empty_like(Gd)
-    nd = T.tt_cholesky_inverse(c, 70, Gd.data_ptr(), L.data_ptr(), Ti.data_ptr(), 0.0, 1e-12)
-    assert nd == 2
+    nd = T.tt_cholesky_inverse(c, n, Gd.data_ptr(), L.data_ptr(), Ti.data_ptr(), 0.0, 1e-12)
+    assert nd == len(dep)
     Lh, Th = L.cpu().numpy(), Ti.cpu().numpy()
-    assert np.all(Lh[:, 40] == 0) and np.all(Lh[:, 65] == 0)
-    assert np.all(Th[40] == 0) and np.all(Th[:, 65] == 0)
+    for d in dep:
+        assert np.all(Lh[:, d] == 0) and np.all(Th[d] == 0) and np.all(Th[:, d] == 0)
     assert np.linalg.norm(Lh @ Lh.T - G) <= 1e-12 * np.linalg.norm(G)
-    keep = [i for i in range(70) if i not in (40, 65)]
+    keep = [i for i in range(n) if i not in dep]
     Q = Th[keep] @ X
-    assert np.allclose(Q @ Q.T, np.eye(68), atol=1e-10)
+    assert np.allclose(Q @ Q.T, np.eye(n - len(dep)), atol=1e-10)
     c.close()

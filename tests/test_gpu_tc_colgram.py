@@ -20,13 +20,21 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("m,n", [(32, 1), (100, 8), (4096, 400), (25600, 400), (25600, 64), (777, 130), (64, 512)])
+@pytest.mark.parametrize("m,n", [(32, 1), (100, 8), (4096, 400), (25600, 400), (25600, 64), (777, 130), (777, 132),
+                                 (64, 512), (3, 20)])
 def test_tc_column_gram(ctx, m, n):
     g = torch.Generator(device="cpu").manual_seed(m * 31 + n)
     Xh = torch.randn(m, n, generator=g, dtype=torch.float32)
     Xh[:, : n // 3] *= 0.01  # columns of very different norms, as in the left sweep
     X = Xh.cuda()
     G = torch.full((n, n), float("nan"), device="cuda", dtype=torch.float32)
+    if (4 * n) % 16:
+        # a row stride that is not a multiple of 16 bytes cannot be a TMA
+        # tensor map: refused before any launch
+        with pytest.raises(T.TTError) as e:
+            T.tt_gram_f32(ctx, n, m, X.data_ptr(), n, G.data_ptr(), 2)
+        assert e.value.name == "TT_ERR_ARG"
+        return
     T.tt_gram_f32(ctx, n, m, X.data_ptr(), n, G.data_ptr(), 2)
     torch.cuda.synchronize()
     Gd = G.cpu().numpy().astype(np.float64)
