@@ -96,6 +96,8 @@ typedef struct {
     uint64_t svd_calls;        /* truncation SVDs actually computed */
     uint64_t certified_bonds;  /* bonds kept whole by the sigma_min certificate */
     uint64_t fallback_orth;    /* orthogonalizations that took the shifted path */
+    uint64_t svd_sweeps;       /* Jacobi sweeps of the truncation SVDs (counted
+                                  only while profiling is on: it costs a sync) */
 } tt_stats;
 
 /* Per-kernel timing of a context (tt_ctx_set_profiling): CUDA events are

@@ -56,6 +56,7 @@ void merge_lane(Ctx& root, Ctx& lane) {
     root.stats.svd_calls += lane.stats.svd_calls;
     root.stats.certified_bonds += lane.stats.certified_bonds;
     root.stats.fallback_orth += lane.stats.fallback_orth;
+    root.stats.svd_sweeps += lane.stats.svd_sweeps;
     lane.stats = tt_stats{};
     for (auto& r : lane.recs) {
         ProfRec q = r;

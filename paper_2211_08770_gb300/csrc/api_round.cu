@@ -207,6 +207,20 @@ struct Rounder {
         return lb;
     }
 
+    // Jacobi tolerances of the truncation SVD.  FP64 storage: rows
+    // orthogonal to the rounding floor of a length-b dot product (b u);
+    // rows below 4 sqrt(b) u ||R|| are rounding noise.  FP32 storage: R
+    // carries FP32 rounding (u_32 relative), so orthogonality beyond
+    // 64 u_32 cannot change the data's singular values, and rows below
+    // u_32 ||R|| are noise; the SVD still runs in FP64 and its rotations
+    // stay exactly orthogonal.
+    static double svd_tol(int b) {
+        return sizeof(T) == 8 ? std::max(1e-15, b * 1.1102230246251565e-16) : 64.0 * 5.960464477539063e-08;
+    }
+    static double svd_floor(int b) {
+        return sizeof(T) == 8 ? 4.0 * sqrt((double)b) * 1.1102230246251565e-16 : 5.960464477539063e-08;
+    }
+
     // truncation rank from sorted singular values (FP64, host)
     int trunc_rank(const std::vector<double>& s, double eps) {
         const int p = (int)s.size();
@@ -268,7 +282,7 @@ struct Rounder {
                 // R = Lp^T (b x b), SVD, truncate
                 transpose<T>(*c, b, b, Lp, Tmp);
                 c->stats.svd_calls++;
-                jacobi_svd<T>(*c, b, b, Tmp, Ub, SVt, sig, (T*)jwork);
+                jacobi_svd<T>(*c, b, b, Tmp, Ub, SVt, sig, (T*)jwork, svd_tol(b), svd_floor(b));
                 std::vector<double> hs(b);
                 TT_CUDA(cudaMemcpyAsync(hs.data(), sig, b * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
                 c->sync();
@@ -298,7 +312,7 @@ struct Rounder {
                     continue;
                 }
                 c->stats.svd_calls++;
-                jacobi_svd<T>(*c, m, b, X, Ub, SVt, sig, (T*)jwork);
+                jacobi_svd<T>(*c, m, b, X, Ub, SVt, sig, (T*)jwork, svd_tol(b), svd_floor(b));
                 std::vector<double> hsg(m);
                 TT_CUDA(cudaMemcpyAsync(hsg.data(), sig, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
                 c->sync();

@@ -68,14 +68,42 @@ tt_tensor* gs_step(Driver& D, const tt_tensor* a, int i, const tt_tensor* const*
     for (int j = 0; j <= i; ++j) col[j] = 0.0;
     Cur prev;
     prev.p = a;
+    std::vector<double> rk(i);
+    std::vector<double> al(i + 1);
+    std::vector<const tt_tensor*> xs(i + 1);
     for (int k = 0; k < (twice ? 2 : 1); ++k) {
         Cur p;
         p.p = prev.p;
-        for (int j = 0; j < i; ++j) {
-            const double rji = D.dot(modified ? p.p : prev.p, Q[j]);
-            col[j] += rji;
-            p.set_owned(D.axpy(p.p, -rji, Q[j]));
-            if (D.pol == TT_ROUND_EVERY_UPDATE) p.set_owned(D.round(p.p));
+        if (!modified && i > 0) {
+            // classical: every projection is against the same vector, so the
+            // i dots are one batched call; with one rounding per pass the
+            // i axpys are one concatenation [p, q_0, ..., q_{i-1}] with
+            // coefficients (1, -r_0, ..., -r_{i-1}), the same TT the
+            // successive axpys build
+            dot_many_internal(D.c, prev.p, i, Q, rk.data());
+            if (D.pol == TT_ROUND_PAPER) {
+                al[0] = 1.0;
+                xs[0] = prev.p;
+                for (int j = 0; j < i; ++j) {
+                    col[j] += rk[j];
+                    al[j + 1] = -rk[j];
+                    xs[j + 1] = Q[j];
+                }
+                p.set_owned(tt_add_internal(D.c, i + 1, al.data(), xs.data()));
+            } else {
+                for (int j = 0; j < i; ++j) {
+                    col[j] += rk[j];
+                    p.set_owned(D.axpy(p.p, -rk[j], Q[j]));
+                    p.set_owned(D.round(p.p));
+                }
+            }
+        } else {
+            for (int j = 0; j < i; ++j) {
+                const double rji = D.dot(p.p, Q[j]);
+                col[j] += rji;
+                p.set_owned(D.axpy(p.p, -rji, Q[j]));
+                if (D.pol == TT_ROUND_EVERY_UPDATE) p.set_owned(D.round(p.p));
+            }
         }
         if (D.pol == TT_ROUND_PAPER || i == 0) p.set_owned(D.round(p.p));
         // prev <- p (move ownership)

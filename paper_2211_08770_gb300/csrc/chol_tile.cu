@@ -57,6 +57,7 @@ struct TileT<float> {
         x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
     }
     __device__ __forceinline__ static float4 pack(const float* x) { return make_float4(x[0], x[1], x[2], x[3]); }
+    __device__ __forceinline__ static float rsqrt(float x) { return rsqrtf(x); }
 };
 template <>
 struct TileT<double> {
@@ -72,6 +73,7 @@ struct TileT<double> {
         x[0] = v.x; x[1] = v.y;
     }
     __device__ __forceinline__ static double2 pack(const double* x) { return make_double2(x[0], x[1]); }
+    __device__ __forceinline__ static double rsqrt(double x) { return 1.0 / sqrt(x); }
 };
 
 // element (r, c) of a swizzled 32 x 32 tile: chunk c / W of row r sits in
@@ -139,8 +141,10 @@ __device__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, const double* od
     for (int c = 0; c < 32; ++c) {
         const C piv = __shfl_sync(FULL, a[c], c);
         const bool keep = isfinite(piv) && piv > tau_c && piv > C(0);
-        const C d = keep ? sqrt(piv) : C(0);
-        const C inv = keep ? C(1) / d : C(0);
+        // reciprocal square root first: one special-function op on the
+        // pivot chain in FP32 (2 ulp; Cholesky's backward error is O(n u))
+        const C inv = keep ? TileT<C>::rsqrt(piv) : C(0);
+        const C d = piv * inv;
         invs[c] = inv;
         if (lane == c) {
             mypiv = piv;
@@ -166,13 +170,15 @@ __device__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, const double* od
             fs.minratio = fmin(fs.minratio, ratio);
         }
     }
-    // inverse: lane c solves column c, x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii
+    // inverse: lane c solves column c, x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii,
+    // L_ik read back from the tile by broadcast loads
+    __syncwarp();
     C x[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
         C s = (i == lane) ? C(1) : C(0);
 #pragma unroll
-        for (int k = 0; k < i; ++k) s = fma(-__shfl_sync(FULL, a[k], i), x[k], s);
+        for (int k = 0; k < i; ++k) s = fma(-tile[tix<C>(i, k)], x[k], s);
         x[i] = s * invs[i];
     }
     store_row<C>(DiT, lane, x);                // DiT row c = column c of T_qq
@@ -464,7 +470,7 @@ __global__ void chol_finish_kernel(int n, S* __restrict__ L, CholStatus* __restr
 
 template <class S, class C>
 constexpr int tile_nt() {
-    return 256;
+    return sizeof(C) == 4 ? 512 : 256;  // FP32: 16 warps share the tile products
 }
 
 template <class S, class C>

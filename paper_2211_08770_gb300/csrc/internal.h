@@ -93,9 +93,16 @@ int chol_tile_max();
 // One-sided Jacobi SVD of the rows of R (p x b, row-major, p <= b):
 // R = U diag(sigma) V^T.  Outputs U (p x p, row-major, columns sorted by
 // decreasing sigma), SVt (p x b, row-major, row i = sigma_i v_i^T, sorted),
-// sigma (p doubles, sorted).  work: p*b + p*p elements of S.
+// sigma (p doubles, sorted).  work: p*b + p*p doubles (W, U^T), FP64
+// arithmetic.  A pair of rows is left alone when |<x,y>| <= tol ||x|| ||y||
+// or when one row's norm is <= floor_rel ||R||_F (noise of the larger rows).
+// Rotations are exact orthogonal transforms, so U diag(sigma) V^T = R up to
+// rounding whatever the tolerance: the discarded rows' norms are exactly the
+// truncation error, and the tolerance only affects how close to optimal the
+// ranks are.
 template <class S>
-void jacobi_svd(Ctx& c, int p, int b, const S* R, S* U, S* SVt, double* sigma, S* work);
+void jacobi_svd(Ctx& c, int p, int b, const S* R, S* U, S* SVt, double* sigma, S* work, double tol,
+                double floor_rel);
 
 // sum of squares of n elements, FP64 accumulation, written to *out (device).
 template <class T>

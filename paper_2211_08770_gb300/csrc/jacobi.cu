@@ -35,9 +35,13 @@ __device__ __forceinline__ double wsum(double v) {
     return v;
 }
 
-// rotation zeroing <x, y>; false when the pair is already orthogonal to tol
-__device__ __forceinline__ bool rotation(double al, double be, double ga, double tol, double& cs, double& sn) {
-    if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) return false;
+// rotation zeroing <x, y>; false when the pair is already orthogonal to tol,
+// or when one of the rows is below the noise floor (squared norm <= floor2):
+// such a row carries rounding noise of the larger rows, not data, and
+// rotating against it only moves that noise around
+__device__ __forceinline__ bool rotation(double al, double be, double ga, double tol, double floor2, double& cs,
+                                         double& sn) {
+    if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be) || fmin(al, be) <= floor2) return false;
     const double zeta = (be - al) / (2.0 * ga);
     const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
     cs = 1.0 / sqrt(1.0 + t * t);
@@ -92,13 +96,15 @@ __device__ bool grid_barrier(unsigned* bar, unsigned& target, int* err) {
 template <int NT>
 __global__ void __launch_bounds__(NT)
 jacobi_coop_kernel(int p, int b, int kb, double* __restrict__ W, double* __restrict__ Ut, int max_sweeps,
-                   double tol, unsigned* bar, unsigned* rot, int* err) {
+                   double tol, double floor_rel, const double* __restrict__ f2, unsigned* bar, unsigned* rot,
+                   int* err) {
     extern __shared__ __align__(16) double js[];
     constexpr int NW = NT / 32;
     __shared__ double red[NW][3];
     __shared__ int s_rot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nblk = 2 * gridDim.x, rl = b + p;
+    const double floor2 = floor_rel * floor_rel * (*f2);
     unsigned target = 0;
     if (tid == 0) s_rot = 0;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -155,7 +161,7 @@ jacobi_coop_kernel(int p, int b, int kb, double* __restrict__ W, double* __restr
                         ga += red[w][2];
                     }
                     double cs, sn;
-                    if (rotation(al, be, ga, tol, cs, sn)) {
+                    if (rotation(al, be, ga, tol, floor2, cs, sn)) {
                         double* x = js + (long)a * rl;
                         double* y = js + (long)c * rl;
                         for (int e = sub * 32 + lane; e < rl; e += wpp * 32) {
@@ -186,8 +192,10 @@ jacobi_coop_kernel(int p, int b, int kb, double* __restrict__ W, double* __restr
 
 // one CTA: all row pairs in round-robin order, one warp per pair, in place in global memory
 __global__ void __launch_bounds__(1024)
-jacobi_small_kernel(int p, int b, double* __restrict__ W, double* __restrict__ Ut, int max_sweeps, double tol) {
+jacobi_small_kernel(int p, int b, double* __restrict__ W, double* __restrict__ Ut, int max_sweeps, double tol,
+                    double floor_rel, const double* __restrict__ f2) {
     __shared__ int s_rot;
+    const double floor2 = floor_rel * floor_rel * (*f2);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int pp = p + (p & 1);
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -208,7 +216,7 @@ jacobi_small_kernel(int p, int b, double* __restrict__ W, double* __restrict__ U
                     ga = fma(x, y, ga);
                 }
                 double cs, sn;
-                if (!rotation(wsum(al), wsum(be), wsum(ga), tol, cs, sn)) continue;
+                if (!rotation(wsum(al), wsum(be), wsum(ga), tol, floor2, cs, sn)) continue;
                 for (int q = lane; q < b; q += 32) {
                     const double x = wi[q], y = wj[q];
                     wi[q] = cs * x - sn * y;
@@ -233,10 +241,17 @@ jacobi_small_kernel(int p, int b, double* __restrict__ W, double* __restrict__ U
 
 template <class S>
 __global__ void __launch_bounds__(1024)
-jacobi_prep_kernel(int p, int b, const S* __restrict__ R, double* __restrict__ W, double* __restrict__ Ut) {
+jacobi_prep_kernel(int p, int b, const S* __restrict__ R, double* __restrict__ W, double* __restrict__ Ut,
+                   double* __restrict__ f2) {
     const long pb = (long)p * b, ppp = (long)p * p;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < pb; e += (long)gridDim.x * blockDim.x)
-        W[e] = (double)R[e];
+    double ss = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < pb; e += (long)gridDim.x * blockDim.x) {
+        const double v = (double)R[e];
+        W[e] = v;
+        ss = fma(v, v, ss);
+    }
+    ss = wsum(ss);
+    if ((threadIdx.x & 31) == 0 && ss != 0.0) atomicAdd(f2, ss);
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < ppp; e += (long)gridDim.x * blockDim.x)
         Ut[e] = (e / p == e % p) ? 1.0 : 0.0;
 }
@@ -280,24 +295,32 @@ jacobi_finish_kernel(int p, int b, const double* __restrict__ W, const double* _
 }  // namespace
 
 template <class S>
-void jacobi_svd(Ctx& c, int p, int b, const S* R, S* U, S* SVt, double* sigma, S* work) {
+void jacobi_svd(Ctx& c, int p, int b, const S* R, S* U, S* SVt, double* sigma, S* work, double tol,
+                double floor_rel) {
     if (p <= 0) return;
     if (p > 1024 || p > b) throw_status(TT_ERR_ARG, "jacobi_svd: need p <= min(b, 1024)");
     constexpr int kMaxSweeps = 40;
-    // a pair counts as orthogonal when |<x, y>| <= tol ||x|| ||y||.  Rounding
-    // in the dots leaves about b u of that ratio, so a fixed 1e-15 is never
-    // met for long rows and every sweep up to the limit runs; b u is (the
-    // one-sided Jacobi convergence test scaled by the row length)
-    const double kTol = std::max(1e-15, (double)b * 1.1102230246251565e-16);
     double* W = reinterpret_cast<double*>(work);
     double* Ut = W + (long)p * b;
     ProfScope ps(c, "jacobi_svd", 0.0, sizeof(S) * (2.0 * p * b + 2.0 * p * p));
+    // ||R||_F^2 (noise floor), barrier counter and per-sweep rotation counts
+    const size_t cbytes = 256 + sizeof(unsigned) * (1 + kMaxSweeps);
+    char* cbuf = (char*)c.alloc(cbytes);
+    struct Rel {
+        Ctx& c;
+        void* p;
+        size_t b;
+        ~Rel() { c.release(p, b); }
+    } rel{c, cbuf, cbytes};
+    TT_CUDA(cudaMemsetAsync(cbuf, 0, cbytes, c.stream));
+    double* f2 = (double*)cbuf;
+    unsigned* ctr = (unsigned*)(cbuf + 256);
     jacobi_prep_kernel<S><<<std::max(1, std::min(2 * c.sm_count, (int)(((long)p * b + 1023) / 1024))), 1024, 0,
-                            c.stream>>>(p, b, R, W, Ut);
+                            c.stream>>>(p, b, R, W, Ut, f2);
     TT_LAUNCHED(c);
     if (p <= 32) {
         const int threads = std::min(1024, std::max(32, ((p + 1) / 2) * 32));
-        jacobi_small_kernel<<<1, threads, 0, c.stream>>>(p, b, W, Ut, kMaxSweeps, kTol);
+        jacobi_small_kernel<<<1, threads, 0, c.stream>>>(p, b, W, Ut, kMaxSweeps, tol, floor_rel, f2);
         TT_LAUNCHED(c);
     } else {
         constexpr int NT = 256;
@@ -325,32 +348,31 @@ void jacobi_svd(Ctx& c, int p, int b, const S* R, S* U, S* SVt, double* sigma, S
         }
         const int m = ((p + kb - 1) / kb + 1) / 2;
         const size_t sm = smem_for(kb);
-        // barrier counter and per-sweep rotation counts
-        const size_t cbytes = sizeof(unsigned) * (1 + kMaxSweeps);
-        unsigned* ctr = (unsigned*)c.alloc(cbytes);
-        struct Rel {
-            Ctx& c;
-            void* p;
-            size_t b;
-            ~Rel() { c.release(p, b); }
-        } rel{c, ctr, cbytes};
-        TT_CUDA(cudaMemsetAsync(ctr, 0, cbytes, c.stream));
         int pa = p, ba = b, kba = kb, ms = kMaxSweeps;
-        double tol = kTol;
+        double tl = tol, fr = floor_rel;
         unsigned* bar = ctr;
         unsigned* rot = ctr + 1;
         int* err = c.tc_err;
-        void* args[] = {&pa, &ba, &kba, &W, &Ut, &ms, &tol, &bar, &rot, &err};
+        void* args[] = {&pa, &ba, &kba, &W, &Ut, &ms, &tl, &fr, &f2, &bar, &rot, &err};
         TT_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel<NT>, dim3(m), dim3(NT), args, sm,
                                             c.stream));
         TT_LAUNCHED(c);
+        if (c.prof) {  // diagnostics: sweeps run = rounds with rotations + the final check
+            unsigned h[kMaxSweeps];
+            TT_CUDA(cudaMemcpyAsync(h, rot, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
+            c.sync();
+            int sw = 0;
+            while (sw < kMaxSweeps && h[sw]) ++sw;
+            c.stats.svd_sweeps += std::min(sw + 1, kMaxSweeps);
+        }
     }
     const size_t smem = (size_t)p * (sizeof(double) + sizeof(int));
     jacobi_finish_kernel<S><<<1, 1024, smem, c.stream>>>(p, b, W, Ut, U, SVt, sigma);
     TT_LAUNCHED(c);
 }
 
-template void jacobi_svd<double>(Ctx&, int, int, const double*, double*, double*, double*, double*);
-template void jacobi_svd<float>(Ctx&, int, int, const float*, float*, float*, double*, float*);
+template void jacobi_svd<double>(Ctx&, int, int, const double*, double*, double*, double*, double*, double,
+                                 double);
+template void jacobi_svd<float>(Ctx&, int, int, const float*, float*, float*, double*, float*, double, double);
 
 }  // namespace ttgb
