@@ -26,6 +26,7 @@
 // timing the candidates on the first call (autotuned), unless fixed.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include <algorithm>
 #include <map>
@@ -127,33 +128,49 @@ struct FactorState {
 
 // Warp 0: factor the diagonal tile q in place (rank drop below tau), write
 // the transposed inverse to DiT and the inverse to TD (natural layout).
+// Lane r holds row r in registers.  Step c: the pivot comes from lane c,
+// column c is scaled, published in col[] and subtracted from the rows below
+// (16-byte broadcast reads of col; entries above the diagonal are zeroed at
+// their own step).  Kept out of line: inlined into the kernel, the compiler
+// schedules this dependent chain several times slower.
 template <class C>
-__device__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, const double* od, double tau, FactorState& fs) {
+__device__ __noinline__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, C* col, const double* od, double tau,
+                                         FactorState* fs) {
+    using TT = TileT<C>;
     const int lane = threadIdx.x & 31;
     C* tile = Lt + (long)tri(q, q) * 1024;
     C a[32];
     load_row<C>(a, tile, lane);
     C invs[32];
     const C tau_c = (C)tau;
-    C mypiv = C(0);   // lane c keeps pivot c: the status is formed after the loop,
-    bool mykeep = true;  // off the pivot chain
+    C mypiv = C(0);      // lane c keeps pivot c: the status is formed after
+    bool mykeep = true;  // the loop, off the pivot chain
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
         const C piv = __shfl_sync(FULL, a[c], c);
         const bool keep = isfinite(piv) && piv > tau_c && piv > C(0);
         // reciprocal square root first: one special-function op on the
         // pivot chain in FP32 (2 ulp; Cholesky's backward error is O(n u))
-        const C inv = keep ? TileT<C>::rsqrt(piv) : C(0);
-        const C d = piv * inv;
+        const C inv = keep ? TT::rsqrt(piv) : C(0);
         invs[c] = inv;
         if (lane == c) {
             mypiv = piv;
             mykeep = keep;
         }
         const C l = (lane > c) ? a[c] * inv : C(0);
-        a[c] = (lane == c) ? d : l;
+        a[c] = (lane == c) ? piv * inv : l;
+        col[lane] = l;
+        __syncwarp();
+        const typename TT::V* cv = reinterpret_cast<const typename TT::V*>(col);
 #pragma unroll
-        for (int k = c + 1; k < 32; ++k) a[k] = fma(-l, __shfl_sync(FULL, l, k), a[k]);
+        for (int j = (c + 1) / TT::W; j < TT::NCH; ++j) {
+            C l4[TT::W];
+            TT::unpack(cv[j], l4);
+#pragma unroll
+            for (int e = 0; e < TT::W; ++e)
+                if (j * TT::W + e > c) a[j * TT::W + e] = fma(-l, l4[e], a[j * TT::W + e]);
+        }
+        __syncwarp();
     }
     store_row<C>(tile, lane, a);
     {
@@ -165,25 +182,65 @@ __device__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, const double* od
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ratio = fmin(ratio, __shfl_xor_sync(FULL, ratio, o));
         if (lane == 0) {
-            if (nonfin) fs.nonfin = 1;
-            fs.ndrop += __popc(drop);
-            fs.minratio = fmin(fs.minratio, ratio);
+            if (nonfin) fs->nonfin = 1;
+            fs->ndrop += __popc(drop);
+            fs->minratio = fmin(fs->minratio, ratio);
         }
     }
-    // inverse: lane c solves column c, x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii,
-    // L_ik read back from the tile by broadcast loads
     __syncwarp();
+    // inverse: lane c solves column c, x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii,
+    // L_ik read back from the tile by broadcast loads, two partial sums
     C x[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
-        C s = (i == lane) ? C(1) : C(0);
+        C s0 = (i == lane) ? C(1) : C(0), s1 = C(0);
 #pragma unroll
-        for (int k = 0; k < i; ++k) s = fma(-tile[tix<C>(i, k)], x[k], s);
-        x[i] = s * invs[i];
+        for (int k = 0; k < i; ++k) {
+            if (k & 1) s1 = fma(-tile[tix<C>(i, k)], x[k], s1);
+            else s0 = fma(-tile[tix<C>(i, k)], x[k], s0);
+        }
+        x[i] = (s0 + s1) * invs[i];
     }
     store_row<C>(DiT, lane, x);                // DiT row c = column c of T_qq
     store_col<C>(TD + (long)q * 1024, lane, x);  // TD natural: (i, c) = x_i of lane c
     __syncwarp();
+}
+
+// the n x n block from the lower tiles (zeros above the diagonal), one
+// 16-byte chunk per item
+template <class S, class C, int NT>
+__device__ void store_lower(int n, int P, const C* Lt, S* out, long ld) {
+    using TT = TileT<C>;
+    const bool vec = ((ld % TT::W) == 0) && ((((uintptr_t)out) & 15) == 0);
+    const int nitem = P * P * 32 * TT::NCH;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < nitem; e += NT) {
+        const int tile = e / (32 * TT::NCH), r = (e / TT::NCH) & 31, ch = e % TT::NCH;
+        const int I = tile / P, J = tile % P;
+        const int gi = I * 32 + r, gj0 = J * 32 + ch * TT::W;
+        if (gi >= n || gj0 >= n) continue;
+        C v[TT::W];
+        if (I >= J) {
+            TT::unpack(*reinterpret_cast<const typename TT::V*>(Lt + (long)tri(I, J) * 1024 + r * 32 +
+                                                                  ((ch ^ (r & (TT::NCH - 1))) * TT::W)),
+                       v);
+            if (I == J) {
+#pragma unroll
+                for (int w = 0; w < TT::W; ++w)
+                    if (ch * TT::W + w > r) v[w] = C(0);
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < TT::W; ++w) v[w] = C(0);
+        }
+        if (vec && gj0 + TT::W <= n) {
+            *reinterpret_cast<typename TT::V*>(out + (long)gi * ld + gj0) = TT::pack(v);
+        } else {
+#pragma unroll
+            for (int w = 0; w < TT::W; ++w)
+                if (gj0 + w < n) out[(long)gi * ld + gj0 + w] = (S)v[w];
+        }
+    }
 }
 
 // Arguments of one factorization.  Standalone (ext == nullptr): the shift is
@@ -219,6 +276,7 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
     extern __shared__ __align__(16) unsigned char ct_smem[];
     __shared__ double od[TileT<C>::PMAX * 32];
     __shared__ double red[2 * NW];
+    __shared__ __align__(16) C colbuf[32];
     const int n = A.n;
     const int P = (n + 31) / 32;
     const int ntile = P * (P + 1) / 2;
@@ -262,27 +320,44 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
     }
     for (int i = tid; i < P * 32; i += NT) od[i] = (i < n) ? (double)A.od_src[(long)i * A.od_stride] + shift : 1.0;
 
-    // ---- load the lower tiles of G (+ shift on the diagonal); padding = identity
-    for (int t = warp; t < ntile * 32; t += NW) {
-        const int slot = t >> 5, r = t & 31;
-        int I = 0;
-        while ((I + 1) * (I + 2) / 2 <= slot) ++I;
-        const int J = slot - I * (I + 1) / 2;
-        const int gi = I * 32 + r, gj = J * 32 + lane;
-        C v;
-        if (gi < n && gj < n) {
-            v = (I == J && lane > r) ? C(0) : (C)A.G[(long)gi * A.ldg + gj];
-            if (gi == gj) v = (C)((double)v + addshift);
-        } else {
-            v = (gi == gj) ? C(1) : C(0);
+    // ---- load the lower tiles of G (+ shift on the diagonal); padding = identity.
+    // One 16-byte chunk (W consecutive columns of a tile row) per item,
+    // several loads in flight per thread
+    {
+        using TT = TileT<C>;
+        const bool vec = ((A.ldg % TT::W) == 0) && ((((uintptr_t)A.G) & 15) == 0);
+        const int nitem = ntile * 32 * TT::NCH;
+#pragma unroll 4
+        for (int e = tid; e < nitem; e += NT) {
+            const int slot = e / (32 * TT::NCH), r = (e / TT::NCH) & 31, ch = e % TT::NCH;
+            int I = 0;
+            while ((I + 1) * (I + 2) / 2 <= slot) ++I;
+            const int J = slot - I * (I + 1) / 2;
+            const int gi = I * 32 + r, gj0 = J * 32 + ch * TT::W;
+            C v[TT::W];
+            if (vec && gi < n && gj0 + TT::W <= n) {
+                TT::unpack(*reinterpret_cast<const typename TT::V*>(A.G + (long)gi * A.ldg + gj0), v);
+            } else {
+#pragma unroll
+                for (int w = 0; w < TT::W; ++w)
+                    v[w] = (gi < n && gj0 + w < n) ? (C)A.G[(long)gi * A.ldg + gj0 + w] : C(0);
+            }
+#pragma unroll
+            for (int w = 0; w < TT::W; ++w) {
+                const int gj = gj0 + w;
+                if (gi >= n || gj >= n) v[w] = (gi == gj) ? C(1) : C(0);
+                else if (I == J && gj > gi) v[w] = C(0);
+                else if (gi == gj) v[w] = (C)((double)v[w] + addshift);
+            }
+            *reinterpret_cast<typename TT::V*>(Lt + (long)slot * 1024 + r * 32 + ((ch ^ (r & (TT::NCH - 1))) * TT::W)) =
+                TT::pack(v);
         }
-        Lt[(long)slot * 1024 + tix<C>(r, lane)] = v;
     }
     __syncthreads();
 
     FactorState fs{0, 0, 1e300};
     // ---- Cholesky, right-looking by panels, diagonal factor one panel ahead
-    if (warp == 0) factor_diag<C>(n, 0, Lt, DiT, TD, od, tau, fs);
+    if (warp == 0) factor_diag<C>(n, 0, Lt, DiT, TD, colbuf, od, tau, &fs);
     __syncthreads();
     for (int p = 0; p < P; ++p) {
         const int R = P - 1 - p;
@@ -312,7 +387,7 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
             tile_fma<C>(acc, a, PT);
             store_row<C>(tile, lane, acc);
             __syncwarp();
-            factor_diag<C>(n, p + 1, Lt, DiT + 0, TD, od, tau, fs);
+            factor_diag<C>(n, p + 1, Lt, DiT, TD, colbuf, od, tau, &fs);
         }
         // tasks 1..ntask-1 in (I, K) order over I = p+1.., K = p+1..I; task 0 is (p+1, p+1)
         for (int t = 1 + (NW > 1 ? warp - 1 : 0); t < ntask; t += (NW > 1 ? NW - 1 : 1)) {
@@ -334,61 +409,61 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
     }
 
     // ---- L out (lower tiles; the strictly upper part of the block zeroed)
-    for (int t = warp; t < P * P * 32; t += NW) {
-        const int I = (t >> 5) / P, J = (t >> 5) % P, r = t & 31;
-        const int gi = I * 32 + r, gj = J * 32 + lane;
-        if (gi < n && gj < n) {
-            C v = C(0);
-            if (I > J || (I == J && lane <= r)) v = Lt[(long)tri(I, J) * 1024 + tix<C>(r, lane)];
-            A.L[(long)gi * A.ldl + gj] = (S)v;
-        }
-    }
+    store_lower<S, C, NT>(n, P, Lt, A.L, A.ldl);
     __syncthreads();
 
-    // ---- in-place inversion, last block column first
-    for (int J = P - 1; J >= 0; --J) {
-        if (J < P - 1) {
-            // Y_I = sum_{K=J+1..I} T_IK L_KJ into PT slot I - J - 1
-            for (int I = J + 1 + warp; I < P; I += NW) {
-                C acc[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) acc[j] = C(0);
-                for (int K = J + 1; K <= I; ++K) {
-                    C a[32];
-                    load_row<C>(a, Lt + (long)tri(I, K) * 1024, lane);
-                    tile_fma<C>(acc, a, Lt + (long)tri(K, J) * 1024);
+    // ---- in-place inversion by doubling: the diagonal tiles hold T_JJ, then
+    // level s merges inverted neighbours [a, a+s) and [a+s, b) with
+    //   U = L21 T11 (over L21), then T21 = -T22 U (over U),
+    // every output tile one warp, held in registers across the barrier
+    // that precedes its store (so the in-place reads are complete).  The
+    // serial depth is 2 (P - 1) tile products instead of P (P + 1) / 2.
+    static_assert(TileT<C>::PMAX * TileT<C>::PMAX <= 4 * NW, "one inversion task per warp");
+    for (int e = tid; e < P * 1024; e += NT) Lt[(long)tri(e >> 10, e >> 10) * 1024 + (e & 1023)] = TD[e];
+    __syncthreads();
+    for (int sz = 1; sz < P; sz *= 2) {
+        // this warp's task (merge start a, output tile I, J), if any
+        int a0 = -1, I = 0, J = 0;
+        {
+            int t = warp;
+            for (int a = 0; a + sz < P; a += 2 * sz) {
+                const int sr = min(sz, P - a - sz);
+                if (t < sr * sz) {
+                    a0 = a;
+                    I = a + sz + t / sz;
+                    J = a + t % sz;
+                    break;
                 }
-                store_row<C>(PT + (long)(I - J - 1) * 1024, lane, acc);
-            }
-            __syncthreads();
-            // T_IJ = -Y_I T_JJ over L_IJ
-            for (int I = J + 1 + warp; I < P; I += NW) {
-                C a[32], acc[32];
-                load_row<C>(a, PT + (long)(I - J - 1) * 1024, lane);
-#pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    a[k] = -a[k];
-                    acc[k] = C(0);
-                }
-                tile_fma<C>(acc, a, TD + (long)J * 1024);
-                store_row<C>(Lt + (long)tri(I, J) * 1024, lane, acc);
+                t -= sr * sz;
             }
         }
-        // the diagonal block of T
-        for (int e = tid; e < 1024; e += NT) Lt[(long)tri(J, J) * 1024 + e] = TD[(long)J * 1024 + e];
-        __syncthreads();
+        for (int phase = 0; phase < 2; ++phase) {
+            C acc[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = C(0);
+            if (a0 >= 0) {
+                // phase 0: U_IJ = sum_{K=J}^{a0+sz-1} L_IK T_KJ
+                // phase 1: T_IJ = -sum_{K=a0+sz}^{I} T_IK U_KJ
+                const int k0 = phase == 0 ? J : a0 + sz;
+                const int k1 = phase == 0 ? a0 + sz - 1 : I;
+                for (int K = k0; K <= k1; ++K) {
+                    C x[32];
+                    load_row<C>(x, Lt + (long)tri(I, K) * 1024, lane);
+                    if (phase == 1) {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) x[k] = -x[k];
+                    }
+                    tile_fma<C>(acc, x, Lt + (long)tri(K, J) * 1024);
+                }
+            }
+            __syncthreads();
+            if (a0 >= 0) store_row<C>(Lt + (long)tri(I, J) * 1024, lane, acc);
+            __syncthreads();
+        }
     }
 
     // ---- T out
-    for (int t = warp; t < P * P * 32; t += NW) {
-        const int I = (t >> 5) / P, J = (t >> 5) % P, r = t & 31;
-        const int gi = I * 32 + r, gj = J * 32 + lane;
-        if (gi < n && gj < n) {
-            C v = C(0);
-            if (I > J || (I == J && lane <= r)) v = Lt[(long)tri(I, J) * 1024 + tix<C>(r, lane)];
-            A.T[(long)gi * A.ldt + gj] = (S)v;
-        }
-    }
+    store_lower<S, C, NT>(n, P, Lt, A.T, A.ldt);
     if (tid == 0) {
         if (A.ext) {
             if (fs.ndrop) atomicAdd(&A.st->ndrop, fs.ndrop);

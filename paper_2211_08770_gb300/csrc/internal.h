@@ -141,6 +141,13 @@ void scatter_blocks(Ctx& c, const BlockList& list, int n, long dst_ld_b, long ds
 template <class T>
 void axpy(Ctx& c, long n, double alpha, const T* x, T* y);  // y += alpha x
 
+// FP32 CUDA-core GEMM / split-K Gram with 128 x 128 tiles (same contracts
+// as gemm() and gram()); false (nothing launched) when a pointer is not
+// 16-byte aligned or a leading dimension (batch stride) not a multiple of 4.
+bool sgemm(Ctx& c, bool tA, bool tB, int M, int N, int K, float alpha, const float* A, long lda, const float* B,
+           long ldb, float beta, float* C, long ldc, int batch, long sA, long sB, long sC);
+bool sgram(Ctx& c, bool rows, int n, long K, const float* X, long ldx, float* G);
+
 // tcgen05 TF32 Gram of the rows of X (n x K, row-major): G = X X^T (lower
 // tiles), split-K, FP32 accumulation in TMEM, atomically added into G (FP32,
 // zeroed first).  Returns false when the shape is not supported.

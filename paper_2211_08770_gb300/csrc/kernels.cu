@@ -133,6 +133,9 @@ void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, lo
         throw_status(TT_ERR_ARG, "gemm with K = 0 and beta != 0");
     }
     if (batch > 65535) throw_status(TT_ERR_ARG, "gemm batch too large");
+    if constexpr (sizeof(T) == 4) {
+        if (sgemm(c, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch, sA, sB, sC)) return;
+    }
     ProfScope ps(c, sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", 2.0 * M * N * (double)K * batch,
                  sizeof(T) * ((double)M * K + (double)K * N + 2.0 * M * N) * batch);
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch);
@@ -142,6 +145,9 @@ void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, lo
 
 template <class T, class S>
 void gram(Ctx& c, bool rows, int n, long K, const T* X, long ldx, S* G) {
+    if constexpr (sizeof(T) == 4 && sizeof(S) == 4) {
+        if (sgram(c, rows, n, K, X, ldx, G)) return;
+    }
     TT_CUDA(cudaMemsetAsync(G, 0, sizeof(S) * (size_t)n * n, c.stream));
     if (n <= 0 || K <= 0) return;
     const int tiles = (n + GBM - 1) / GBM;
