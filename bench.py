@@ -54,6 +54,12 @@ def roofline_for(fam, prof, peaks, src):
         return "alu", prof["flops"] / secs / 1e12, peak, "TFLOP/s", "152 SMs x 128 FP32 lanes x 2 x max SM clock"
     if fam in ("gemm_f64", "gram_f64"):
         return "alu", prof["flops"] / secs / 1e12, 1.25, "TFLOP/s", "nominal GB300 FP64 rate"
+    if fam == "chol_inv":
+        # the r x r Cholesky + inverse: single-CTA (latency-bound) factors of the
+        # diagonal blocks plus CUDA-core GEMMs; the roofline is the FP32 ALU of the GPU
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        return "alu", prof["flops"] / secs / 1e12, peak, "TFLOP/s", (
+            "152 SMs x 128 FP32 lanes x 2 x max SM clock (the kernel is latency-bound on few SMs)")
     return "hbm", prof["bytes"] / secs / 1e9, peaks["hbm_gbs"], "GB/s", "%s HBM copy bandwidth" % src
 
 
