@@ -221,6 +221,72 @@ struct Rounder {
         return sizeof(T) == 8 ? 4.0 * sqrt((double)b) * 1.1102230246251565e-16 : 5.960464477539063e-08;
     }
 
+    // Truncation of bond k for FP32 data by the FP32 column Jacobi: R (p x b,
+    // row-major, ldr = b) with its columns given as the rows of Wsrc (b x p).
+    // The kept left vectors U_r are re-orthonormalized (one Cholesky QR pass)
+    // and core_{k+1} <- (U_r^T R) core_{k+1}: an exact orthogonal projection.
+    // Its error ||R - U_r U_r^T R||_F is measured (FP64 accumulation) and the
+    // rank raised until it is <= eps, so the rounding bound holds whatever
+    // the FP32 SVD's accuracy; FP32 rotations only cost optimality of the
+    // rank near the threshold.  Used for p >= kSvd32Min, where the FP64
+    // multi-CTA Jacobi takes tens of milliseconds.  qmul: core_k <- core_k U_r
+    // (else core_k <- U_r, when Q = I).  False: not taken (nothing done).
+    static constexpr int kSvd32Min = 96;
+    bool trunc_f32(int m, int p, int b, const T* Wsrc, long ldw, const T* R, double eps, int k, long NR,
+                   bool qmul) {
+        if constexpr (sizeof(T) != 4) {
+            return false;
+        } else {
+            if (p < kSvd32Min) return false;
+            if (!jacobi_cols_f32(*c, b, p, Wsrc, ldw, (float*)jwork, (float*)Ub, sig, 8.0 * sqrt((double)p) * ug_fb,
+                                 ug_fb))
+                return false;
+            std::vector<double> hs(b);
+            TT_CUDA(cudaMemcpyAsync(hs.data(), sig, b * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            c->sync();
+            const double err2_before = err2;
+            int rp = std::min(trunc_rank(hs, eps), p);
+            err2 = err2_before;
+            T* Uk = Ub;                 // sorted unit columns, p x b (ld b)
+            T* Uo = SVt;                // orthonormal U_r, p x rp (ld rp)
+            T* S = Tmp == R ? Lf[1] : Tmp;  // U_r^T R, rp x b (ld b)
+            T* E = G;                   // R - U_r S
+            // FP32 rounding of S = U_r^T R and of R itself leaves about
+            // sqrt(p) u_32 ||R|| in any FP32 truncation: the guard accepts
+            // residuals within that of eps (it catches SVD subspace errors,
+            // not the storage precision)
+            sumsq<T>(*c, (long)p * b, R, dsc + 13);
+            double r2 = 0.0;
+            TT_CUDA(cudaMemcpyAsync(&r2, dsc + 13, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            double res2 = 0.0;
+            for (int attempt = 0;; ++attempt) {
+                gram<T, T>(*c, false, rp, p, Uk, b, G);
+                chol_inv<T, T>(*c, rp, G, Lf[2], Ti[2], 0.0, 8.0 * ug_fb * sqrt((double)rp), next_st());
+                mm(false, true, p, rp, rp, Uk, b, Ti[2], rp, Uo, rp);
+                mm(true, false, rp, b, p, Uo, rp, R, b, S, b);
+                TT_CUDA(cudaMemcpyAsync(E, R, sizeof(T) * (size_t)p * b, cudaMemcpyDeviceToDevice, c->stream));
+                gemm<T>(*c, false, false, p, b, rp, T(-1), Uo, rp, S, b, T(1), E, b);
+                sumsq<T>(*c, (long)p * b, E, dsc + 14);
+                TT_CUDA(cudaMemcpyAsync(&res2, dsc + 14, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+                c->sync();
+                const double noise2 = 16.0 * p * ug_fb * ug_fb * r2;
+                if (res2 <= eps * eps + noise2 || rp >= p || attempt >= 6) break;
+                rp = std::min(p, rp + std::max(1, rp / 8));
+            }
+            err2 += res2;
+            if (qmul) {
+                mm(false, false, m, rp, b, core[k], b, Uo, rp, spare, rp);
+                std::swap(core[k], spare);
+            } else {
+                TT_CUDA(cudaMemcpyAsync(core[k], Uo, sizeof(T) * (size_t)p * rp, cudaMemcpyDeviceToDevice, c->stream));
+            }
+            mm(false, false, rp, (int)NR, b, S, b, core[k + 1], NR, spare, NR);
+            std::swap(core[k + 1], spare);
+            r[k + 1] = rp;
+            return true;
+        }
+    }
+
     // truncation rank from sorted singular values (FP64, host)
     int trunc_rank(const std::vector<double>& s, double eps) {
         const int p = (int)s.size();
@@ -282,6 +348,8 @@ struct Rounder {
                 // R = Lp^T (b x b), SVD, truncate
                 transpose<T>(*c, b, b, Lp, Tmp);
                 c->stats.svd_calls++;
+                // FP32 data: columns of R = rows of Lp, FP32 column Jacobi
+                if (trunc_f32(m, b, b, Lp, b, Tmp, eps, k, NR, true)) continue;
                 jacobi_svd<T>(*c, b, b, Tmp, Ub, SVt, sig, (T*)jwork, svd_tol(b), svd_floor(b));
                 std::vector<double> hs(b);
                 TT_CUDA(cudaMemcpyAsync(hs.data(), sig, b * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -312,6 +380,11 @@ struct Rounder {
                     continue;
                 }
                 c->stats.svd_calls++;
+                // FP32 data: columns of X = rows of X^T (b x m, in Tmp)
+                if constexpr (sizeof(T) == 4) {
+                    transpose<T>(*c, b, m, X, Tmp);
+                    if (trunc_f32(m, m, b, Tmp, m, X, eps, k, NR, false)) continue;
+                }
                 jacobi_svd<T>(*c, m, b, X, Ub, SVt, sig, (T*)jwork, svd_tol(b), svd_floor(b));
                 std::vector<double> hsg(m);
                 TT_CUDA(cudaMemcpyAsync(hsg.data(), sig, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

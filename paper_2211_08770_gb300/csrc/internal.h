@@ -104,6 +104,16 @@ template <class S>
 void jacobi_svd(Ctx& c, int p, int b, const S* R, S* U, S* SVt, double* sigma, S* work, double tol,
                 double floor_rel);
 
+// FP32 one-sided Jacobi on the columns of R for FP32 data: W (nr x len,
+// row-major, ld_src) holds the columns of R as rows; on return sigma (nr
+// doubles, device) holds the column norms of the orthogonalized R sorted
+// decreasingly and U (len x nr, row-major) the matching unit columns
+// (orthogonal to about tol; callers re-orthonormalize what they keep).
+// Wwork: nr x round_up(len, 4) floats.  False (nothing launched) when the
+// rows do not fit one thread-block cluster's shared memory.
+bool jacobi_cols_f32(Ctx& c, int nr, int len, const float* Wsrc, long ld_src, float* Wwork, float* U,
+                     double* sigma, double tol, double floor_rel);
+
 // sum of squares of n elements, FP64 accumulation, written to *out (device).
 template <class T>
 void sumsq(Ctx& c, long n, const T* x, double* out);

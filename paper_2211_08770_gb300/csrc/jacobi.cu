@@ -20,6 +20,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 
 namespace ttgb {
@@ -374,5 +376,300 @@ void jacobi_svd(Ctx& c, int p, int b, const S* R, S* U, S* SVt, double* sigma, S
 template void jacobi_svd<double>(Ctx&, int, int, const double*, double*, double*, double*, double*, double,
                                  double);
 template void jacobi_svd<float>(Ctx&, int, int, const float*, float*, float*, double*, float*, double, double);
+
+
+// ---------------------------------------------------------------------------
+// FP32 column Jacobi for data stored in FP32 (TT_MIXED_TF32 / TT_FP32).
+//
+// The columns of R are orthogonalized (Hestenes: R V = U Sigma) without
+// accumulating V: the converged columns are sigma_i u_i, which is all the
+// truncation needs (the caller re-orthonormalizes the kept u_i and forms the
+// next core's factor as U^T R, an exact orthogonal projection, so the
+// truncation error is exactly the discarded part).  The rows handled here are
+// the columns of R (rows of W = R^T, nr rows of length len).
+//
+// R is FP32 data (relative rounding 2^-24), so FP32 rotations suffice; they
+// run at 64x the FP64 rate.  A thread-block cluster of C CTAs keeps all rows
+// in shared memory as 2C blocks of kb rows, two per CTA.  Each round a CTA
+// orthogonalizes its two blocks against each other (kb steps of kb disjoint
+// pairs, one warp per pair), the first round of a sweep also within each
+// block, then the blocks move to the next CTA of the circle schedule (every
+// block pair meets once in 2C - 1 rounds) through distributed shared memory.
+// Cluster barriers are hardware barriers: no spin-waits.
+namespace {
+
+namespace cg = cooperative_groups;
+
+constexpr int J32_NT = 512;
+constexpr int J32_MAXC = 8;
+
+struct J32Pair {
+    float* x;
+    float* y;
+};
+
+// one warp: rotate rows x, y (length len) if not orthogonal to tol; true if rotated
+__device__ __forceinline__ bool j32_rotate(float* x, float* y, int len, float tol, float floor2) {
+    const int lane = threadIdx.x & 31;
+    float al = 0.f, be = 0.f, ga = 0.f;
+    for (int e = lane; e < len; e += 32) {
+        const float u = x[e], v = y[e];
+        al = fmaf(u, u, al);
+        be = fmaf(v, v, be);
+        ga = fmaf(u, v, ga);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        al += __shfl_xor_sync(FULL, al, o);
+        be += __shfl_xor_sync(FULL, be, o);
+        ga += __shfl_xor_sync(FULL, ga, o);
+    }
+    if (ga == 0.f || fabsf(ga) <= tol * sqrtf(al * be) || fminf(al, be) <= floor2) return false;
+    const float zeta = (be - al) / (2.f * ga);
+    const float t = fabsf(zeta) > 1e15f ? 0.5f / zeta
+                                         : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+    const float cs = rsqrtf(1.f + t * t), sn = cs * t;
+    for (int e = lane; e < len; e += 32) {
+        const float u = x[e], v = y[e];
+        x[e] = cs * u - sn * v;
+        y[e] = sn * u + cs * v;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(J32_NT)
+jac32_kernel(int nr, int len, int kb, float* __restrict__ W, int max_sweeps, float tol, float floor_rel,
+             int* __restrict__ sweeps_out) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int me = (int)cl.block_rank();
+    extern __shared__ __align__(16) float js32[];
+    __shared__ int s_rot;
+    __shared__ double s_f2;
+    __shared__ int ids[2][J32_MAXC];  // block ids at the top / bottom of each CTA
+    const int tid = threadIdx.x, warp = tid >> 5, NW = J32_NT / 32;
+    const long bl = (long)kb * len;
+    float* A0 = js32;
+    float* A1 = js32 + bl;
+    float* B0 = js32 + 2 * bl;
+    float* B1 = js32 + 3 * bl;
+    auto rows_of = [&](int blk) { return max(0, min(kb, nr - blk * kb)); };
+    if (tid < C) {
+        ids[0][tid] = 2 * tid;
+        ids[1][tid] = 2 * tid + 1;
+    }
+    __syncthreads();
+    // load this CTA's two blocks; missing rows are zero
+    {
+        const int bt = ids[0][me], bb = ids[1][me];
+        for (long e = tid; e < 2 * bl; e += J32_NT) {
+            const int s = (int)(e / bl);
+            const long off = e % bl;
+            const int blk = s == 0 ? bt : bb;
+            const int r = (int)(off / len);
+            float v = 0.f;
+            if (r < rows_of(blk)) v = W[(long)(blk * kb + r) * len + off % len];
+            js32[e] = v;
+        }
+    }
+    // ||W||_F^2 over the cluster (noise floor)
+    {
+        double ss = 0.0;
+        for (long e = tid; e < 2 * bl; e += J32_NT) ss += (double)js32[e] * js32[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
+        if (tid == 0) s_f2 = 0.0;
+        __syncthreads();
+        if ((tid & 31) == 0) atomicAdd(&s_f2, ss);
+        __syncthreads();
+    }
+    cl.sync();
+    double f2 = 0.0;
+    for (int r = 0; r < C; ++r) f2 += *cl.map_shared_rank(&s_f2, r);
+    const float floor2 = (float)(floor_rel * floor_rel * f2);
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int s = 0; s < 2 * C - 1; ++s) {
+            const int n0 = rows_of(ids[0][me]), n1 = rows_of(ids[1][me]);
+            bool rot = false;
+            if (s == 0) {
+                // within each block: round-robin over kb (padded even) rows, both blocks at once
+                const int kp = kb + (kb & 1);
+                for (int st = 0; st < kp - 1; ++st) {
+                    for (int q = warp; q < kp; q += NW) {  // q < kp/2: block 0, else block 1
+                        const int b = q < kp / 2 ? 0 : 1;
+                        int i, j;
+                        rr_pair(kp, st, q - b * (kp / 2), i, j);
+                        const int nb = b ? n1 : n0;
+                        if (i < nb && j < nb) {
+                            float* base = b ? A1 : A0;
+                            rot |= j32_rotate(base + (long)i * len, base + (long)j * len, len, tol, floor2);
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            // between the blocks: kb steps of kb disjoint pairs (i, (i + st) mod kb)
+            for (int st = 0; st < kb; ++st) {
+                for (int i = warp; i < kb; i += NW) {
+                    const int j = (i + st) % kb;
+                    if (i < n0 && j < n1) rot |= j32_rotate(A0 + (long)i * len, A1 + (long)j * len, len, tol, floor2);
+                }
+                __syncthreads();
+            }
+            if (rot && (tid & 31) == 0) s_rot = 1;
+            if (C == 1) continue;
+            // circle move: top of 0 stays, bottom of 0 -> top of 1, top of k -> top of k+1,
+            // top of C-1 -> bottom of C-1, bottom of k+1 -> bottom of k
+            cl.sync();
+            {
+                const int srcT = me == 0 ? 0 : (me == 1 ? 0 : me - 1);
+                const int slotT = me == 0 ? 0 : (me == 1 ? 1 : 0);
+                const int srcB = me == C - 1 ? C - 1 : me + 1;
+                const int slotB = me == C - 1 ? 0 : 1;
+                const float* rT = cl.map_shared_rank(js32 + slotT * bl, srcT);
+                const float* rB = cl.map_shared_rank(js32 + slotB * bl, srcB);
+                const float4* rT4 = reinterpret_cast<const float4*>(rT);
+                const float4* rB4 = reinterpret_cast<const float4*>(rB);
+                float4* dT = reinterpret_cast<float4*>(B0);
+                float4* dB = reinterpret_cast<float4*>(B1);
+                for (long e = tid; e < bl / 4; e += J32_NT) {
+                    dT[e] = rT4[e];
+                    dB[e] = rB4[e];
+                }
+            }
+            cl.sync();
+            {
+                // new arrangement (all CTAs apply the same update)
+                __shared__ int nid[2][J32_MAXC];
+                if (tid < C) {
+                    const int k = tid;
+                    nid[0][k] = k == 0 ? ids[0][0] : (k == 1 ? ids[1][0] : ids[0][k - 1]);
+                    nid[1][k] = k == C - 1 ? ids[0][C - 1] : ids[1][k + 1];
+                }
+                __syncthreads();
+                if (tid < C) {
+                    ids[0][tid] = nid[0][tid];
+                    ids[1][tid] = nid[1][tid];
+                }
+                for (long e = tid; e < bl / 4; e += J32_NT) {
+                    reinterpret_cast<float4*>(A0)[e] = reinterpret_cast<const float4*>(B0)[e];
+                    reinterpret_cast<float4*>(A1)[e] = reinterpret_cast<const float4*>(B1)[e];
+                }
+                __syncthreads();
+            }
+        }
+        // converged when no CTA rotated in this sweep
+        cl.sync();
+        int any = 0;
+        for (int r = 0; r < C; ++r) any |= *cl.map_shared_rank(&s_rot, r);
+        cl.sync();
+        if (!any) {
+            ++sweep;
+            break;
+        }
+    }
+    // rows back to W
+    {
+        const int bt = ids[0][me], bb = ids[1][me];
+        for (long e = tid; e < 2 * bl; e += J32_NT) {
+            const int s = (int)(e / bl);
+            const long off = e % bl;
+            const int blk = s == 0 ? bt : bb;
+            const int r = (int)(off / len);
+            if (r < rows_of(blk)) W[(long)(blk * kb + r) * len + off % len] = js32[e];
+        }
+    }
+    if (me == 0 && tid == 0) *sweeps_out = sweep;
+}
+
+// sigma_i = ||row i|| (FP64 accumulation), sorted decreasingly; column r of U
+// (len x nr, row-major) = the r-th row by norm, normalized (zero if sigma = 0)
+__global__ void __launch_bounds__(1024)
+jac32_finish_kernel(int nr, int len, int ldw, const float* __restrict__ W, float* __restrict__ U,
+                    double* __restrict__ sigma) {
+    extern __shared__ __align__(16) unsigned char jf32_smem[];
+    double* sig = reinterpret_cast<double*>(jf32_smem);
+    int* perm = reinterpret_cast<int*>(sig + nr);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = w; i < nr; i += nw) {
+        double s = 0.0;
+        for (int t = lane; t < len; t += 32) s = fma((double)W[(long)i * ldw + t], (double)W[(long)i * ldw + t], s);
+        s = wsum(s);
+        if (lane == 0) sig[i] = sqrt(s);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        int rank = 0;
+        const double si = sig[i];
+        for (int j = 0; j < nr; ++j) rank += (sig[j] > si) || (sig[j] == si && j < i);
+        perm[rank] = i;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) sigma[r] = sig[perm[r]];
+    const long tot = (long)len * nr;
+    for (long e = threadIdx.x; e < tot; e += blockDim.x) {
+        const long t = e / nr, r = e % nr;
+        const int i = perm[r];
+        const double s = sig[i];
+        U[e] = s > 0.0 ? (float)((double)W[(long)i * ldw + t] / s) : 0.f;
+    }
+}
+
+}  // namespace
+
+bool jacobi_cols_f32(Ctx& c, int nr, int len, const float* Wsrc, long ld_src, float* Wwork, float* U,
+                     double* sigma, double tol, double floor_rel) {
+    if (nr <= 0 || len <= 0) return true;
+    const int len4 = (len + 3) & ~3;  // rows padded with zeros to 16 bytes for the block moves
+    // kb rows per block, C <= 8 CTAs with 4 block slots each in shared memory
+    const int kmax = (int)((200 * 1024) / (16L * len4));
+    if (kmax < 1) return false;
+    int kb = std::max(1, (nr + 2 * J32_MAXC - 1) / (2 * J32_MAXC));
+    kb = std::max(kb, std::min(4, (nr + 1) / 2));
+    if (kb > kmax) return false;
+    int C = (nr + 2 * kb - 1) / (2 * kb);
+    C = std::max(1, std::min(C, J32_MAXC));
+    if (2L * C * kb < nr) return false;
+    const size_t smem = 16ul * kb * len4;
+    static std::atomic<bool> attr{false};
+    set_smem_once(attr, jac32_kernel, 200 * 1024);
+    ProfScope ps(c, "jacobi_svd", 0.0, 4.0 * (2.0 * nr * len + (double)len * nr));
+    if (len4 != len) TT_CUDA(cudaMemsetAsync(Wwork, 0, sizeof(float) * (size_t)nr * len4, c.stream));
+    TT_CUDA(cudaMemcpy2DAsync(Wwork, len4 * sizeof(float), Wsrc, ld_src * sizeof(float), len * sizeof(float), nr,
+                              cudaMemcpyDeviceToDevice, c.stream));
+    int* sw = (int*)c.alloc(sizeof(int));
+    struct Rel {
+        Ctx& c;
+        void* p;
+        ~Rel() { c.release(p, sizeof(int)); }
+    } rel{c, sw};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(J32_NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    TT_CUDA(cudaLaunchKernelEx(&cfg, jac32_kernel, nr, len4, kb, Wwork, 30, (float)tol, (float)floor_rel, sw));
+    TT_LAUNCHED(c);
+    const size_t fsm = (size_t)nr * (sizeof(double) + sizeof(int));
+    jac32_finish_kernel<<<1, 1024, fsm, c.stream>>>(nr, len, len4, Wwork, U, sigma);
+    TT_LAUNCHED(c);
+    if (c.prof) {
+        int h = 0;
+        TT_CUDA(cudaMemcpyAsync(&h, sw, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        c.stats.svd_sweeps += h;
+    }
+    return true;
+}
 
 }  // namespace ttgb

@@ -15,7 +15,10 @@ namespace ttgb {
 // 64x64 output tile, BK = 16, 256 threads, 4x4 outputs per thread (strided
 // by 16 so that shared-memory reads broadcast).  MODE 0: plain (blockIdx.z
 // = batch).  MODE 1: Gram, only tiles with tile_row >= tile_col, blockIdx.z
-// = split of K, result atomically added into C of type CT.
+// = split of K, result atomically added into C of type CT.  MODE 2: split-K
+// of a plain product (few output tiles, long K: the contractions of a TT dot
+// against a low-rank tensor), alpha times each partial added atomically into
+// a zeroed C.
 namespace {
 
 constexpr int GBM = 64, GBN = 64, GBK = 16;
@@ -36,7 +39,7 @@ gemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda,
         B += blockIdx.z * sB;
         C += blockIdx.z * sC;
     } else {
-        if (blockIdx.x > blockIdx.y) return;  // upper tiles of a symmetric result
+        if (MODE == 1 && blockIdx.x > blockIdx.y) return;  // upper tiles of a symmetric result
         kbeg = (long)blockIdx.z * kchunk;
         kend = min(K, kbeg + kchunk);
         if (kbeg >= kend) return;
@@ -95,8 +98,10 @@ gemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda,
                 T v = alpha * acc[i][j];
                 if (beta != T(0)) v += beta * (T)C[gm * ldc + gn];
                 C[gm * ldc + gn] = (CT)v;
-            } else {
+            } else if (MODE == 1) {
                 atomicAdd(&C[gm * ldc + gn], (CT)acc[i][j]);
+            } else {
+                atomicAdd(&C[gm * ldc + gn], (CT)(alpha * acc[i][j]));
             }
         }
     }
@@ -140,6 +145,20 @@ void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, lo
                  sizeof(T) * ((double)M * K + (double)K * N + 2.0 * M * N) * batch);
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch);
     if (grid.y > 65535) throw_status(TT_ERR_ARG, "gemm M too large");
+    const long tiles = (long)grid.x * grid.y;
+    const long ksteps = (K + GBK - 1) / GBK;
+    if (batch == 1 && beta == T(0) && tiles < c.sm_count && ksteps >= 64) {
+        // few output tiles and a long contraction: split K over about two
+        // CTAs per SM (at least 16 k-steps each), partials added atomically
+        long splits = std::min<long>((2L * c.sm_count + tiles - 1) / tiles, ksteps / 16);
+        splits = std::min<long>(splits, 65535);
+        const long kchunk = ((ksteps + splits - 1) / splits) * GBK;
+        splits = (K + kchunk - 1) / kchunk;
+        TT_CUDA(cudaMemset2DAsync(C, ldc * sizeof(T), 0, N * sizeof(T), M, c.stream));
+        grid.z = (unsigned)splits;
+        launch_gemm<T, T, 2>(c, tA, tB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, 0, 0, kchunk);
+        return;
+    }
     launch_gemm<T, T, 0>(c, tA, tB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, K);
 }
 
