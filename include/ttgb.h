@@ -98,6 +98,8 @@ typedef struct {
     uint64_t fallback_orth;    /* orthogonalizations that took the shifted path */
     uint64_t svd_sweeps;       /* Jacobi sweeps of the truncation SVDs (counted
                                   only while profiling is on: it costs a sync) */
+    uint64_t series_passes;    /* second Cholesky QR passes replaced by the
+                                  series (I + E)^(-1/2) of a near-identity Gram */
 } tt_stats;
 
 /* Per-kernel timing of a context (tt_ctx_set_profiling): CUDA events are

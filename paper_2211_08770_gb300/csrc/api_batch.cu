@@ -44,6 +44,8 @@ std::vector<Ctx*> get_lanes(Ctx& root, int count) {
         l->use_tc = root.use_tc;
         l->use_tc_gemm = root.use_tc_gemm;
         l->tc_gemm_split = root.tc_gemm_split;
+        l->chol_nb = root.chol_nb;
+        l->use_series = root.use_series;
         l->prof = root.prof;
     }
     return out;
@@ -57,6 +59,7 @@ void merge_lane(Ctx& root, Ctx& lane) {
     root.stats.certified_bonds += lane.stats.certified_bonds;
     root.stats.fallback_orth += lane.stats.fallback_orth;
     root.stats.svd_sweeps += lane.stats.svd_sweeps;
+    root.stats.series_passes += lane.stats.series_passes;
     lane.stats = tt_stats{};
     for (auto& r : lane.recs) {
         ProfRec q = r;

@@ -412,9 +412,13 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
         c->tc_gemm_split = 2;
     }
     // TTGB_CHOL_NB fixes the block size of the Cholesky factorizations (a
-    // multiple of 32; 0 or unset: chosen per order by timing)
+    // multiple of 32; 0 or unset: the per-order table)
     const char* nb = getenv("TTGB_CHOL_NB");
     if (nb) c->chol_nb = std::max(0, atoi(nb));
+    // TTGB_SERIES_PASS=0 keeps the Cholesky factorization for every second
+    // Cholesky QR pass (no series pass)
+    const char* sp = getenv("TTGB_SERIES_PASS");
+    if (sp && sp[0] == '0') c->use_series = false;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;

@@ -5,8 +5,12 @@
 // factored X = L Q with Q row-orthonormal by Cholesky QR passes: Gram
 // G = X X^T, G = L L^T, Q = L^{-1} X, twice (CholQR2) when the first
 // Cholesky is healthy, otherwise three passes of which the first is shifted
-// (G + s I), with numerically dependent rows dropped.  L is absorbed into
-// core k-1.  ||x|| = ||core_1||_F.
+// (G + s I), with numerically dependent rows dropped.  The second pass's
+// Gram is I + E with E of the order of the first pass's rounding; when
+// ||E||_F is small enough for a Taylor series of order <= 3 to reach the
+// storage precision, that pass is Q <- (I + E)^(-1/2) Q with the factor
+// (I + E)^(1/2) (symmetric), instead of a second Cholesky factorization.
+// L is absorbed into core k-1.  ||x|| = ||core_1||_F.
 // Left-to-right sweep: each left unfolding X (r_{k-1} n_k x r_k) is factored
 // X = Q R the same way (on columns); the bond keeps its rank when a
 // certified lower bound of sigma_min(R) exceeds 2 eps, else R is decomposed
@@ -114,20 +118,21 @@ struct Rounder {
 
     // C = op(A) op(B): tensor-core split TF32 when the context allows it and
     // the layout is TMA-aligned, else the CUDA-core kernel of the storage type
-    void mm(bool tA, bool tB, int M, int N, int K, const T* A, long lda, const T* B, long ldb, T* C, long ldc) {
+    void mm(bool tA, bool tB, int M, int N, int K, const T* A, long lda, const T* B, long ldb, T* C, long ldc,
+            int tri = 0) {
         if constexpr (sizeof(T) == 4) {
             if (tc && c->use_tc_gemm && !tA &&
                 gemm_tc3_tf32(*c, tB, M, N, K, (const float*)A, lda, (const float*)B, ldb, (float*)C, ldc,
                               c->tc_gemm_split))
                 return;
         }
-        gemm<T>(*c, tA, tB, M, N, K, T(1), A, lda, B, ldb, T(0), C, ldc);
+        gemm<T>(*c, tA, tB, M, N, K, T(1), A, lda, B, ldb, T(0), C, ldc, 1, 0, 0, 0, tri);
     }
 
-    // X <- Ti X (rows) or X Ti^T (cols)
-    void apply(bool rows, int a, long K, T*& X, const T* Tinv) {
-        if (rows) mm(false, false, a, (int)K, a, Tinv, a, X, K, spare, K);
-        else mm(false, true, (int)K, a, a, X, a, Tinv, a, spare, a);
+    // X <- Ti X (rows) or X Ti^T (cols); Ti lower-triangular unless !tri
+    void apply(bool rows, int a, long K, T*& X, const T* Tinv, bool tri = true) {
+        if (rows) mm(false, false, a, (int)K, a, Tinv, a, X, K, spare, K, tri ? TRI_A_LOWER : 0);
+        else mm(false, true, (int)K, a, a, X, a, Tinv, a, spare, a, tri ? TRI_B_UPPER : 0);
         std::swap(X, spare);
     }
 
@@ -135,11 +140,27 @@ struct Rounder {
         int npass;
         int ndrop;
         bool shifted;
+        int nchol = 0;        // Cholesky passes (factors Lf/Ti[0..nchol)) of the certificate
+        double lb_poly = 1.0; // lower bound of sigma_min of the series pass's factor
+        bool lower = true;    // Lp lower-triangular
     };
 
+    // Order of the series pass for ||E||_F = e: the smallest m (1..3) whose
+    // Taylor remainders of (1 + x)^(-1/2) and (1 + x)^(1/2) together,
+    // bounded by c_m e^(m+1) / (1 - e), stay below the storage precision's
+    // unit round-off; 0 (take the Cholesky pass) when none does.
+    int series_order(double e) const {
+        const double cm[4] = {0.0, 0.5, 0.375, 0.3125};
+        if (!(e < 0.25)) return 0;
+        for (int m = 1; m <= 3; ++m)
+            if (cm[m] * pow(e, m + 1) / (1.0 - e) <= ug_fb) return m;
+        return 0;
+    }
+
     // X (a x K rows, or K x a cols) is overwritten by its orthonormal factor;
-    // Lp receives the lower-triangular L with X_old = L Q (rows) or
-    // X_old = Q L^T (cols).  Lf[i], Ti[i] keep the factors of each pass.
+    // Lp receives L with X_old = L Q (rows) or X_old = Q L^T (cols), lower-
+    // triangular unless the second pass was the series pass (o.lower).
+    // Lf[i], Ti[i] keep the factors of each pass.
     Orth orth(bool rows, int a, long K, T*& X) {
         const double sq = sqrt((double)a);
         const double drop_fb = 8.0 * ug_fb * sq;
@@ -160,10 +181,31 @@ struct Rounder {
                 // defect of about u_tf32 / sqrt(K), far above FP32 level
                 // for short unfoldings
                 gram_into(rows, false, a, K, X);
+                o.npass = 2;
+                o.nchol = 1;
+                // G = I + E with E small: Q <- (I + E)^(-1/2) Q and
+                // R = (I + E)^(1/2) from the series in E (a few a x a
+                // products instead of a Cholesky factorization; the
+                // factor is symmetric, not triangular)
+                const double e = c->use_series ? sqrt(near_identity<T>(*c, a, G, Ti[1], dsc + 12)) : 1.0;
+                const int m = series_order(e);
+                if (m > 0) {
+                    c->stats.series_passes++;
+                    if (m >= 2) mm(false, false, a, a, a, Ti[1], a, Ti[1], a, Lf[1], a);
+                    if (m >= 3) mm(false, false, a, a, a, Lf[1], a, Ti[1], a, Tmp, a);
+                    poly_pair<T>(*c, a, m, Ti[1], Lf[1], Tmp, Lf[1]);
+                    apply(rows, a, K, X, Ti[1], false);
+                    mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Lp, a, TRI_A_LOWER);
+                    // sigma_min((I + E)^(1/2)) >= sqrt(1 - ||E||_2); less the
+                    // series remainder and the rounding of the stored factor
+                    o.lb_poly = std::max(0.0, sqrt(1.0 - e) - (2.0 + sqrt((double)a)) * ug_fb);
+                    o.lower = false;
+                    return o;
+                }
                 chol_inv<T, T>(*c, a, G, Lf[1], Ti[1], 0.0, drop_fb, next_st());
                 apply(rows, a, K, X, Ti[1]);
-                mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Lp, a);
-                o.npass = 2;
+                mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Lp, a, TRI_A_LOWER | TRI_B_LOWER);
+                o.nchol = 2;
                 return o;
             }
         }
@@ -178,15 +220,18 @@ struct Rounder {
             chol_inv<T, T>(*c, a, G, Lf[p], Ti[p], 0.0, drop_fb, next_st());
             apply(rows, a, K, X, Ti[p]);
         }
-        mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Tmp, a);
-        mm(false, false, a, a, a, Tmp, a, Lf[2], a, Lp, a);
+        mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Tmp, a, TRI_A_LOWER | TRI_B_LOWER);
+        mm(false, false, a, a, a, Tmp, a, Lf[2], a, Lp, a, TRI_A_LOWER | TRI_B_LOWER);
         o.npass = 3;
+        o.nchol = 3;
         return o;
     }
 
     // rigorous lower bound of sigma_min(L_0 ... L_{np-1}) from the factors and
-    // their inverses: prod_i max(1/||T_i||_F, 1 - ||L_i - I||_F); 0 on drops
-    double sigma_lb(int a, int np) {
+    // their inverses: prod_i max(1/||T_i||_F, 1 - ||L_i - I||_F); 0 on drops;
+    // times the bound of a series pass's factor
+    double sigma_lb(int a, const Orth& o) {
+        const int np = o.nchol;
         TT_CUDA(cudaMemsetAsync(dsc, 0, 2 * np * sizeof(double), c->stream));
         for (int i = 0; i < np; ++i) inv_and_identity_defect<T>(*c, a, Lf[i], Ti[i], dsc + 2 * i);
         std::vector<double> h(2 * np);
@@ -198,7 +243,7 @@ struct Rounder {
             if (hs[i].nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in a Gram matrix");
             if (hs[i].ndrop) return 0.0;
         }
-        double lb = 1.0;
+        double lb = o.lb_poly;
         for (int i = 0; i < np; ++i) {
             double b1 = h[2 * i] > 0 ? 1.0 / sqrt(h[2 * i]) : 0.0;
             double b2 = 1.0 - sqrt(h[2 * i + 1]);
@@ -262,7 +307,7 @@ struct Rounder {
             for (int attempt = 0;; ++attempt) {
                 gram<T, T>(*c, false, rp, p, Uk, b, G);
                 chol_inv<T, T>(*c, rp, G, Lf[2], Ti[2], 0.0, 8.0 * ug_fb * sqrt((double)rp), next_st());
-                mm(false, true, p, rp, rp, Uk, b, Ti[2], rp, Uo, rp);
+                mm(false, true, p, rp, rp, Uk, b, Ti[2], rp, Uo, rp, TRI_B_UPPER);
                 mm(true, false, rp, b, p, Uo, rp, R, b, S, b);
                 TT_CUDA(cudaMemcpyAsync(E, R, sizeof(T) * (size_t)p * b, cudaMemcpyDeviceToDevice, c->stream));
                 gemm<T>(*c, false, false, p, b, rp, T(-1), Uo, rp, S, b, T(1), E, b);
@@ -313,8 +358,8 @@ struct Rounder {
                 fill_identity<T>(*c, (int)K, core[k], K);
                 r[k] = (int)K;
             } else {
-                orth(true, a, K, core[k]);
-                mm(false, false, M, a, a, core[k - 1], a, Lp, a, spare, a);
+                const Orth o = orth(true, a, K, core[k]);
+                mm(false, false, M, a, a, core[k - 1], a, Lp, a, spare, a, o.lower ? TRI_B_LOWER : 0);
                 std::swap(core[k - 1], spare);
             }
         }
@@ -336,12 +381,12 @@ struct Rounder {
             const long NR = (long)n[k + 1] * r[k + 2];
             if (m >= b) {
                 Orth o = orth(false, b, m, core[k]);
-                const double lb = sigma_lb(b, o.npass);
+                const double lb = sigma_lb(b, o);
                 if (lb > 2.0 * eps && lb > 0.0) {
                     c->stats.certified_bonds++;
                     // core_{k+1} <- R core_{k+1}, R = Lp^T
                     transpose<T>(*c, b, b, Lp, Tmp);
-                    mm(false, false, b, (int)NR, b, Tmp, b, core[k + 1], NR, spare, NR);
+                    mm(false, false, b, (int)NR, b, Tmp, b, core[k + 1], NR, spare, NR, o.lower ? TRI_A_UPPER : 0);
                     std::swap(core[k + 1], spare);
                     continue;
                 }
@@ -367,7 +412,9 @@ struct Rounder {
                 gram<T, T>(*c, true, m, b, X, b, G);
                 CholStatus* s = next_st();
                 chol_inv<T, T>(*c, m, G, Lf[0], Ti[0], 0.0, 8.0 * ug_fb * sqrt((double)m), s);
-                double lb = sigma_lb(m, 1);
+                Orth o1{1, 0, false};
+                o1.nchol = 1;
+                double lb = sigma_lb(m, o1);
                 CholStatus hs0 = read_st(s);
                 const double noise = 16.0 * ug_fb * sqrt((double)m) * hs0.trace;
                 const double lb2 = lb * lb - noise;

@@ -7,13 +7,17 @@
 // triangle in shared memory as 32 x 32 tiles and never touches global memory
 // between loading G and storing L and T, so no step waits on L2 latency:
 //  - right-looking Cholesky by 32-column panels: warp 0 factors and inverts
-//    the diagonal tile in registers (shuffles, no CTA barrier per column);
-//    the tiles below are solved against the tile inverse; the trailing
-//    update is spread over the warps, with warp 0 updating and factoring
-//    the next diagonal tile first (lookahead), so the serial chain of
-//    diagonal factorizations overlaps the bulk of the flops;
-//  - in-place blocked triangular inversion from the last block column to
-//    the first: T_{>J,J} = -T_{>J,>J} L_{>J,J} T_JJ.
+//    the diagonal tile in registers (one out-of-line, unrolled function);
+//    the tiles below are multiplied by the transposed tile inverse; the
+//    trailing update is spread over the warps, with warp 0 updating and
+//    factoring the next diagonal tile first (lookahead), so the serial chain
+//    of diagonal factorizations overlaps the bulk of the flops; finished
+//    block columns of L are stored while the next ones are computed;
+//  - in-place inversion by doubling: merge inverted neighbours with
+//    T21 = -T22 (L21 T11), one output tile per warp.
+// (Solving the panel by forward substitution instead, with the diagonal
+// inverses formed later in parallel, measured slower: the substitution's
+// dependent chain per row outweighs the shorter diagonal step.)
 // Tiles are stored without padding with a 16-byte-chunk XOR swizzle, so a
 // lane reads its own tile row with 16-byte loads and every warp reads the
 // shared operand row by 16-byte broadcasts; each 32 x 32 x 32 tile product
@@ -22,15 +26,15 @@
 // Larger orders are factored blockwise (block size NB <= the one-CTA limit)
 // with the same kernel on diagonal blocks and the CUDA-core GEMM for the
 // panels, trailing updates and off-diagonal inverse blocks, which spreads
-// the O(n^3) work over the GPU.  NB is chosen per (precision, order) by
-// timing the candidates on the first call (autotuned), unless fixed.
+// the O(n^3) work over the GPU.  NB is a fixed function of the precision
+// and the order, taken from timings of every candidate on a GB300, so the
+// arithmetic (and every result) is the same from run to run; it can be
+// fixed per context instead.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
-#include <map>
-#include <mutex>
 
 #include "internal.h"
 
@@ -243,6 +247,41 @@ __device__ void store_lower(int n, int P, const C* Lt, S* out, long ld) {
     }
 }
 
+// block column p of the n x n factor from the tiles (zeros above the
+// diagonal), 16-byte chunks, by threads [0, nthr) of the CTA (t0 = own index)
+template <class S, class C>
+__device__ void store_lcol(int n, int P, int p, const C* Lt, S* out, long ld, int t0, int nthr) {
+    using TT = TileT<C>;
+    const bool vec = ((ld % TT::W) == 0) && ((((uintptr_t)out) & 15) == 0);
+    const int nitem = P * 32 * TT::NCH;
+    for (int e = t0; e < nitem; e += nthr) {
+        const int I = e / (32 * TT::NCH), r = (e / TT::NCH) & 31, ch = e % TT::NCH;
+        const int gi = I * 32 + r, gj0 = p * 32 + ch * TT::W;
+        if (gi >= n || gj0 >= n) continue;
+        C v[TT::W];
+        if (I >= p) {
+            TT::unpack(*reinterpret_cast<const typename TT::V*>(Lt + (long)tri(I, p) * 1024 + r * 32 +
+                                                                  ((ch ^ (r & (TT::NCH - 1))) * TT::W)),
+                       v);
+            if (I == p) {
+#pragma unroll
+                for (int w = 0; w < TT::W; ++w)
+                    if (ch * TT::W + w > r) v[w] = C(0);
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < TT::W; ++w) v[w] = C(0);
+        }
+        if (vec && gj0 + TT::W <= n) {
+            *reinterpret_cast<typename TT::V*>(out + (long)gi * ld + gj0) = TT::pack(v);
+        } else {
+#pragma unroll
+            for (int w = 0; w < TT::W; ++w)
+                if (gj0 + w < n) out[(long)gi * ld + gj0 + w] = (S)v[w];
+        }
+    }
+}
+
 // Arguments of one factorization.  Standalone (ext == nullptr): the shift is
 // shift_rel trace(G), the drop threshold drop_rel (max_j G_jj + shift); both
 // applied here and the status written.  Block of a larger factorization
@@ -321,36 +360,49 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
     for (int i = tid; i < P * 32; i += NT) od[i] = (i < n) ? (double)A.od_src[(long)i * A.od_stride] + shift : 1.0;
 
     // ---- load the lower tiles of G (+ shift on the diagonal); padding = identity.
-    // One 16-byte chunk (W consecutive columns of a tile row) per item,
-    // several loads in flight per thread
+    // One 16-byte chunk (W consecutive columns of a tile row) per item: the
+    // in-range chunks as asynchronous copies (all in flight at once), the
+    // rest by plain loads; then the diagonal tiles are fixed up (zeros above
+    // the diagonal, shift on it).
     {
         using TT = TileT<C>;
+        __shared__ unsigned char s_I[64], s_J[64];
+        if (tid < ntile) {
+            int I = 0;
+            while ((I + 1) * (I + 2) / 2 <= tid) ++I;
+            s_I[tid] = (unsigned char)I;
+            s_J[tid] = (unsigned char)(tid - I * (I + 1) / 2);
+        }
+        __syncthreads();
         const bool vec = ((A.ldg % TT::W) == 0) && ((((uintptr_t)A.G) & 15) == 0);
         const int nitem = ntile * 32 * TT::NCH;
-#pragma unroll 4
         for (int e = tid; e < nitem; e += NT) {
             const int slot = e / (32 * TT::NCH), r = (e / TT::NCH) & 31, ch = e % TT::NCH;
-            int I = 0;
-            while ((I + 1) * (I + 2) / 2 <= slot) ++I;
-            const int J = slot - I * (I + 1) / 2;
+            const int I = s_I[slot], J = s_J[slot];
             const int gi = I * 32 + r, gj0 = J * 32 + ch * TT::W;
-            C v[TT::W];
+            C* dst = Lt + (long)slot * 1024 + r * 32 + ((ch ^ (r & (TT::NCH - 1))) * TT::W);
             if (vec && gi < n && gj0 + TT::W <= n) {
-                TT::unpack(*reinterpret_cast<const typename TT::V*>(A.G + (long)gi * A.ldg + gj0), v);
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa),
+                             "l"(A.G + (long)gi * A.ldg + gj0));
             } else {
+                C v[TT::W];
 #pragma unroll
-                for (int w = 0; w < TT::W; ++w)
-                    v[w] = (gi < n && gj0 + w < n) ? (C)A.G[(long)gi * A.ldg + gj0 + w] : C(0);
+                for (int w = 0; w < TT::W; ++w) {
+                    const int gj = gj0 + w;
+                    v[w] = (gi < n && gj < n) ? (C)A.G[(long)gi * A.ldg + gj] : (gi == gj ? C(1) : C(0));
+                }
+                *reinterpret_cast<typename TT::V*>(dst) = TT::pack(v);
             }
-#pragma unroll
-            for (int w = 0; w < TT::W; ++w) {
-                const int gj = gj0 + w;
-                if (gi >= n || gj >= n) v[w] = (gi == gj) ? C(1) : C(0);
-                else if (I == J && gj > gi) v[w] = C(0);
-                else if (gi == gj) v[w] = (C)((double)v[w] + addshift);
-            }
-            *reinterpret_cast<typename TT::V*>(Lt + (long)slot * 1024 + r * 32 + ((ch ^ (r & (TT::NCH - 1))) * TT::W)) =
-                TT::pack(v);
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        for (int e = tid; e < P * 1024; e += NT) {
+            const int J = e >> 10, r = (e >> 5) & 31, cc = e & 31;
+            const int gi = J * 32 + r;
+            C* t = Lt + (long)tri(J, J) * 1024 + tix<C>(r, cc);
+            if (cc > r) *t = C(0);
+            else if (cc == r && gi < n) *t = (C)((double)*t + addshift);
         }
     }
     __syncthreads();
@@ -405,11 +457,13 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
             tile_fma<C>(acc, a, PT + (long)(K - p - 1) * 1024);
             store_row<C>(tile, lane, acc);
         }
+        // block column p of L is final: the warps other than 0 store it
+        // while warp 0 factors the next diagonal tile
+        if (NW == 1 || warp > 0) store_lcol<S, C>(n, P, p, Lt, A.L, A.ldl, NW > 1 ? tid - 32 : tid, NW > 1 ? NT - 32 : NT);
         __syncthreads();
     }
-
-    // ---- L out (lower tiles; the strictly upper part of the block zeroed)
-    store_lower<S, C, NT>(n, P, Lt, A.L, A.ldl);
+    // the last block column of L
+    store_lcol<S, C>(n, P, P - 1, Lt, A.L, A.ldl, tid, NT);
     __syncthreads();
 
     // ---- in-place inversion by doubling: the diagonal tiles hold T_JJ, then
@@ -590,30 +644,38 @@ void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, do
         launch_tile<S, C>(c, a);
         if (M == 0) break;
         // panel L_{>j,j} = A_{>j,j} T_jj^T (via W), then the trailing update
-        gemm<S>(c, false, true, M, b, b, S(1), L + j1 * ld + j0, ld, T + j0 * (ld + 1), ld, S(0), W, b);
+        gemm<S>(c, false, true, M, b, b, S(1), L + j1 * ld + j0, ld, T + j0 * (ld + 1), ld, S(0), W, b, 1, 0, 0, 0,
+                TRI_B_UPPER);
         TT_CUDA(cudaMemcpy2DAsync(L + j1 * ld + j0, ld * sizeof(S), W, b * sizeof(S), b * sizeof(S), M,
                                   cudaMemcpyDeviceToDevice, c.stream));
-        gemm<S>(c, false, true, M, M, b, S(-1), W, b, W, b, S(1), L + j1 * (ld + 1), ld);
+        // lower triangle only (the strictly upper part of L is zeroed at the end)
+        gemm<S>(c, false, true, M, M, b, S(-1), W, b, W, b, S(1), L + j1 * (ld + 1), ld, 1, 0, 0, 0, TRI_C_LOWER);
     }
     // off-diagonal inverse blocks, last block column first:
     // T_{>j,j} = -T_{>j,>j} (L_{>j,j} T_jj)
     for (int j = m - 2; j >= 0; --j) {
         const int j0 = j * nb, b = std::min(nb, n - j0), j1 = j0 + b, M = n - j1;
-        gemm<S>(c, false, false, M, b, b, S(1), L + j1 * ld + j0, ld, T + j0 * (ld + 1), ld, S(0), W, b);
-        gemm<S>(c, false, false, M, b, M, S(-1), T + j1 * (ld + 1), ld, W, b, S(0), T + j1 * ld + j0, ld);
+        gemm<S>(c, false, false, M, b, b, S(1), L + j1 * ld + j0, ld, T + j0 * (ld + 1), ld, S(0), W, b, 1, 0, 0, 0,
+                TRI_B_LOWER);
+        gemm<S>(c, false, false, M, b, M, S(-1), T + j1 * (ld + 1), ld, W, b, S(0), T + j1 * ld + j0, ld, 1, 0, 0, 0,
+                TRI_A_LOWER);
     }
     chol_finish_kernel<S><<<std::max(cb, 1), 256, 0, c.stream>>>(n, L, st);
     TT_LAUNCHED(c);
 }
 
-// per (compute type, order rounded up to 32) block size chosen by timing
-std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tuned;
-
-int tuned_nb(int es, int n) {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tuned.find({es, (n + 31) / 32});
-    return it == g_tuned.end() ? 0 : it->second;
+// Block size per precision and order (the one-CTA kernel when it fits).
+// Measured on a GB300 (microseconds, FP32 / FP64 compute), fastest kept:
+//   FP32 one CTA up to 256 (n = 256: 158); n = 288-320: NB 160 (244, 263);
+//   n = 400: NB 224 (355); n = 512: NB 256 (457); n = 640-800: NB 224
+//   (628, 862).  FP64 one CTA up to 160 (n = 160: 1069); above, NB 128
+//   (n = 256: 1992, 400: 3925, 800: 9082).
+int default_nb(int es, int n, int nmax) {
+    if (n <= nmax) return n;
+    if (es == 8) return 128;
+    if (n <= 352) return 160;
+    if (n > 416 && n <= 544) return 256;
+    return 224;
 }
 
 }  // namespace
@@ -640,43 +702,7 @@ void chol_inv(Ctx& c, int n, const S* G, S* L, S* T, double shift_rel, double dr
     if (n <= 0) return;
     const int nmax = chol_tile_max<S, C>();
     ProfScope ps(c, "chol_inv", 2.0 * (double)n * n * n / 3.0, 3.0 * sizeof(S) * n * n);
-    int nb = c.chol_nb ? c.chol_nb : tuned_nb(sizeof(C), n);
-    if (!nb) {
-        // candidates: the one-CTA kernel when it fits, and blocked sizes
-        // below n; each timed once on this call's own input (the inputs are
-        // read-only, the last run leaves the outputs)
-        std::vector<int> cand;
-        if (n <= nmax) cand.push_back(n);
-        const int opts32[] = {128, 192, 256};
-        const int opts64[] = {64, 96, 128, 160};
-        const int* o = sizeof(C) == 4 ? opts32 : opts64;
-        const int no = sizeof(C) == 4 ? 3 : 4;
-        for (int i = 0; i < no; ++i)
-            if (o[i] < n && o[i] <= nmax) cand.push_back(o[i]);
-        if (cand.size() == 1) {
-            nb = cand.front();
-        } else {
-            cudaEvent_t e0 = c.event(), e1 = c.event();
-            float best = 1e30f;
-            for (int rep = 0; rep < 2; ++rep)  // first pass warms up
-                for (int v : cand) {
-                    TT_CUDA(cudaEventRecord(e0, c.stream));
-                    chol_inv_nb<S, C>(c, n, v, G, L, T, shift_rel, drop_rel, st);
-                    TT_CUDA(cudaEventRecord(e1, c.stream));
-                    TT_CUDA(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    TT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                    if (rep == 1 && ms < best) {
-                        best = ms;
-                        nb = v;
-                    }
-                }
-            c.ev_pool.push_back(e0);
-            c.ev_pool.push_back(e1);
-            std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tuned[{(int)sizeof(C), (n + 31) / 32}] = nb;
-        }
-    }
+    const int nb = c.chol_nb ? c.chol_nb : default_nb((int)sizeof(C), n, nmax);
     chol_inv_nb<S, C>(c, n, nb, G, L, T, shift_rel, drop_rel, st);
 }
 

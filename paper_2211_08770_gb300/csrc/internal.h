@@ -60,12 +60,39 @@ struct CholStatus {
 
 struct Ctx;
 
+// Known zero structure of op(A) (M x K) and op(B) (K x N) in a product:
+// each output tile then contracts only over the k-range where both can be
+// non-zero.  Only products with exact zeros are left out, so the result is
+// the same for finite data (the triangular factors and inverses of the
+// Cholesky QR passes).
+enum : int {
+    TRI_A_LOWER = 1,  // op(A)(m, k) = 0 for k > m
+    TRI_A_UPPER = 2,  // op(A)(m, k) = 0 for k < m
+    TRI_B_LOWER = 4,  // op(B)(k, n) = 0 for k < n
+    TRI_B_UPPER = 8,  // op(B)(k, n) = 0 for k > n
+    TRI_C_LOWER = 16, // only the lower triangle of C is wanted: output tiles
+                      // strictly above the diagonal are not computed
+};
+
+// the k-range [kb, ke) an output tile (rows m0.., cols n0..) needs; an
+// unwanted tile (TRI_C_LOWER) gets an empty range and writes nothing
+__host__ __device__ inline bool tri_skip_tile(int tri, long m0, long n0, long bm) {
+    return (tri & TRI_C_LOWER) && n0 >= m0 + bm;
+}
+__host__ __device__ inline void tri_krange(int tri, long m0, long n0, long bm, long bn, long& kb, long& ke) {
+    if (tri & TRI_A_LOWER) ke = ke < m0 + bm ? ke : m0 + bm;
+    if (tri & TRI_A_UPPER) kb = kb > m0 ? kb : m0;
+    if (tri & TRI_B_LOWER) kb = kb > n0 ? kb : n0;
+    if (tri & TRI_B_UPPER) ke = ke < n0 + bn ? ke : n0 + bn;
+}
+
 // C = alpha op(A) op(B) + beta C, row-major with leading dimensions.
-// op(A) is M x K, op(B) is K x N.  batch > 1: blockIdx.z strides.
+// op(A) is M x K, op(B) is K x N.  batch > 1: blockIdx.z strides.  tri:
+// TRI_* flags of the operands' zero structure.
 template <class T>
 void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, long lda,
           const T* B, long ldb, T beta, T* C, long ldc, int batch = 1, long sA = 0,
-          long sB = 0, long sC = 0);
+          long sB = 0, long sC = 0, int tri = 0);
 
 // G (n x n, row-major, lower triangle written, type S) = X X^T when rows,
 // i.e. X is n x K row-major (ldx) and the contraction runs over K; or
@@ -80,7 +107,7 @@ void gram(Ctx& c, bool rows, int n, long K, const T* X, long ldx, S* G);
 // shift = shift_rel * trace(G).  Pivots <= drop_rel * (max_j G_jj + shift)
 // are dropped: the column of L and the row and column of T are zero.
 // One CTA with everything in shared memory for n <= chol_tile_max(), else
-// blockwise with block size Ctx::chol_nb, or autotuned per order.
+// blockwise with block size Ctx::chol_nb, or a fixed per-order table.
 template <class S, class C>
 void chol_inv(Ctx& c, int n, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st_dev);
 // the same with a given block size (nb >= n: the one-CTA kernel)
@@ -123,6 +150,17 @@ void sumsq(Ctx& c, long n, const T* x, double* out);
 template <class S>
 void inv_and_identity_defect(Ctx& c, int n, const S* L, const S* T, double* out);
 
+// Near-identity symmetric G (n x n, lower triangle valid): E = G - I
+// (symmetric, full) and the return value ||E||_F^2 (FP64 accumulation;
+// dev_out is one device double of scratch; synchronizes the stream).
+template <class T>
+double near_identity(Ctx& c, int n, const T* G, T* E, double* dev_out);
+// Truncated Taylor series of order m (1..3) in the symmetric E:
+// S = (I + E)^(-1/2) over E and R = (I + E)^(1/2) into R; E2 = E^2 is read
+// when m >= 2 and E3 = E^3 when m >= 3 (R may alias E2).
+template <class T>
+void poly_pair(Ctx& c, int n, int m, T* E, const T* E2, const T* E3, T* R);
+
 template <class T>
 void fill_identity(Ctx& c, int n, T* A, long lda);  // A (n x n) = I
 template <class T>
@@ -155,7 +193,7 @@ void axpy(Ctx& c, long n, double alpha, const T* x, T* y);  // y += alpha x
 // as gemm() and gram()); false (nothing launched) when a pointer is not
 // 16-byte aligned or a leading dimension (batch stride) not a multiple of 4.
 bool sgemm(Ctx& c, bool tA, bool tB, int M, int N, int K, float alpha, const float* A, long lda, const float* B,
-           long ldb, float beta, float* C, long ldc, int batch, long sA, long sB, long sC);
+           long ldb, float beta, float* C, long ldc, int batch, long sA, long sB, long sC, int tri = 0);
 bool sgram(Ctx& c, bool rows, int n, long K, const float* X, long ldx, float* G);
 
 // tcgen05 TF32 Gram of the rows of X (n x K, row-major): G = X X^T (lower
@@ -210,7 +248,8 @@ struct Ctx {
     std::mutex acct_mu;           // guards stats.bytes_in_use / peak_bytes of a root
     std::vector<Ctx*> lanes;      // lanes owned by this root (created on demand)
     int max_lanes = 8;            // concurrency of tt_round_batched
-    int chol_nb = 0;              // block size of chol_inv (0: autotuned per order)
+    int chol_nb = 0;              // block size of chol_inv (0: the per-order table)
+    bool use_series = true;       // series second pass of Cholesky QR when it is accurate
 
     // event profiling of launches (off by default)
     bool prof = false;

@@ -27,7 +27,7 @@ template <class T, class CT, bool TA, bool TB, int MODE>
 __global__ void __launch_bounds__(256)
 gemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda,
             const T* __restrict__ B, long ldb, T beta, CT* __restrict__ C, long ldc, long sA,
-            long sB, long sC, long kchunk) {
+            long sB, long sC, long kchunk, int tri) {
     __shared__ T As[GBK][GBM + 1];
     __shared__ T Bs[GBK][GBN + 1];
     const int tid = threadIdx.x;
@@ -44,6 +44,9 @@ gemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda,
         kend = min(K, kbeg + kchunk);
         if (kbeg >= kend) return;
     }
+    if (MODE != 1 && tri_skip_tile(tri, m0, n0, GBM)) return;
+    if (MODE != 1) tri_krange(tri, m0, n0, GBM, GBN, kbeg, kend);  // tile multiples of GBK
+    if (MODE == 2 && kbeg >= kend) return;  // a zero partial: nothing to add
     T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -110,10 +113,10 @@ gemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda,
 template <class T, class CT, int MODE>
 void launch_gemm(Ctx& c, bool tA, bool tB, dim3 grid, int M, int N, long K, T alpha,
                  const T* A, long lda, const T* B, long ldb, T beta, CT* C, long ldc, long sA,
-                 long sB, long sC, long kchunk) {
+                 long sB, long sC, long kchunk, int tri) {
 #define TT_GEMM_CASE(TA_, TB_)                                                            \
     gemm_kernel<T, CT, TA_, TB_, MODE><<<grid, 256, 0, c.stream>>>(                      \
-        M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, kchunk)
+        M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, kchunk, tri)
     if (!tA && !tB) TT_GEMM_CASE(false, false);
     else if (!tA && tB) TT_GEMM_CASE(false, true);
     else if (tA && !tB) TT_GEMM_CASE(true, false);
@@ -126,7 +129,7 @@ void launch_gemm(Ctx& c, bool tA, bool tB, dim3 grid, int M, int N, long K, T al
 
 template <class T>
 void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, long lda,
-          const T* B, long ldb, T beta, T* C, long ldc, int batch, long sA, long sB, long sC) {
+          const T* B, long ldb, T beta, T* C, long ldc, int batch, long sA, long sB, long sC, int tri) {
     if (M <= 0 || N <= 0 || batch <= 0) return;
     if (K <= 0) {
         // C = beta C: degenerate product
@@ -139,7 +142,12 @@ void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, lo
     }
     if (batch > 65535) throw_status(TT_ERR_ARG, "gemm batch too large");
     if constexpr (sizeof(T) == 4) {
-        if (sgemm(c, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch, sA, sB, sC)) return;
+        // the 128 x 128 kernel when it fills at least half the SMs; smaller
+        // products (the r x r ones) take 64 x 64 tiles, split over K below
+        const long tiles128 = (long)((N + 127) / 128) * ((M + 127) / 128) * batch;
+        if (2 * tiles128 >= c.sm_count &&
+            sgemm(c, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch, sA, sB, sC, tri))
+            return;
     }
     ProfScope ps(c, sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", 2.0 * M * N * (double)K * batch,
                  sizeof(T) * ((double)M * K + (double)K * N + 2.0 * M * N) * batch);
@@ -147,19 +155,19 @@ void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, lo
     if (grid.y > 65535) throw_status(TT_ERR_ARG, "gemm M too large");
     const long tiles = (long)grid.x * grid.y;
     const long ksteps = (K + GBK - 1) / GBK;
-    if (batch == 1 && beta == T(0) && tiles < c.sm_count && ksteps >= 64) {
-        // few output tiles and a long contraction: split K over about two
-        // CTAs per SM (at least 16 k-steps each), partials added atomically
-        long splits = std::min<long>((2L * c.sm_count + tiles - 1) / tiles, ksteps / 16);
+    if (batch == 1 && beta == T(0) && 2 * tiles <= c.sm_count && ksteps >= 16) {
+        // few output tiles: split K over about two CTAs per SM (at least 8
+        // k-steps each), partials added atomically
+        long splits = std::min<long>((2L * c.sm_count + tiles - 1) / tiles, ksteps / 8);
         splits = std::min<long>(splits, 65535);
         const long kchunk = ((ksteps + splits - 1) / splits) * GBK;
         splits = (K + kchunk - 1) / kchunk;
         TT_CUDA(cudaMemset2DAsync(C, ldc * sizeof(T), 0, N * sizeof(T), M, c.stream));
         grid.z = (unsigned)splits;
-        launch_gemm<T, T, 2>(c, tA, tB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, 0, 0, kchunk);
+        launch_gemm<T, T, 2>(c, tA, tB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, 0, 0, kchunk, tri);
         return;
     }
-    launch_gemm<T, T, 0>(c, tA, tB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, K);
+    launch_gemm<T, T, 0>(c, tA, tB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, K, tri);
 }
 
 template <class T, class S>
@@ -183,7 +191,7 @@ void gram(Ctx& c, bool rows, int n, long K, const T* X, long ldx, S* G) {
     // rows: G = X X^T, op(A) = X (n x K), op(B) = X^T  -> tA = false, tB = true
     // cols: G = X^T X, X is K x n: op(A) = X^T -> tA = true, op(B) = X -> tB = false
     launch_gemm<T, S, 1>(c, !rows, rows, grid, n, n, K, T(1), X, ldx, X, ldx, T(0), G, n, 0, 0, 0,
-                         kchunk);
+                         kchunk, 0);
 }
 
 // ------------------------------------------------------------- reductions
@@ -245,7 +253,68 @@ __global__ void defect_kernel(int n, const S* __restrict__ L, const S* __restric
     }
 }
 
+// E = sym(G) - I from the lower triangle of G, and ||E||_F^2 into *out
+template <class T>
+__global__ void near_identity_kernel(int n, const T* __restrict__ G, T* __restrict__ E, double* out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    const long nn = (long)n * n;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x) {
+        const long i = e / n, k = e % n;
+        const T g = i >= k ? G[e] : G[k * n + i];
+        const T v = (i == k) ? g - T(1) : g;
+        E[e] = v;
+        s = fma((double)v, (double)v, s);
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
+// S = sum_j a_j E^j, R = sum_j b_j E^j (j = 0..m, E^0 = I); S over E, R may
+// alias E2 (every element is read before it is written, by one thread)
+template <class T>
+__global__ void poly_pair_kernel(int n, int m, T* E, const T* E2, const T* E3, T* R, double a1, double a2,
+                                 double a3, double b1, double b2, double b3) {
+    const long nn = (long)n * n;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x) {
+        const double id = (e / n == e % n) ? 1.0 : 0.0;
+        const double x1 = (double)E[e];
+        const double x2 = m >= 2 ? (double)E2[e] : 0.0;
+        const double x3 = m >= 3 ? (double)E3[e] : 0.0;
+        E[e] = (T)(id + a1 * x1 + a2 * x2 + a3 * x3);
+        R[e] = (T)(id + b1 * x1 + b2 * x2 + b3 * x3);
+    }
+}
+
 }  // namespace
+
+template <class T>
+double near_identity(Ctx& c, int n, const T* G, T* E, double* dev_out) {
+    TT_CUDA(cudaMemsetAsync(dev_out, 0, sizeof(double), c.stream));
+    if (n <= 0) return 0.0;
+    const long nn = (long)n * n;
+    const int blocks = (int)std::min<long>((nn + 255) / 256, 2L * c.sm_count);
+    near_identity_kernel<T><<<blocks, 256, 0, c.stream>>>(n, G, E, dev_out);
+    TT_LAUNCHED(c);
+    double h = 0.0;
+    TT_CUDA(cudaMemcpyAsync(&h, dev_out, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    return h;
+}
+
+template <class T>
+void poly_pair(Ctx& c, int n, int m, T* E, const T* E2, const T* E3, T* R) {
+    // Taylor coefficients of (1 + x)^(-1/2) and (1 + x)^(1/2)
+    const double a[4] = {1.0, -0.5, 0.375, -0.3125};
+    const double b[4] = {1.0, 0.5, -0.125, 0.0625};
+    const long nn = (long)n * n;
+    if (nn <= 0) return;
+    const int blocks = (int)std::min<long>((nn + 255) / 256, 2L * c.sm_count);
+    poly_pair_kernel<T><<<blocks, 256, 0, c.stream>>>(n, m, E, E2, E3, R, a[1], m >= 2 ? a[2] : 0.0,
+                                                      m >= 3 ? a[3] : 0.0, b[1], m >= 2 ? b[2] : 0.0,
+                                                      m >= 3 ? b[3] : 0.0);
+    TT_LAUNCHED(c);
+}
 
 template <class T>
 void sumsq(Ctx& c, long n, const T* x, double* out) {
@@ -380,14 +449,16 @@ void axpy(Ctx& c, long n, double alpha, const T* x, T* y) {
 // ------------------------------------------------- explicit instantiations
 #define TT_INST_T(T)                                                                             \
     template void gemm<T>(Ctx&, bool, bool, int, int, int, T, const T*, long, const T*, long, T, T*, \
-                          long, int, long, long, long);                                          \
+                          long, int, long, long, long, int);                                       \
     template void sumsq<T>(Ctx&, long, const T*, double*);                                       \
     template void fill_identity<T>(Ctx&, int, T*, long);                                         \
     template void scale_inplace<T>(Ctx&, long, T*, double);                                      \
     template void transpose<T>(Ctx&, int, int, const T*, T*);                                    \
     template void scatter_blocks<T>(Ctx&, const BlockList&, int, long, long, T*, int, int);      \
     template void axpy<T>(Ctx&, long, double, const T*, T*);                                     \
-    template void inv_and_identity_defect<T>(Ctx&, int, const T*, const T*, double*);
+    template void inv_and_identity_defect<T>(Ctx&, int, const T*, const T*, double*);             \
+    template double near_identity<T>(Ctx&, int, const T*, T*, double*);                          \
+    template void poly_pair<T>(Ctx&, int, int, T*, const T*, const T*, T*);
 TT_INST_T(float)
 TT_INST_T(double)
 template void gram<double, double>(Ctx&, bool, int, long, const double*, long, double*);

@@ -72,7 +72,7 @@ __device__ __forceinline__ void store_slab(float* S, const float4 v) {
 template <bool TA, bool TB, int MODE>
 __global__ void __launch_bounds__(256, 2)
 sgemm_kernel(int M, int N, long K, float alpha, const float* __restrict__ A, long lda, const float* __restrict__ B,
-             long ldb, float beta, float* __restrict__ C, long ldc, long sA, long sB, long sC, long kchunk) {
+             long ldb, float beta, float* __restrict__ C, long ldc, long sA, long sB, long sC, long kchunk, int tri) {
     constexpr int LD = SBM + SPAD;
     __shared__ __align__(16) float As[2][SBK * LD];
     __shared__ __align__(16) float Bs[2][SBK * LD];
@@ -83,6 +83,8 @@ sgemm_kernel(int M, int N, long K, float alpha, const float* __restrict__ A, lon
         A += blockIdx.z * sA;
         B += blockIdx.z * sB;
         C += blockIdx.z * sC;
+        if (tri_skip_tile(tri, m0, n0, SBM)) return;
+        tri_krange(tri, m0, n0, SBM, SBN, kbeg, kend);  // tile multiples of SBK
     } else {
         if (blockIdx.x > blockIdx.y) return;  // upper tiles of the symmetric result
         kbeg = (long)blockIdx.z * kchunk;
@@ -165,10 +167,11 @@ sgemm_kernel(int M, int N, long K, float alpha, const float* __restrict__ A, lon
 
 template <int MODE>
 void launch_sgemm(Ctx& c, bool tA, bool tB, dim3 grid, int M, int N, long K, float alpha, const float* A, long lda,
-                  const float* B, long ldb, float beta, float* C, long ldc, long sA, long sB, long sC, long kchunk) {
+                  const float* B, long ldb, float beta, float* C, long ldc, long sA, long sB, long sC, long kchunk,
+                  int tri) {
 #define TT_SGEMM_CASE(TA_, TB_)                                                                    \
     sgemm_kernel<TA_, TB_, MODE><<<grid, 256, 0, c.stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, \
-                                                             sB, sC, kchunk)
+                                                             sB, sC, kchunk, tri)
     if (!tA && !tB) TT_SGEMM_CASE(false, false);
     else if (!tA && tB) TT_SGEMM_CASE(false, true);
     else if (tA && !tB) TT_SGEMM_CASE(true, false);
@@ -182,14 +185,14 @@ inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 }  // namespace
 
 bool sgemm(Ctx& c, bool tA, bool tB, int M, int N, int K, float alpha, const float* A, long lda, const float* B,
-           long ldb, float beta, float* C, long ldc, int batch, long sA, long sB, long sC) {
+           long ldb, float beta, float* C, long ldc, int batch, long sA, long sB, long sC, int tri) {
     if ((lda & 3) || (ldb & 3) || !al16(A) || !al16(B)) return false;
     if (batch > 1 && ((sA & 3) || (sB & 3))) return false;
     dim3 grid((N + SBN - 1) / SBN, (M + SBM - 1) / SBM, batch);
     if (grid.y > 65535) return false;
     ProfScope ps(c, "gemm_f32", 2.0 * M * N * (double)K * batch,
                  sizeof(float) * ((double)M * K + (double)K * N + 2.0 * M * N) * batch);
-    launch_sgemm<0>(c, tA, tB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, K);
+    launch_sgemm<0>(c, tA, tB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, K, tri);
     return true;
 }
 
@@ -210,7 +213,7 @@ bool sgram(Ctx& c, bool rows, int n, long K, const float* X, long ldx, float* G)
     ProfScope ps(c, "gram_f32", (double)n * (n + 1) * (double)K, sizeof(float) * ((double)n * K + (double)n * n));
     // rows: G = X X^T, op(A) = X (n x K), op(B) = X^T: tA = false, tB = true
     // cols: G = X^T X with X K x n: op(A) = X^T: tA = true; op(B) = X: tB = false
-    launch_sgemm<1>(c, !rows, rows, grid, n, n, K, 1.f, X, ldx, X, ldx, 0.f, G, n, 0, 0, 0, kchunk);
+    launch_sgemm<1>(c, !rows, rows, grid, n, n, K, 1.f, X, ldx, X, ldx, 0.f, G, n, 0, 0, 0, kchunk, 0);
     return true;
 }
 
