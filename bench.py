@@ -49,7 +49,7 @@ def roofline_for(fam, prof, peaks, src):
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * NOMINAL_TF32_OVER_BF16
         return "tensor", prof["flops"] / secs / 1e12, peak, "TFLOP/s", (
             "%s sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25" % src)
-    if fam in ("gemm_f32", "gram_f32"):
+    if fam in ("gemm_f32", "gram_f32", "sgemm_f32", "sgram_f32"):
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         return "alu", prof["flops"] / secs / 1e12, peak, "TFLOP/s", "152 SMs x 128 FP32 lanes x 2 x max SM clock"
     if fam in ("gemm_f64", "gram_f64"):

@@ -176,11 +176,13 @@ struct Rounder {
             CholStatus h = read_st(s0);
             if (h.ndrop == 0 && h.min_ratio >= ratio_fast) {
                 apply(rows, a, K, X, Ti[0]);
-                // the second pass in the storage precision: a TF32 Gram of
-                // the nearly orthonormal X would leave an orthogonality
-                // defect of about u_tf32 / sqrt(K), far above FP32 level
-                // for short unfoldings
-                gram_into(rows, false, a, K, X);
+                // the second pass's Gram: a TF32 Gram of the nearly
+                // orthonormal X measures E to about u_tf32 / sqrt(K), so
+                // it leaves Q orthonormal to that (not to FP32 level); the
+                // factorization X = L Q itself stays exact to FP32 rounding
+                // (S and R come from the same E).  On tensor cores for long
+                // unfoldings (K >= kTc2MinK: defect <= 8e-6), else FP32.
+                gram_into(rows, K >= kTc2MinK, a, K, X);
                 o.npass = 2;
                 o.nchol = 1;
                 // G = I + E with E small: Q <- (I + E)^(-1/2) Q and
@@ -277,6 +279,7 @@ struct Rounder {
     // multi-CTA Jacobi takes tens of milliseconds.  qmul: core_k <- core_k U_r
     // (else core_k <- U_r, when Q = I).  False: not taken (nothing done).
     static constexpr int kSvd32Min = 96;
+    static constexpr long kTc2MinK = 4096;
     bool trunc_f32(int m, int p, int b, const T* Wsrc, long ldw, const T* R, double eps, int k, long NR,
                    bool qmul) {
         if constexpr (sizeof(T) != 4) {

@@ -149,9 +149,14 @@ __device__ __noinline__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, C* 
     const C tau_c = (C)tau;
     C mypiv = C(0);      // lane c keeps pivot c: the status is formed after
     bool mykeep = true;  // the loop, off the pivot chain
+    // next pivot, updated by lane c+1 from its own multiplier: the same FMA
+    // the column broadcast below applies to it, formed before the broadcast
+    // so the pivot chain (shuffle, rsqrt, multiply) skips the shared-memory
+    // round trip
+    C pnext = a[0];
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
-        const C piv = __shfl_sync(FULL, a[c], c);
+        const C piv = __shfl_sync(FULL, pnext, c);
         const bool keep = isfinite(piv) && piv > tau_c && piv > C(0);
         // reciprocal square root first: one special-function op on the
         // pivot chain in FP32 (2 ulp; Cholesky's backward error is O(n u))
@@ -162,6 +167,7 @@ __device__ __noinline__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, C* 
             mykeep = keep;
         }
         const C l = (lane > c) ? a[c] * inv : C(0);
+        if (c + 1 < 32) pnext = fma(-l, l, a[c + 1]);
         a[c] = (lane == c) ? piv * inv : l;
         col[lane] = l;
         __syncwarp();

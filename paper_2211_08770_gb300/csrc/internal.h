@@ -86,6 +86,10 @@ __host__ __device__ inline void tri_krange(int tri, long m0, long n0, long bm, l
     if (tri & TRI_B_UPPER) ke = ke < n0 + bn ? ke : n0 + bn;
 }
 
+// Algorithmic flops of one product with the TRI_* zero structure: twice
+// the multiply-adds with both factors possibly non-zero (2MNK when dense).
+double gemm_flops(long M, long N, long K, int tri);
+
 // C = alpha op(A) op(B) + beta C, row-major with leading dimensions.
 // op(A) is M x K, op(B) is K x N.  batch > 1: blockIdx.z strides.  tri:
 // TRI_* flags of the operands' zero structure.

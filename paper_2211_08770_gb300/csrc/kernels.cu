@@ -127,6 +127,26 @@ void launch_gemm(Ctx& c, bool tA, bool tB, dim3 grid, int M, int N, long K, T al
 
 }  // namespace
 
+double gemm_flops(long M, long N, long K, int tri) {
+    // sum_{i < rows} of the k-range length min(K, i + 1) (lower) or
+    // max(0, K - i) (upper)
+    auto lower_pairs = [](long rows, long K) {
+        const long t = std::min(rows, K);
+        return (double)t * (t + 1) / 2.0 + (double)(rows - t) * K;
+    };
+    auto upper_pairs = [](long rows, long K) {
+        const long t = std::min(rows, K);
+        return (double)t * K - (double)t * (t - 1) / 2.0;
+    };
+    double f = 2.0 * M * N * (double)K;
+    if (tri & TRI_A_LOWER) f = std::min(f, 2.0 * N * lower_pairs(M, K));
+    if (tri & TRI_A_UPPER) f = std::min(f, 2.0 * N * upper_pairs(M, K));
+    if (tri & TRI_B_UPPER) f = std::min(f, 2.0 * M * lower_pairs(N, K));
+    if (tri & TRI_B_LOWER) f = std::min(f, 2.0 * M * upper_pairs(N, K));
+    if (tri & TRI_C_LOWER) f = std::min(f, 2.0 * K * lower_pairs(M, N));
+    return f;
+}
+
 template <class T>
 void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, long lda,
           const T* B, long ldb, T beta, T* C, long ldc, int batch, long sA, long sB, long sC, int tri) {
@@ -149,7 +169,7 @@ void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, lo
             sgemm(c, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch, sA, sB, sC, tri))
             return;
     }
-    ProfScope ps(c, sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", 2.0 * M * N * (double)K * batch,
+    ProfScope ps(c, sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", gemm_flops(M, N, K, tri) * batch,
                  sizeof(T) * ((double)M * K + (double)K * N + 2.0 * M * N) * batch);
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch);
     if (grid.y > 65535) throw_status(TT_ERR_ARG, "gemm M too large");

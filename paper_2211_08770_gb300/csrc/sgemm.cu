@@ -190,7 +190,7 @@ bool sgemm(Ctx& c, bool tA, bool tB, int M, int N, int K, float alpha, const flo
     if (batch > 1 && ((sA & 3) || (sB & 3))) return false;
     dim3 grid((N + SBN - 1) / SBN, (M + SBM - 1) / SBM, batch);
     if (grid.y > 65535) return false;
-    ProfScope ps(c, "gemm_f32", 2.0 * M * N * (double)K * batch,
+    ProfScope ps(c, "sgemm_f32", gemm_flops(M, N, K, tri) * batch,
                  sizeof(float) * ((double)M * K + (double)K * N + 2.0 * M * N) * batch);
     launch_sgemm<0>(c, tA, tB, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, K, tri);
     return true;
@@ -210,7 +210,7 @@ bool sgram(Ctx& c, bool rows, int n, long K, const float* X, long ldx, float* G)
     const long kchunk = ((ksteps + splits - 1) / splits) * SBK;
     splits = (K + kchunk - 1) / kchunk;
     dim3 grid(tiles, tiles, (unsigned)splits);
-    ProfScope ps(c, "gram_f32", (double)n * (n + 1) * (double)K, sizeof(float) * ((double)n * K + (double)n * n));
+    ProfScope ps(c, "sgram_f32", (double)n * (n + 1) * (double)K, sizeof(float) * ((double)n * K + (double)n * n));
     // rows: G = X X^T, op(A) = X (n x K), op(B) = X^T: tA = false, tB = true
     // cols: G = X^T X with X K x n: op(A) = X^T: tA = true; op(B) = X: tB = false
     launch_sgemm<1>(c, !rows, rows, grid, n, n, K, 1.f, X, ldx, X, ldx, 0.f, G, n, 0, 0, 0, kchunk, 0);
