@@ -7,7 +7,10 @@
 // (two 4 x 4 quadrants 64 apart, so a warp's shared-memory reads are 16-byte
 // broadcasts or conflict-free), BK = 8 with the next k-slab loaded into
 // registers while the current one is multiplied (double-buffered shared
-// memory, one barrier per slab).  Operands enter with 16-byte loads; the
+// memory, one barrier per slab).  The products are packed FP32x2 FMAs (two
+// accumulators per instruction: the kernel is issue-bound), and in a partial
+// edge tile the warps whose outputs lie beyond the edge skip them (r = 400
+// leaves 112 of the last tile's 128 rows or columns empty).  Operands enter with 16-byte loads; the
 // row-major M x K (or N x K) side is transposed into k-major shared memory on
 // the way, with the tile rows padded by four floats so the scattered stores
 // do not collide.  Requires 16-byte aligned pointers and leading dimensions
@@ -67,17 +70,35 @@ __device__ __forceinline__ void store_slab(float* S, const float4 v) {
     }
 }
 
+// acc (two adjacent FP32 accumulators) += a * (b.x, b.y): one packed
+// FP32x2 FMA (sm_100 and later), half the issue slots of two FFMAs; the same
+// rounding as two fmaf
+__device__ __forceinline__ void fma2(float& c0, float& c1, float a, float b0, float b1) {
+    unsigned long long cc, ap, bp;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(cc) : "f"(c0), "f"(c1));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(ap) : "f"(a));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(bp) : "f"(b0), "f"(b1));
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(cc) : "l"(ap), "l"(bp));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(c0), "=f"(c1) : "l"(cc));
+}
+
 // C (M x N) = alpha op(A) op(B) + beta C   (MODE 0, blockIdx.z = batch)
 // C += op(A) op(B) on lower tiles, split-K (MODE 1, blockIdx.z = K split)
-template <bool TA, bool TB, int MODE>
+// CW: a warp covers 2 column groups x 16 row groups (else 16 x 2), so a
+// warp whose outputs all fall beyond N (CW) or M (!CW) in a partial edge
+// tile skips the products (it still stages its share of the operands).
+template <bool TA, bool TB, int MODE, bool CW>
 __global__ void __launch_bounds__(256, 2)
 sgemm_kernel(int M, int N, long K, float alpha, const float* __restrict__ A, long lda, const float* __restrict__ B,
              long ldb, float beta, float* __restrict__ C, long ldc, long sA, long sB, long sC, long kchunk, int tri) {
     constexpr int LD = SBM + SPAD;
     __shared__ __align__(16) float As[2][SBK * LD];
     __shared__ __align__(16) float Bs[2][SBK * LD];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x;
+    const int tx = CW ? tid >> 4 : tid & 15, ty = CW ? tid & 15 : tid >> 4;
     const int m0 = blockIdx.y * SBM, n0 = blockIdx.x * SBN;
+    // outputs 4 t.. precede 64 + 4 t.., so the first group decides
+    const bool live = CW ? (n0 + 4 * tx < N) : (m0 + 4 * ty < M);
     long kbeg = 0, kend = K;
     if (MODE == 0) {
         A += blockIdx.z * sA;
@@ -111,18 +132,20 @@ sgemm_kernel(int M, int N, long K, float alpha, const float* __restrict__ A, lon
         }
         const float* a_s = As[buf];
         const float* b_s = Bs[buf];
+        if (live) {
 #pragma unroll
-        for (int kk = 0; kk < SBK; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4*>(a_s + kk * LD + 4 * ty);
-            const float4 a1 = *reinterpret_cast<const float4*>(a_s + kk * LD + 64 + 4 * ty);
-            const float4 b0 = *reinterpret_cast<const float4*>(b_s + kk * LD + 4 * tx);
-            const float4 b1 = *reinterpret_cast<const float4*>(b_s + kk * LD + 64 + 4 * tx);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            for (int kk = 0; kk < SBK; ++kk) {
+                const float4 a0 = *reinterpret_cast<const float4*>(a_s + kk * LD + 4 * ty);
+                const float4 a1 = *reinterpret_cast<const float4*>(a_s + kk * LD + 64 + 4 * ty);
+                const float4 b0 = *reinterpret_cast<const float4*>(b_s + kk * LD + 4 * tx);
+                const float4 b1 = *reinterpret_cast<const float4*>(b_s + kk * LD + 64 + 4 * tx);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                    for (int j = 0; j < 8; j += 2) fma2(acc[i][j], acc[i][j + 1], av[i], bv[j], bv[j + 1]);
+            }
         }
         if (more) {
             store_slab<TA>(As[buf ^ 1], ra);
@@ -169,9 +192,22 @@ template <int MODE>
 void launch_sgemm(Ctx& c, bool tA, bool tB, dim3 grid, int M, int N, long K, float alpha, const float* A, long lda,
                   const float* B, long ldb, float beta, float* C, long ldc, long sA, long sB, long sC, long kchunk,
                   int tri) {
-#define TT_SGEMM_CASE(TA_, TB_)                                                                    \
-    sgemm_kernel<TA_, TB_, MODE><<<grid, 256, 0, c.stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, \
-                                                             sB, sC, kchunk, tri)
+    // skip along the dimension whose edge tile wastes more of its width
+    const int wm = (int)(grid.y * SBM - M), wn = (int)(grid.x * SBN - N);
+    const bool cw = MODE == 0 && wn > wm;
+#define TT_SGEMM_CASE(TA_, TB_)                                                                                  \
+    do {                                                                                                         \
+        if constexpr (MODE == 0)                                                                                 \
+            if (cw) {                                                                                            \
+                sgemm_kernel<TA_, TB_, MODE, true><<<grid, 256, 0, c.stream>>>(M, N, K, alpha, A, lda, B, ldb,   \
+                                                                               beta, C, ldc, sA, sB, sC, kchunk, \
+                                                                               tri);                             \
+                break;                                                                                           \
+            }                                                                                                    \
+            sgemm_kernel<TA_, TB_, MODE, false><<<grid, 256, 0, c.stream>>>(M, N, K, alpha, A, lda, B, ldb,      \
+                                                                            beta, C, ldc, sA, sB, sC, kchunk,    \
+                                                                            tri);                                \
+    } while (0)
     if (!tA && !tB) TT_SGEMM_CASE(false, false);
     else if (!tA && tB) TT_SGEMM_CASE(false, true);
     else if (tA && !tB) TT_SGEMM_CASE(true, false);

@@ -1,7 +1,10 @@
 """FP32 CUDA-core GEMM and Gram (the products TT-round keeps in FP32
 arithmetic) through tt_gemm_f32(..., 0) and tt_gram_f32(..., 0), against an
-FP64 product of the same FP32 operands.  Aligned layouts take the 128 x 128
-kernel, unaligned leading dimensions the 64 x 64 one; both are covered.
+FP64 product of the same FP32 operands.  Aligned products with enough
+128 x 128 output tiles to fill half the SMs take the 128 x 128 kernel
+(partial edge tiles along M, along N and along both, with warps beyond the
+edge skipping their products), the others the 64 x 64 one (split over K
+when it has few output tiles); all are covered.
 FP32 accumulation over K terms: error below ~sqrt(K) u_32 |a_i||b_j| for
 these random operands; the bound (1 + sqrt(K)) 1e-6 leaves a margin of ~10
 while any indexing error is O(1)."""
@@ -26,7 +29,7 @@ def ctx():
 @pytest.mark.parametrize("trans_b", [False, True])
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (3, 5, 7), (128, 128, 8), (129, 127, 13), (400, 25600, 400),
                                    (25600, 400, 400), (400, 1000, 4), (64, 640, 20), (1000, 36, 400),
-                                   (257, 130, 1000)])
+                                   (257, 130, 1000), (1000, 10000, 64), (9000, 1000, 33), (1030, 2000, 50)])
 def test_sgemm(ctx, trans_b, M, N, K):
     rng = np.random.default_rng(M + 5 * N + 11 * K + trans_b)
     A = rng.standard_normal((M, K)).astype(np.float32)
