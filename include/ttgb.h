@@ -100,6 +100,8 @@ typedef struct {
                                   only while profiling is on: it costs a sync) */
     uint64_t series_passes;    /* second Cholesky QR passes replaced by the
                                   series (I + E)^(-1/2) of a near-identity Gram */
+    uint64_t series_retries;   /* roundings redone with Cholesky passes because a
+                                  series pass met a Gram too far from I */
 } tt_stats;
 
 /* Per-kernel timing of a context (tt_ctx_set_profiling): CUDA events are
@@ -131,6 +133,11 @@ tt_precision tt_ctx_precision(const tt_ctx* ctx);
 
 /* Enables (on != 0) or disables event timing of the library's launches. */
 tt_status tt_ctx_set_profiling(tt_ctx* ctx, int on);
+/* Restricts event timing to one kernel family (its name as reported by
+ * tt_ctx_get_profile, copied); NULL or "" times every family again.  Two
+ * events per timed launch cost host time, which shows in a step made of
+ * many short launches; timing one family keeps that small. */
+tt_status tt_ctx_set_profiling_family(tt_ctx* ctx, const char* family);
 /* Synchronizes the stream and writes up to max_entries aggregated records
  * (one per kernel family, since the last reset) to out; *n_entries receives
  * the number of families. */

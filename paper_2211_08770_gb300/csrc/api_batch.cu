@@ -46,7 +46,9 @@ std::vector<Ctx*> get_lanes(Ctx& root, int count) {
         l->tc_gemm_split = root.tc_gemm_split;
         l->chol_nb = root.chol_nb;
         l->use_series = root.use_series;
+        l->series_force_retry = root.series_force_retry;
         l->prof = root.prof;
+        l->prof_only = root.prof_only;
     }
     return out;
 }
@@ -60,6 +62,7 @@ void merge_lane(Ctx& root, Ctx& lane) {
     root.stats.fallback_orth += lane.stats.fallback_orth;
     root.stats.svd_sweeps += lane.stats.svd_sweeps;
     root.stats.series_passes += lane.stats.series_passes;
+    root.stats.series_retries += lane.stats.series_retries;
     lane.stats = tt_stats{};
     for (auto& r : lane.recs) {
         ProfRec q = r;

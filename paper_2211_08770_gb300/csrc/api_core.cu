@@ -107,6 +107,7 @@ ProfScope::ProfScope(Ctx& ctx, const char* name, double fl, double by) : c(ctx),
     // only the outermost scope records: launches made inside another
     // instrumented call (the GEMMs of the blocked Cholesky) count for it
     if (c.prof_nest++ > 0 || !c.prof) return;
+    if (!c.prof_only.empty() && c.prof_only != name) return;
     fam = c.family(name);
     a = c.event();
     TT_CUDA(cudaEventRecord(a, c.stream));
@@ -416,9 +417,12 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     const char* nb = getenv("TTGB_CHOL_NB");
     if (nb) c->chol_nb = std::max(0, atoi(nb));
     // TTGB_SERIES_PASS=0 keeps the Cholesky factorization for every second
-    // Cholesky QR pass (no series pass)
+    // Cholesky QR pass (no series pass); =retry treats every series pass as
+    // invalid, so each rounding is redone with Cholesky passes (exercises
+    // the retry path)
     const char* sp = getenv("TTGB_SERIES_PASS");
     if (sp && sp[0] == '0') c->use_series = false;
+    if (sp && sp[0] == 'r') c->series_force_retry = true;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
@@ -457,6 +461,12 @@ tt_precision tt_ctx_precision(const tt_ctx* ctx) { return ctx ? ctx->prec : TT_F
 tt_status tt_ctx_set_profiling(tt_ctx* ctx, int on) {
     if (!ctx) return TT_ERR_ARG;
     ctx->prof = on != 0;
+    return TT_OK;
+}
+
+tt_status tt_ctx_set_profiling_family(tt_ctx* ctx, const char* family) {
+    if (!ctx) return TT_ERR_ARG;
+    ctx->prof_only = family ? family : "";
     return TT_OK;
 }
 

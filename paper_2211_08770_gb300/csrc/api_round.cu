@@ -41,13 +41,22 @@ struct Rounder {
     size_t ws_bytes = 0;
     std::vector<T*> core;
     T* spare = nullptr;
-    T *G, *Lf[3], *Ti[3], *Lp, *Tmp, *Ub, *SVt;
+    T *G, *Lf[3], *Ti[3], *Lp, *Tmp, *Ub, *SVt, *Mp;
+    // Deferred second-pass transforms of the right-to-left sweep: core k
+    // holds Q1 and the orthonormal core is Pend[k] * Q1 (Pend[k] is
+    // r_{k-1} x r_{k-1}); the left-to-right sweep folds Pend[k] into the
+    // matrix it absorbs into core k, an r x r product instead of a second
+    // apply over the whole core
+    T* Pend;
+    std::vector<char> pend;
     double* jwork;
     double* sig;
     double* dsc;             // device scalars
     CholStatus* st;          // per-Cholesky statuses of this rounding
     int nst = 0, st_cap = 0;
     double err2 = 0.0;       // accumulated discarded tail (squared, absolute)
+    bool series = true;      // second Cholesky QR passes by the series
+    bool series_used = false;
 
     Rounder(tt_ctx* ctx, const tt_tensor* x) : c(ctx), d(x->d), n(x->n), r(x->r) {
         const bool is64 = sizeof(T) == 8;
@@ -74,9 +83,14 @@ struct Rounder {
         Tmp = (T*)p; p += small_b;
         Ub = (T*)p; p += small_b;
         SVt = (T*)p; p += small_b;
+        Mp = (T*)p; p += small_b;
+        Pend = (T*)p; p += (size_t)d * small_b;
+        pend.assign(d + 1, 0);
         jwork = (double*)p; p += al(2 * rr * sizeof(double));
         sig = (double*)p; p += al(rmax * sizeof(double));
         dsc = (double*)p; p += al(16 * sizeof(double));
+        series = ctx->use_series;
+        TT_CUDA(cudaMemsetAsync(dsc, 0, 16 * sizeof(double), c->stream));
         st = (CholStatus*)p;
         for (int k = 0; k < d; ++k)
             TT_CUDA(cudaMemcpyAsync(core[k], x->cores[k], sizeof(T) * x->core_elems(k), cudaMemcpyDeviceToDevice,
@@ -85,11 +99,11 @@ struct Rounder {
     ~Rounder() { if (ws) c->release(ws, ws_bytes); }
 
     // bytes of the workspace carved in the constructor (d + 1 core buffers,
-    // eleven r x r matrices, Jacobi work, singular values, scalars, statuses)
+    // 12 + d r x r matrices, Jacobi work, singular values, scalars, statuses)
     static size_t workspace_bytes(int d, int rmax, size_t cap, size_t es) {
         auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
         const size_t rr = (size_t)rmax * rmax;
-        return (d + 1) * al(cap * es) + 11 * al(rr * es) + al(2 * rr * sizeof(double)) + al(rmax * sizeof(double)) +
+        return (d + 1) * al(cap * es) + (12 + d) * al(rr * es) + al(2 * rr * sizeof(double)) + al(rmax * sizeof(double)) +
                al(16 * sizeof(double)) + al((16 * d + 16) * sizeof(CholStatus));
     }
 
@@ -141,27 +155,22 @@ struct Rounder {
         int ndrop;
         bool shifted;
         int nchol = 0;        // Cholesky passes (factors Lf/Ti[0..nchol)) of the certificate
-        double lb_poly = 1.0; // lower bound of sigma_min of the series pass's factor
+        bool series = false;  // the second pass was the series pass (||E||_F^2 in dsc[12])
         bool lower = true;    // Lp lower-triangular
+        bool deferred = false;  // X holds Q1; the orthonormal factor is S Q1 (S in the defer slot)
     };
 
-    // Order of the series pass for ||E||_F = e: the smallest m (1..3) whose
-    // Taylor remainders of (1 + x)^(-1/2) and (1 + x)^(1/2) together,
-    // bounded by c_m e^(m+1) / (1 - e), stay below the storage precision's
-    // unit round-off; 0 (take the Cholesky pass) when none does.
-    int series_order(double e) const {
-        const double cm[4] = {0.0, 0.5, 0.375, 0.3125};
-        if (!(e < 0.25)) return 0;
-        for (int m = 1; m <= 3; ++m)
-            if (cm[m] * pow(e, m + 1) / (1.0 - e) <= ug_fb) return m;
-        return 0;
-    }
+    // The series pass is of order 3: valid while the Taylor remainders of
+    // (1 + x)^(-1/2) and (1 + x)^(1/2) after the cubic terms, together at
+    // most (35 + 5) / 128 e^4 / (1 - e) for ||E||_F = e, stay below the
+    // storage precision's unit round-off (e <= 0.021 FP32, 1.4e-4 FP64).
+    bool series_valid(double e) const { return e < 0.25 && 0.3125 * pow(e, 4) / (1.0 - e) <= ug_fb; }
 
     // X (a x K rows, or K x a cols) is overwritten by its orthonormal factor;
     // Lp receives L with X_old = L Q (rows) or X_old = Q L^T (cols), lower-
     // triangular unless the second pass was the series pass (o.lower).
     // Lf[i], Ti[i] keep the factors of each pass.
-    Orth orth(bool rows, int a, long K, T*& X) {
+    Orth orth(bool rows, int a, long K, T*& X, T* defer = nullptr) {
         const double sq = sqrt((double)a);
         const double drop_fb = 8.0 * ug_fb * sq;
         const double ratio_fast = tc ? 10.0 * ug_fast : 100.0 * ug_fast;
@@ -185,22 +194,32 @@ struct Rounder {
                 gram_into(rows, K >= kTc2MinK, a, K, X);
                 o.npass = 2;
                 o.nchol = 1;
-                // G = I + E with E small: Q <- (I + E)^(-1/2) Q and
-                // R = (I + E)^(1/2) from the series in E (a few a x a
-                // products instead of a Cholesky factorization; the
-                // factor is symmetric, not triangular)
-                const double e = c->use_series ? sqrt(near_identity<T>(*c, a, G, Ti[1], dsc + 12)) : 1.0;
-                const int m = series_order(e);
-                if (m > 0) {
+                if (series) {
+                    // G = I + E with E small: Q <- (I + E)^(-1/2) Q and
+                    // R = (I + E)^(1/2) from the cubic series in E (two
+                    // a x a products instead of a Cholesky factorization;
+                    // the factor is symmetric, not triangular).  ||E||_F is
+                    // checked at the end of the rounding (one maximum on
+                    // the device, read with the statuses), not here: no
+                    // synchronization; a rounding where it was too large
+                    // is redone with Cholesky passes.
                     c->stats.series_passes++;
-                    if (m >= 2) mm(false, false, a, a, a, Ti[1], a, Ti[1], a, Lf[1], a);
-                    if (m >= 3) mm(false, false, a, a, a, Lf[1], a, Ti[1], a, Tmp, a);
-                    poly_pair<T>(*c, a, m, Ti[1], Lf[1], Tmp, Lf[1]);
-                    apply(rows, a, K, X, Ti[1], false);
+                    series_used = true;
+                    near_identity<T>(*c, a, G, Ti[1], dsc + 12);
+                    mm(false, false, a, a, a, Ti[1], a, Ti[1], a, Lf[1], a);
+                    mm(false, false, a, a, a, Lf[1], a, Ti[1], a, Tmp, a);
+                    poly_pair<T>(*c, a, 3, Ti[1], Lf[1], Tmp, Lf[1], dsc + 12, dsc + 11);
+                    if (defer) {
+                        // X keeps Q1; S Q1 is formed by the caller's later
+                        // products (rows only: S acts on the row index)
+                        TT_CUDA(cudaMemcpyAsync(defer, Ti[1], sizeof(T) * (size_t)a * a, cudaMemcpyDeviceToDevice,
+                                                c->stream));
+                        o.deferred = true;
+                    } else {
+                        apply(rows, a, K, X, Ti[1], false);
+                    }
                     mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Lp, a, TRI_A_LOWER);
-                    // sigma_min((I + E)^(1/2)) >= sqrt(1 - ||E||_2); less the
-                    // series remainder and the rounding of the stored factor
-                    o.lb_poly = std::max(0.0, sqrt(1.0 - e) - (2.0 + sqrt((double)a)) * ug_fb);
+                    o.series = true;
                     o.lower = false;
                     return o;
                 }
@@ -236,16 +255,24 @@ struct Rounder {
         const int np = o.nchol;
         TT_CUDA(cudaMemsetAsync(dsc, 0, 2 * np * sizeof(double), c->stream));
         for (int i = 0; i < np; ++i) inv_and_identity_defect<T>(*c, a, Lf[i], Ti[i], dsc + 2 * i);
-        std::vector<double> h(2 * np);
+        std::vector<double> h(13);
         std::vector<CholStatus> hs(nst);
-        TT_CUDA(cudaMemcpyAsync(h.data(), dsc, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        TT_CUDA(cudaMemcpyAsync(h.data(), dsc, 13 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         TT_CUDA(cudaMemcpyAsync(hs.data(), st, nst * sizeof(CholStatus), cudaMemcpyDeviceToHost, c->stream));
         c->sync();
         for (int i = nst - np; i < nst; ++i) {
             if (hs[i].nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in a Gram matrix");
             if (hs[i].ndrop) return 0.0;
         }
-        double lb = o.lb_poly;
+        double lb = 1.0;
+        if (o.series) {
+            // sigma_min((I + E)^(1/2)) >= sqrt(1 - ||E||_2); less the series
+            // remainder and the rounding of the stored factor.  An invalid
+            // series pass gives no bound (the rounding is redone anyway).
+            const double e = sqrt(h[12]);
+            if (!series_valid(e)) return 0.0;
+            lb = std::max(0.0, sqrt(1.0 - e) - (2.0 + sqrt((double)a)) * ug_fb);
+        }
         for (int i = 0; i < np; ++i) {
             double b1 = h[2 * i] > 0 ? 1.0 / sqrt(h[2 * i]) : 0.0;
             double b2 = 1.0 - sqrt(h[2 * i + 1]);
@@ -266,6 +293,22 @@ struct Rounder {
     }
     static double svd_floor(int b) {
         return sizeof(T) == 8 ? 4.0 * sqrt((double)b) * 1.1102230246251565e-16 : 5.960464477539063e-08;
+    }
+
+    // core_{k+1} <- M core_{k+1} (M: rows x r_{k+1}, ld ldm), with core
+    // k+1's deferred transform folded in first (M Pend[k+1], r x r)
+    void absorb_next(int k, int rows, const T* M, long ldm, int tri) {
+        const int b = r[k + 1];
+        const long NR = (long)n[k + 1] * r[k + 2];
+        if (pend[k + 1]) {
+            mm(false, false, rows, b, b, M, ldm, Pend + (size_t)(k + 1) * rmax * rmax, b, Mp, b);
+            M = Mp;
+            ldm = b;
+            tri = 0;
+            pend[k + 1] = 0;
+        }
+        mm(false, false, rows, (int)NR, b, M, ldm, core[k + 1], NR, spare, NR, tri);
+        std::swap(core[k + 1], spare);
     }
 
     // Truncation of bond k for FP32 data by the FP32 column Jacobi: R (p x b,
@@ -328,8 +371,7 @@ struct Rounder {
             } else {
                 TT_CUDA(cudaMemcpyAsync(core[k], Uo, sizeof(T) * (size_t)p * rp, cudaMemcpyDeviceToDevice, c->stream));
             }
-            mm(false, false, rp, (int)NR, b, S, b, core[k + 1], NR, spare, NR);
-            std::swap(core[k + 1], spare);
+            absorb_next(k, rp, S, b, 0);
             r[k + 1] = rp;
             return true;
         }
@@ -361,7 +403,8 @@ struct Rounder {
                 fill_identity<T>(*c, (int)K, core[k], K);
                 r[k] = (int)K;
             } else {
-                const Orth o = orth(true, a, K, core[k]);
+                const Orth o = orth(true, a, K, core[k], Pend + (size_t)k * rmax * rmax);
+                pend[k] = o.deferred;
                 mm(false, false, M, a, a, core[k - 1], a, Lp, a, spare, a, o.lower ? TRI_B_LOWER : 0);
                 std::swap(core[k - 1], spare);
             }
@@ -389,8 +432,7 @@ struct Rounder {
                     c->stats.certified_bonds++;
                     // core_{k+1} <- R core_{k+1}, R = Lp^T
                     transpose<T>(*c, b, b, Lp, Tmp);
-                    mm(false, false, b, (int)NR, b, Tmp, b, core[k + 1], NR, spare, NR, o.lower ? TRI_A_UPPER : 0);
-                    std::swap(core[k + 1], spare);
+                    absorb_next(k, b, Tmp, b, o.lower ? TRI_A_UPPER : 0);
                     continue;
                 }
                 // R = Lp^T (b x b), SVD, truncate
@@ -405,8 +447,7 @@ struct Rounder {
                 const int rp = trunc_rank(hs, eps);
                 mm(false, false, m, rp, b, core[k], b, Ub, b, spare, rp);
                 std::swap(core[k], spare);
-                mm(false, false, rp, (int)NR, b, SVt, b, core[k + 1], NR, spare, NR);
-                std::swap(core[k + 1], spare);
+                absorb_next(k, rp, SVt, b, 0);
                 r[k + 1] = rp;
             } else {
                 // m < b: Q = I_m, R = X (m x b); certificate from the Gram of
@@ -423,8 +464,7 @@ struct Rounder {
                 const double lb2 = lb * lb - noise;
                 if (lb > 0.0 && lb2 > 4.0 * eps * eps) {
                     c->stats.certified_bonds++;
-                    mm(false, false, m, (int)NR, b, X, b, core[k + 1], NR, spare, NR);
-                    std::swap(core[k + 1], spare);
+                    absorb_next(k, m, X, b, 0);
                     fill_identity<T>(*c, m, core[k], m);
                     r[k + 1] = m;
                     continue;
@@ -443,21 +483,25 @@ struct Rounder {
                 // core_k <- U[:, :rp] (m x rp)
                 TT_CUDA(cudaMemcpy2DAsync(core[k], rp * sizeof(T), Ub, m * sizeof(T), rp * sizeof(T), m,
                                           cudaMemcpyDeviceToDevice, c->stream));
-                mm(false, false, rp, (int)NR, b, SVt, b, core[k + 1], NR, spare, NR);
-                std::swap(core[k + 1], spare);
+                absorb_next(k, rp, SVt, b, 0);
                 r[k + 1] = rp;
             }
         }
     }
 
     // one synchronization: the device wait flag (tensor-core and Jacobi
-    // kernels) and every factorization status of this rounding
-    void check_all_status() {
+    // kernels), every factorization status of this rounding and the largest
+    // ||E||_F of its series passes; false when a series pass was outside
+    // its validity (the caller redoes the rounding without them)
+    bool check_all_status() {
         std::vector<CholStatus> hs(nst);
         int flag = 0;
+        double e2max = 0.0;
         TT_CUDA(cudaMemcpyAsync(&flag, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         if (nst)
             TT_CUDA(cudaMemcpyAsync(hs.data(), st, nst * sizeof(CholStatus), cudaMemcpyDeviceToHost, c->stream));
+        if (series_used)
+            TT_CUDA(cudaMemcpyAsync(&e2max, dsc + 11, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         c->sync();
         if (flag) {
             TT_CUDA(cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream));
@@ -465,6 +509,8 @@ struct Rounder {
         }
         for (auto& h : hs)
             if (h.nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in a Gram matrix");
+        if (!std::isfinite(e2max)) throw_status(TT_ERR_NONFINITE, "NaN or Inf in a Gram matrix");
+        return !series_used || (series_valid(sqrt(e2max)) && !c->series_force_retry);
     }
 
     tt_tensor* emit() {
@@ -477,18 +523,7 @@ struct Rounder {
 };
 
 template <class T>
-tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est) {
-    ctx->stats.roundings++;
-    if (x->d == 1) {
-        if (err_est) *err_est = 0.0;
-        return copy_tensor(ctx, x);
-    }
-    Rounder<T> R(ctx, x);
-    R.rl_sweep();
-    const double nrm = R.core_norm(0);
-    const double eps = delta * nrm / sqrt((double)(x->d - 1));
-    R.lr_sweep(eps);
-    R.check_all_status();
+tt_tensor* finish_round(Rounder<T>& R, const tt_tensor* x, double nrm, double* err_est) {
     tt_tensor* y = R.emit();
     if (sizeof(T) == 8) {
         // FP64: cores 1..d-1 are left-orthonormal to working accuracy, so
@@ -507,6 +542,28 @@ tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_es
 }
 
 template <class T>
+tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est) {
+    ctx->stats.roundings++;
+    if (x->d == 1) {
+        if (err_est) *err_est = 0.0;
+        return copy_tensor(ctx, x);
+    }
+    for (int attempt = 0;; ++attempt) {
+        Rounder<T> R(ctx, x);
+        if (attempt > 0) R.series = false;
+        R.rl_sweep();
+        const double nrm = R.core_norm(0);
+        R.lr_sweep(delta * nrm / sqrt((double)(x->d - 1)));
+        if (!R.check_all_status()) {
+            // a series pass met a Gram too far from I: redo with Cholesky passes
+            ctx->stats.series_retries++;
+            continue;
+        }
+        return finish_round(R, x, nrm, err_est);
+    }
+}
+
+template <class T>
 double norm_t(tt_ctx* ctx, const tt_tensor* x) {
     if (x->d == 1) {
         Rounder<T> R(ctx, x);
@@ -514,7 +571,14 @@ double norm_t(tt_ctx* ctx, const tt_tensor* x) {
     }
     Rounder<T> R(ctx, x);
     R.rl_sweep();
-    R.check_all_status();
+    if (!R.check_all_status()) {
+        ctx->stats.series_retries++;
+        Rounder<T> R2(ctx, x);
+        R2.series = false;
+        R2.rl_sweep();
+        R2.check_all_status();
+        return R2.core_norm(0);
+    }
     return R.core_norm(0);
 }
 

@@ -155,15 +155,17 @@ template <class S>
 void inv_and_identity_defect(Ctx& c, int n, const S* L, const S* T, double* out);
 
 // Near-identity symmetric G (n x n, lower triangle valid): E = G - I
-// (symmetric, full) and the return value ||E||_F^2 (FP64 accumulation;
-// dev_out is one device double of scratch; synchronizes the stream).
+// (symmetric, full) and ||E||_F^2 into *dev_out (FP64 accumulation).
 template <class T>
-double near_identity(Ctx& c, int n, const T* G, T* E, double* dev_out);
+void near_identity(Ctx& c, int n, const T* G, T* E, double* dev_out);
 // Truncated Taylor series of order m (1..3) in the symmetric E:
 // S = (I + E)^(-1/2) over E and R = (I + E)^(1/2) into R; E2 = E^2 is read
-// when m >= 2 and E3 = E^3 when m >= 3 (R may alias E2).
+// when m >= 2 and E3 = E^3 when m >= 3 (R may alias E2).  When e2max is
+// given, *e2max becomes max(*e2max, *e2) (device scalars: ||E||_F^2 of this
+// pass and the running maximum).
 template <class T>
-void poly_pair(Ctx& c, int n, int m, T* E, const T* E2, const T* E3, T* R);
+void poly_pair(Ctx& c, int n, int m, T* E, const T* E2, const T* E3, T* R, const double* e2 = nullptr,
+               double* e2max = nullptr);
 
 template <class T>
 void fill_identity(Ctx& c, int n, T* A, long lda);  // A (n x n) = I
@@ -254,10 +256,12 @@ struct Ctx {
     int max_lanes = 8;            // concurrency of tt_round_batched
     int chol_nb = 0;              // block size of chol_inv (0: the per-order table)
     bool use_series = true;       // series second pass of Cholesky QR when it is accurate
+    bool series_force_retry = false;  // treat series passes as invalid (tests the retry)
 
     // event profiling of launches (off by default)
     bool prof = false;
     int prof_nest = 0;            // open ProfScopes: only the outermost records
+    std::string prof_only;        // time only this family ("" = all)
     std::vector<std::string> fam_names;
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> ev_pool;

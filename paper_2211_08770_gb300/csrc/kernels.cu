@@ -110,6 +110,96 @@ gemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda,
     }
 }
 
+// Products of r x r size (the series pass, the factor products): 32 x 32
+// output tile per CTA (169 CTAs at r = 400, about one per SM), 256 threads
+// with 2 x 2 outputs each; the CTA's row and column slices of op(A) and
+// op(B) for a K chunk of up to RKC are staged whole in shared memory
+// (op(A) row-major, op(B) k-major, so a warp reads two broadcast A values
+// and 16 consecutive B values per k), one barrier per chunk.  No split-K,
+// no atomics.
+constexpr int RT = 32;
+
+template <class T>
+constexpr int rgemm_kc() { return sizeof(T) == 4 ? 512 : 256; }
+
+template <class T>
+size_t rgemm_smem() { return sizeof(T) * (size_t)(RT * (rgemm_kc<T>() + 1) + rgemm_kc<T>() * (RT + 1)); }
+
+template <class T, bool TA, bool TB>
+__global__ void __launch_bounds__(256)
+rgemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda, const T* __restrict__ B, long ldb,
+             T beta, T* __restrict__ C, long ldc, int tri) {
+    constexpr int KC = rgemm_kc<T>();
+    extern __shared__ __align__(16) unsigned char rg_smem[];
+    T* As = reinterpret_cast<T*>(rg_smem);  // [RT][KC + 1]
+    T* Bs = As + RT * (KC + 1);              // [KC][RT + 1]
+    const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+    const int m0 = blockIdx.y * RT, n0 = blockIdx.x * RT;
+    if (tri_skip_tile(tri, m0, n0, RT)) return;
+    long kb = 0, ke = K;
+    tri_krange(tri, m0, n0, RT, RT, kb, ke);
+    T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+    for (long k0 = kb; k0 < ke; k0 += KC) {
+        const int kc = (int)min((long)KC, ke - k0);
+        // stage op(A)(m0 + i, k0 + k) and op(B)(k0 + k, n0 + j): the lanes
+        // of a warp run along the global operand's contiguous index, the
+        // warps along the other one (several loads in flight per thread)
+        const int warp = tid >> 5, lane = tid & 31;
+        if (!TA) {
+#pragma unroll
+            for (int i = warp; i < RT; i += 8) {
+                const long gm = m0 + i;
+                const T* src = A + gm * lda + k0;
+#pragma unroll 4
+                for (int k = lane; k < kc; k += 32) As[i * (KC + 1) + k] = gm < M ? src[k] : T(0);
+            }
+        } else {
+            const long gm = m0 + lane;
+#pragma unroll 4
+            for (int k = warp; k < kc; k += 8) As[lane * (KC + 1) + k] = gm < M ? A[(k0 + k) * lda + gm] : T(0);
+        }
+        if (!TB) {
+            const long gn = n0 + lane;
+#pragma unroll 4
+            for (int k = warp; k < kc; k += 8) Bs[k * (RT + 1) + lane] = gn < N ? B[(k0 + k) * ldb + gn] : T(0);
+        } else {
+#pragma unroll
+            for (int j = warp; j < RT; j += 8) {
+                const long gn = n0 + j;
+                const T* src = B + gn * ldb + k0;
+#pragma unroll 4
+                for (int k = lane; k < kc; k += 32) Bs[k * (RT + 1) + j] = gn < N ? src[k] : T(0);
+            }
+        }
+        __syncthreads();
+        const T* a0 = As + ti * (KC + 1);
+        const T* a1 = As + (ti + 16) * (KC + 1);
+#pragma unroll 8
+        for (int k = 0; k < kc; ++k) {
+            const T x0 = a0[k], x1 = a1[k];
+            const T y0 = Bs[k * (RT + 1) + tj], y1 = Bs[k * (RT + 1) + tj + 16];
+            acc[0][0] = fma(x0, y0, acc[0][0]);
+            acc[0][1] = fma(x0, y1, acc[0][1]);
+            acc[1][0] = fma(x1, y0, acc[1][0]);
+            acc[1][1] = fma(x1, y1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const long gm = m0 + ti + 16 * a;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const long gn = n0 + tj + 16 * b;
+            if (gn >= N) continue;
+            T v = alpha * acc[a][b];
+            if (beta != T(0)) v += beta * C[gm * ldc + gn];
+            C[gm * ldc + gn] = v;
+        }
+    }
+}
+
 template <class T, class CT, int MODE>
 void launch_gemm(Ctx& c, bool tA, bool tB, dim3 grid, int M, int N, long K, T alpha,
                  const T* A, long lda, const T* B, long ldb, T beta, CT* C, long ldc, long sA,
@@ -168,6 +258,25 @@ void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, lo
         if (2 * tiles128 >= c.sm_count &&
             sgemm(c, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch, sA, sB, sC, tri))
             return;
+    }
+    if (batch == 1 && K <= 2048 && (long)((M + RT - 1) / RT) * ((N + RT - 1) / RT) <= 2L * c.sm_count) {
+        ProfScope ps(c, sizeof(T) == 8 ? "rgemm_f64" : "rgemm_f32", gemm_flops(M, N, K, tri),
+                     sizeof(T) * ((double)M * K + (double)K * N + 2.0 * M * N));
+        dim3 g((N + RT - 1) / RT, (M + RT - 1) / RT);
+        const int sm = (int)rgemm_smem<T>();
+#define TT_RGEMM_CASE(TA_, TB_)                                                                             \
+    do {                                                                                                    \
+        static std::atomic<bool> attr{false};                                                               \
+        set_smem_once(attr, rgemm_kernel<T, TA_, TB_>, sm);                                                 \
+        rgemm_kernel<T, TA_, TB_><<<g, 256, sm, c.stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri); \
+    } while (0)
+        if (!tA && !tB) TT_RGEMM_CASE(false, false);
+        else if (!tA && tB) TT_RGEMM_CASE(false, true);
+        else if (tA && !tB) TT_RGEMM_CASE(true, false);
+        else TT_RGEMM_CASE(true, true);
+#undef TT_RGEMM_CASE
+        TT_LAUNCHED(c);
+        return;
     }
     ProfScope ps(c, sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", gemm_flops(M, N, K, tri) * batch,
                  sizeof(T) * ((double)M * K + (double)K * N + 2.0 * M * N) * batch);
@@ -294,7 +403,11 @@ __global__ void near_identity_kernel(int n, const T* __restrict__ G, T* __restri
 // alias E2 (every element is read before it is written, by one thread)
 template <class T>
 __global__ void poly_pair_kernel(int n, int m, T* E, const T* E2, const T* E3, T* R, double a1, double a2,
-                                 double a3, double b1, double b2, double b3) {
+                                 double a3, double b1, double b2, double b3, const double* e2, double* e2max) {
+    // running maximum of ||E||_F^2 over the series passes (non-negative
+    // doubles order like their bit patterns)
+    if (e2max && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicMax(reinterpret_cast<unsigned long long*>(e2max), (unsigned long long)__double_as_longlong(*e2));
     const long nn = (long)n * n;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x) {
         const double id = (e / n == e % n) ? 1.0 : 0.0;
@@ -309,21 +422,17 @@ __global__ void poly_pair_kernel(int n, int m, T* E, const T* E2, const T* E3, T
 }  // namespace
 
 template <class T>
-double near_identity(Ctx& c, int n, const T* G, T* E, double* dev_out) {
+void near_identity(Ctx& c, int n, const T* G, T* E, double* dev_out) {
     TT_CUDA(cudaMemsetAsync(dev_out, 0, sizeof(double), c.stream));
-    if (n <= 0) return 0.0;
+    if (n <= 0) return;
     const long nn = (long)n * n;
     const int blocks = (int)std::min<long>((nn + 255) / 256, 2L * c.sm_count);
     near_identity_kernel<T><<<blocks, 256, 0, c.stream>>>(n, G, E, dev_out);
     TT_LAUNCHED(c);
-    double h = 0.0;
-    TT_CUDA(cudaMemcpyAsync(&h, dev_out, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-    c.sync();
-    return h;
 }
 
 template <class T>
-void poly_pair(Ctx& c, int n, int m, T* E, const T* E2, const T* E3, T* R) {
+void poly_pair(Ctx& c, int n, int m, T* E, const T* E2, const T* E3, T* R, const double* e2, double* e2max) {
     // Taylor coefficients of (1 + x)^(-1/2) and (1 + x)^(1/2)
     const double a[4] = {1.0, -0.5, 0.375, -0.3125};
     const double b[4] = {1.0, 0.5, -0.125, 0.0625};
@@ -332,7 +441,7 @@ void poly_pair(Ctx& c, int n, int m, T* E, const T* E2, const T* E3, T* R) {
     const int blocks = (int)std::min<long>((nn + 255) / 256, 2L * c.sm_count);
     poly_pair_kernel<T><<<blocks, 256, 0, c.stream>>>(n, m, E, E2, E3, R, a[1], m >= 2 ? a[2] : 0.0,
                                                       m >= 3 ? a[3] : 0.0, b[1], m >= 2 ? b[2] : 0.0,
-                                                      m >= 3 ? b[3] : 0.0);
+                                                      m >= 3 ? b[3] : 0.0, e2, e2max);
     TT_LAUNCHED(c);
 }
 
@@ -477,8 +586,8 @@ void axpy(Ctx& c, long n, double alpha, const T* x, T* y) {
     template void scatter_blocks<T>(Ctx&, const BlockList&, int, long, long, T*, int, int);      \
     template void axpy<T>(Ctx&, long, double, const T*, T*);                                     \
     template void inv_and_identity_defect<T>(Ctx&, int, const T*, const T*, double*);             \
-    template double near_identity<T>(Ctx&, int, const T*, T*, double*);                          \
-    template void poly_pair<T>(Ctx&, int, int, T*, const T*, const T*, T*);
+    template void near_identity<T>(Ctx&, int, const T*, T*, double*);                            \
+    template void poly_pair<T>(Ctx&, int, int, T*, const T*, const T*, T*, const double*, double*);
 TT_INST_T(float)
 TT_INST_T(double)
 template void gram<double, double>(Ctx&, bool, int, long, const double*, long, double*);

@@ -35,7 +35,7 @@ class TTError(RuntimeError):
 class _Stats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("kernel_launches", "roundings", "host_syncs", "bytes_in_use",
                                            "peak_bytes", "svd_calls", "certified_bonds", "fallback_orth", "svd_sweeps",
-                                           "series_passes")]
+                                           "series_passes", "series_retries")]
 
 
 class _Prof(C.Structure):
@@ -58,6 +58,7 @@ _SIGS = {
     "tt_ctx_reset_stats": (None, [_P]),
     "tt_ctx_precision": (_I, [_P]),
     "tt_ctx_set_profiling": (_I, [_P, _I]),
+    "tt_ctx_set_profiling_family": (_I, [_P, C.c_char_p]),
     "tt_ctx_get_profile": (_I, [_P, C.POINTER(_Prof), _I, _PI]),
     "tt_ctx_reset_profile": (None, [_P]),
     "tt_tensor_create": (_I, [_P, _I, _PI, _PI, C.POINTER(_PD), C.POINTER(_P)]),
@@ -153,8 +154,12 @@ class Ctx:
     def reset_stats(self):
         lib().tt_ctx_reset_stats(self._h)
 
-    def set_profiling(self, on=True):
+    def set_profiling(self, on=True, family=None):
+        """Event timing of the library's launches; family: time only that
+        kernel family (None: all)."""
         _check(lib().tt_ctx_set_profiling(self._h, 1 if on else 0), "tt_ctx_set_profiling")
+        _check(lib().tt_ctx_set_profiling_family(self._h, family.encode() if family else None),
+               "tt_ctx_set_profiling_family")
 
     def reset_profile(self):
         lib().tt_ctx_reset_profile(self._h)

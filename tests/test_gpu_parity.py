@@ -171,6 +171,30 @@ def test_round_series_second_pass_against_cholesky_pass(prec, monkeypatch):
     assert O.tt_diff_norm(out["1"][0], out["0"][0]) <= tol * nx
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed_tf32"])
+def test_round_series_retry_gives_the_cholesky_result(prec, monkeypatch):
+    # A rounding whose series pass is judged invalid (forced here) is redone
+    # with Cholesky passes: one retry per rounding, and the result of the
+    # series-free rounding (up to the run-to-run order of the split-K sums).
+    x = _sum_case(23, 5, 6, 20, 7)
+    out = {}
+    for sp in ("retry", "0"):
+        monkeypatch.setenv("TTGB_SERIES_PASS", sp)
+        c = T.Ctx(0, prec)
+        try:
+            y, err = T.tt_round(c, up(c, x), 1e-6)
+            st = c.stats()
+            out[sp] = (y.cores(), err, st["series_retries"], st["series_passes"])
+        finally:
+            c.close()
+    assert out["retry"][2] == 1 and out["retry"][3] > 0
+    assert out["0"][2] == 0 and out["0"][3] == 0
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert O.tt_ranks(out["retry"][0]) == O.tt_ranks(out["0"][0])
+    assert O.tt_diff_norm(out["retry"][0], out["0"][0]) <= tol * O.tt_norm(x)
+    assert out["retry"][1] <= 1e-6 and out["0"][1] <= 1e-6
+
+
 def test_round_mixed_exact_ranks_on_well_separated_spectrum(ctxs):
     # random sums: every singular value is far from eps, so ranks are exact
     x = _sum_case(12, 6, 6, 16, 5)
