@@ -149,8 +149,8 @@ void      tt_ctx_reset_profile(tt_ctx* ctx);
 /* Creates a TT with d cores, mode sizes n[0..d-1] and ranks r[0..d]
  * (r[0] = r[d] = 1) in the context's storage type.  host_cores[k] points to
  * r[k]*n[k]*r[k+1] doubles in the [r][n][r] layout, copied to the device
- * (converted to FP32 for FP32 contexts); host_cores == NULL gives zeros.
- * The host arrays are read before the call returns. */
+ * (narrowed to FP32 on the device for FP32 contexts); host_cores == NULL
+ * gives zeros.  The host arrays are read before the call returns. */
 tt_status tt_tensor_create(tt_ctx* ctx, int d, const int* n, const int* r,
                            const double* const* host_cores, tt_tensor** out);
 
@@ -167,8 +167,21 @@ tt_status tt_tensor_shape(const tt_tensor* x, int* d, int* n, int* r);
 /* Device pointer of core k (for zero-copy readers). */
 tt_status tt_tensor_core_ptr(const tt_tensor* x, int k, void** dev_ptr);
 
-/* Copies the cores to host_cores[k] (r[k]*n[k]*r[k+1] doubles each). */
+/* Copies the cores to host_cores[k] (r[k]*n[k]*r[k+1] doubles each;
+ * FP32 storage is widened on the device first). */
 tt_status tt_tensor_download(tt_ctx* ctx, const tt_tensor* x, double* const* host_cores);
+
+/* As tt_tensor_create, but host_cores[k] already holds the core in the
+ * context's storage type (float for TT_MIXED_TF32 and TT_FP32, double for
+ * TT_FP64) and is copied without conversion.  From page-locked host memory
+ * the copies are asynchronous on the context's stream: the host buffers must
+ * stay unchanged until a later synchronizing call on the context returns
+ * (tt_tensor_download*, tt_dot, tt_norm, tt_round ... all synchronize). */
+tt_status tt_tensor_create_storage(tt_ctx* ctx, int d, const int* n, const int* r,
+                                   const void* const* host_cores, tt_tensor** out);
+/* Copies the cores to host_cores[k] in the storage type (no conversion) and
+ * waits for the copies; page-locked buffers give full-bandwidth copies. */
+tt_status tt_tensor_download_storage(tt_ctx* ctx, const tt_tensor* x, void* const* host_cores);
 
 void tt_tensor_free(tt_tensor* x);
 

@@ -528,17 +528,60 @@ tt_status tt_tensor_create(tt_ctx* ctx, int d, const int* n, const int* r, const
             } else if (t->dtype == TT_DTYPE_F64) {
                 TT_CUDA(cudaMemcpyAsync(t->cores[k], host_cores[k], ne * 8, cudaMemcpyHostToDevice, ctx->stream));
             } else {
-                std::vector<float> tmp(ne);
-                for (size_t e = 0; e < ne; ++e) tmp[e] = (float)host_cores[k][e];
-                // pageable source: the call returns once tmp is staged
-                TT_CUDA(cudaMemcpyAsync(t->cores[k], tmp.data(), ne * 4, cudaMemcpyHostToDevice, ctx->stream));
+                // FP64 staging on the device, narrowed there (stream-ordered
+                // release); the host arrays are read before the call returns
+                double* st = (double*)ctx->alloc(ne * 8);
+                TT_CUDA(cudaMemcpyAsync(st, host_cores[k], ne * 8, cudaMemcpyHostToDevice, ctx->stream));
+                convert<double, float>(*ctx, (long)ne, st, (float*)t->cores[k]);
+                ctx->release(st, ne * 8);
             }
+        }
+        bool pinned = false;
+        for (int k = 0; host_cores && k < d && !pinned; ++k) {
+            cudaPointerAttributes at;
+            pinned = host_cores[k] && cudaPointerGetAttributes(&at, host_cores[k]) == cudaSuccess &&
+                     at.type == cudaMemoryTypeHost;
+        }
+        cudaGetLastError();
+        if (pinned) ctx->sync();  // page-locked sources are read asynchronously
+    } catch (...) {
+        free_tensor(t);
+        throw;
+    }
+    *out = t;
+    TT_API_END
+}
+
+tt_status tt_tensor_create_storage(tt_ctx* ctx, int d, const int* n, const int* r, const void* const* host_cores,
+                                   tt_tensor** out) {
+    TT_API_BEGIN
+    if (!ctx || !out || !host_cores) throw_status(TT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    tt_tensor* t = new_tensor(ctx, d, n, r);
+    try {
+        for (int k = 0; k < d; ++k) {
+            if (!host_cores[k]) throw_status(TT_ERR_ARG, "NULL host core");
+            const size_t bytes = t->core_elems(k) * dtype_size(t->dtype);
+            TT_CUDA(cudaMemcpyAsync(t->cores[k], host_cores[k], bytes, cudaMemcpyHostToDevice, ctx->stream));
         }
     } catch (...) {
         free_tensor(t);
         throw;
     }
     *out = t;
+    TT_API_END
+}
+
+tt_status tt_tensor_download_storage(tt_ctx* ctx, const tt_tensor* x, void* const* host_cores) {
+    TT_API_BEGIN
+    if (!ctx || !host_cores) throw_status(TT_ERR_ARG, "NULL argument");
+    check_tensor(ctx, x);
+    for (int k = 0; k < x->d; ++k) {
+        if (!host_cores[k]) throw_status(TT_ERR_ARG, "NULL host core");
+        const size_t bytes = x->core_elems(k) * dtype_size(x->dtype);
+        TT_CUDA(cudaMemcpyAsync(host_cores[k], x->cores[k], bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    ctx->sync();
     TT_API_END
 }
 
@@ -591,10 +634,10 @@ tt_status tt_tensor_download(tt_ctx* ctx, const tt_tensor* x, double* const* hos
         if (x->dtype == TT_DTYPE_F64) {
             TT_CUDA(cudaMemcpyAsync(host_cores[k], x->cores[k], ne * 8, cudaMemcpyDeviceToHost, ctx->stream));
         } else {
-            std::vector<float> tmp(ne);
-            TT_CUDA(cudaMemcpyAsync(tmp.data(), x->cores[k], ne * 4, cudaMemcpyDeviceToHost, ctx->stream));
-            ctx->sync();
-            for (size_t e = 0; e < ne; ++e) host_cores[k][e] = tmp[e];
+            double* st = (double*)ctx->alloc(ne * 8);
+            convert<float, double>(*ctx, (long)ne, (const float*)x->cores[k], st);
+            TT_CUDA(cudaMemcpyAsync(host_cores[k], st, ne * 8, cudaMemcpyDeviceToHost, ctx->stream));
+            ctx->release(st, ne * 8);
         }
     }
     ctx->sync();

@@ -66,6 +66,8 @@ _SIGS = {
     "tt_tensor_shape": (_I, [_P, _PI, _PI, _PI]),
     "tt_tensor_core_ptr": (_I, [_P, _I, _PP]),
     "tt_tensor_download": (_I, [_P, _P, C.POINTER(_PD)]),
+    "tt_tensor_create_storage": (_I, [_P, _I, _PI, _PI, C.POINTER(_P), C.POINTER(_P)]),
+    "tt_tensor_download_storage": (_I, [_P, _P, C.POINTER(_P)]),
     "tt_tensor_free": (None, [_P]),
     "tt_add": (_I, [_P, _I, _PD, _PP, C.POINTER(_P)]),
     "tt_scale": (_I, [_P, _P, _D, C.POINTER(_P)]),
@@ -233,6 +235,22 @@ class TT:
         _check(lib().tt_tensor_download(self.ctx.handle, self._h, ptrs), "tt_tensor_download")
         return out
 
+    def download_storage(self, out):
+        """Copies the cores into the given host arrays (numpy, the context's
+        storage dtype, at least r_{k-1} n_k r_k elements each; page-locked
+        memory gives full-bandwidth copies) without conversion; returns views
+        of the right shapes."""
+        d, n, r = self.shape()
+        views = []
+        for k in range(d):
+            v = out[k].reshape(-1)[: r[k] * n[k] * r[k + 1]]
+            if not v.flags["C_CONTIGUOUS"]:
+                raise ValueError("host buffer %d is not contiguous" % k)
+            views.append(v.reshape(r[k], n[k], r[k + 1]))
+        ptrs = (_P * d)(*[v.ctypes.data for v in views])
+        _check(lib().tt_tensor_download_storage(self.ctx.handle, self._h, ptrs), "tt_tensor_download_storage")
+        return views
+
     def free(self):
         if self._h:
             lib().tt_tensor_free(self._h)
@@ -257,6 +275,24 @@ def tt_tensor_create(ctx, cores):
     ptrs = (_PD * d)(*[c.ctypes.data_as(_PD) for c in cores])
     h = _P()
     _check(lib().tt_tensor_create(ctx.handle, d, n, r, ptrs, C.byref(h)), "tt_tensor_create")
+    return TT(ctx, h)
+
+
+def tt_tensor_create_storage(ctx, cores):
+    """tt_tensor_create from host arrays already in the context's storage
+    dtype (float32 for mixed_tf32 / fp32, float64 for fp64), copied without
+    conversion.  From page-locked memory the copies are asynchronous: keep
+    the arrays unchanged until a later synchronizing call returns."""
+    want = np.float64 if ctx.precision == "fp64" else np.float32
+    for c in cores:
+        if c.dtype != want or not c.flags["C_CONTIGUOUS"]:
+            raise ValueError("cores must be C-contiguous %s arrays" % np.dtype(want).name)
+    d = len(cores)
+    n = (C.c_int * d)(*[c.shape[1] for c in cores])
+    r = (C.c_int * (d + 1))(*([c.shape[0] for c in cores] + [cores[-1].shape[2]]))
+    ptrs = (_P * d)(*[c.ctypes.data for c in cores])
+    h = _P()
+    _check(lib().tt_tensor_create_storage(ctx.handle, d, n, r, ptrs, C.byref(h)), "tt_tensor_create_storage")
     return TT(ctx, h)
 
 

@@ -1,0 +1,66 @@
+"""Host <-> device transfers of TT cores: the FP64 entry points (narrowed or
+widened on the device for FP32 storage) and the storage-type entry points
+(no conversion), from pageable and page-locked host memory."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+T = pytest.importorskip("paper_2211_08770_gb300.ttgb")
+
+from ttinputs import random_tt  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    from paper_2211_08770_gb300 import build
+    build.build()
+    out = {p: T.Ctx(0, p) for p in ("fp64", "mixed_tf32")}
+    yield out
+    for c in out.values():
+        c.close()
+
+
+def _cores():
+    return random_tt(np.random.default_rng(5), [7, 33, 5, 64], [1, 6, 17, 9, 1])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_tf32"])
+def test_fp64_entry_points_round_trip(ctxs, prec):
+    # FP32 storage: the device narrowing and widening are round-to-nearest
+    # conversions, the same as the host's
+    c = ctxs[prec]
+    x = _cores()
+    got = T.tt_tensor_create(c, x).cores()
+    for a, b in zip(got, x):
+        want = b if prec == "fp64" else b.astype(np.float32).astype(np.float64)
+        assert np.array_equal(a, want)
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "mixed_tf32"])
+def test_storage_entry_points_round_trip(ctxs, prec, pinned):
+    c = ctxs[prec]
+    dt = np.float64 if prec == "fp64" else np.float32
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    x = [a.astype(dt) for a in _cores()]
+    if pinned:
+        hin = []
+        for a in x:
+            b = torch.empty(a.shape, dtype=tdt, pin_memory=True).numpy()
+            b[...] = a
+            hin.append(b)
+        out = [torch.full((a.size + 3,), float("nan"), dtype=tdt, pin_memory=True).numpy() for a in x]
+    else:
+        hin = [a.copy() for a in x]
+        out = [np.full(a.size + 3, np.nan, dtype=dt) for a in x]
+    t = T.tt_tensor_create_storage(c, hin)
+    views = t.download_storage(out)
+    for v, a in zip(views, x):
+        assert v.shape == a.shape and np.array_equal(v, a)
+    # the FP64 reader sees the same values
+    for g, a in zip(t.cores(), x):
+        assert np.array_equal(g, a.astype(np.float64))
+    with pytest.raises(ValueError):
+        T.tt_tensor_create_storage(c, [a.astype(np.float16) for a in x])
