@@ -110,92 +110,119 @@ gemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda,
     }
 }
 
-// Products of r x r size (the series pass, the factor products): 32 x 32
-// output tile per CTA (169 CTAs at r = 400, about one per SM), 256 threads
-// with 2 x 2 outputs each; the CTA's row and column slices of op(A) and
-// op(B) for a K chunk of up to RKC are staged whole in shared memory
-// (op(A) row-major, op(B) k-major, so a warp reads two broadcast A values
-// and 16 consecutive B values per k), one barrier per chunk.  No split-K,
-// no atomics.
+// Products of r x r size (the series pass, the factor products, the blocked
+// Cholesky's panel and trailing products): 32 x 32 output tile per CTA (169
+// CTAs at r = 400), 256 threads in 4 groups that split each K chunk, 4 x 4
+// outputs per thread read as 16-byte vectors from k-major shared tiles, the
+// groups' partial tiles summed through shared memory at the end.  A chunk
+// (KC of K) of both operands is staged by element-wise asynchronous copies
+// (zero-filled outside the matrices, any layout or alignment).  No split
+// over CTAs, no atomics.
 constexpr int RT = 32;
 
 template <class T>
-constexpr int rgemm_kc() { return sizeof(T) == 4 ? 512 : 256; }
+struct Vec4;
+template <>
+struct Vec4<float> {
+    __device__ __forceinline__ static void ld(const float* p, float* x) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+};
+template <>
+struct Vec4<double> {
+    __device__ __forceinline__ static void ld(const double* p, double* x) {
+        const double2 u = *reinterpret_cast<const double2*>(p), v = *reinterpret_cast<const double2*>(p + 2);
+        x[0] = u.x; x[1] = u.y; x[2] = v.x; x[3] = v.y;
+    }
+};
 
 template <class T>
-size_t rgemm_smem() { return sizeof(T) * (size_t)(RT * (rgemm_kc<T>() + 1) + rgemm_kc<T>() * (RT + 1)); }
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "n"(sizeof(T)), "r"(ok ? (int)sizeof(T) : 0));
+}
 
 template <class T, bool TA, bool TB>
 __global__ void __launch_bounds__(256)
 rgemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda, const T* __restrict__ B, long ldb,
              T beta, T* __restrict__ C, long ldc, int tri) {
-    constexpr int KC = rgemm_kc<T>();
-    extern __shared__ __align__(16) unsigned char rg_smem[];
-    T* As = reinterpret_cast<T*>(rg_smem);  // [RT][KC + 1]
-    T* Bs = As + RT * (KC + 1);              // [KC][RT + 1]
-    const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+    constexpr int KC = sizeof(T) == 4 ? 128 : 64;
+    constexpr int LDK = RT + 4;            // k-major rows of 32 (+ pad), 16-byte aligned
+    constexpr int PER = RT * KC / 256;     // staged elements per thread and operand
+    constexpr int SM = 2 * KC * LDK > 3 * RT * (RT + 1) ? 2 * KC * LDK : 3 * RT * (RT + 1);
+    __shared__ __align__(16) T smem[SM];
+    T* As = smem;             // As[k][i] = op(A)(m0 + i, k0 + k)
+    T* Bs = smem + KC * LDK;  // Bs[k][j] = op(B)(k0 + k, n0 + j)
+    const int tid = threadIdx.x;
+    const int grp = tid >> 6, t = tid & 63, ti = t >> 3, tj = t & 7;
     const int m0 = blockIdx.y * RT, n0 = blockIdx.x * RT;
     if (tri_skip_tile(tri, m0, n0, RT)) return;
     long kb = 0, ke = K;
     tri_krange(tri, m0, n0, RT, RT, kb, ke);
-    T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+    T acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
     for (long k0 = kb; k0 < ke; k0 += KC) {
         const int kc = (int)min((long)KC, ke - k0);
-        // stage op(A)(m0 + i, k0 + k) and op(B)(k0 + k, n0 + j): the lanes
-        // of a warp run along the global operand's contiguous index, the
-        // warps along the other one (several loads in flight per thread)
-        const int warp = tid >> 5, lane = tid & 31;
-        if (!TA) {
 #pragma unroll
-            for (int i = warp; i < RT; i += 8) {
+        for (int q = 0; q < PER; ++q) {
+            // element e of the chunk, the global operand's contiguous index fastest
+            const int e = tid + 256 * q;
+            {
+                const int k = TA ? e / RT : e % KC, i = TA ? e % RT : e / KC;
                 const long gm = m0 + i;
-                const T* src = A + gm * lda + k0;
-#pragma unroll 4
-                for (int k = lane; k < kc; k += 32) As[i * (KC + 1) + k] = gm < M ? src[k] : T(0);
+                const bool ok = gm < M && k < kc;
+                cp_async_elem(As + k * LDK + i, ok ? (TA ? A + (k0 + k) * lda + gm : A + gm * lda + k0 + k) : A, ok);
             }
-        } else {
-            const long gm = m0 + lane;
-#pragma unroll 4
-            for (int k = warp; k < kc; k += 8) As[lane * (KC + 1) + k] = gm < M ? A[(k0 + k) * lda + gm] : T(0);
-        }
-        if (!TB) {
-            const long gn = n0 + lane;
-#pragma unroll 4
-            for (int k = warp; k < kc; k += 8) Bs[k * (RT + 1) + lane] = gn < N ? B[(k0 + k) * ldb + gn] : T(0);
-        } else {
-#pragma unroll
-            for (int j = warp; j < RT; j += 8) {
+            {
+                const int k = TB ? e % KC : e / RT, j = TB ? e / KC : e % RT;
                 const long gn = n0 + j;
-                const T* src = B + gn * ldb + k0;
-#pragma unroll 4
-                for (int k = lane; k < kc; k += 32) Bs[k * (RT + 1) + j] = gn < N ? src[k] : T(0);
+                const bool ok = gn < N && k < kc;
+                cp_async_elem(Bs + k * LDK + j, ok ? (TB ? B + gn * ldb + k0 + k : B + (k0 + k) * ldb + gn) : B, ok);
             }
         }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
-        const T* a0 = As + ti * (KC + 1);
-        const T* a1 = As + (ti + 16) * (KC + 1);
-#pragma unroll 8
-        for (int k = 0; k < kc; ++k) {
-            const T x0 = a0[k], x1 = a1[k];
-            const T y0 = Bs[k * (RT + 1) + tj], y1 = Bs[k * (RT + 1) + tj + 16];
-            acc[0][0] = fma(x0, y0, acc[0][0]);
-            acc[0][1] = fma(x0, y1, acc[0][1]);
-            acc[1][0] = fma(x1, y0, acc[1][0]);
-            acc[1][1] = fma(x1, y1, acc[1][1]);
+#pragma unroll 4
+        for (int k = grp; k < kc; k += 4) {
+            T a[4], b[4];
+            Vec4<T>::ld(As + k * LDK + 4 * ti, a);
+            Vec4<T>::ld(Bs + k * LDK + 4 * tj, b);
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
         }
         __syncthreads();
     }
+    // groups 1..3 leave their partial tiles in shared memory, group 0 sums
+    T* red = smem;  // [3][RT][RT + 1]
+    if (grp > 0) {
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const long gm = m0 + ti + 16 * a;
-        if (gm >= M) continue;
+        for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const long gn = n0 + tj + 16 * b;
-            if (gn >= N) continue;
-            T v = alpha * acc[a][b];
-            if (beta != T(0)) v += beta * C[gm * ldc + gn];
-            C[gm * ldc + gn] = v;
+            for (int y = 0; y < 4; ++y) red[((grp - 1) * RT + 4 * ti + x) * (RT + 1) + 4 * tj + y] = acc[x][y];
+    }
+    __syncthreads();
+    if (grp == 0) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const long gm = m0 + 4 * ti + x;
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const long gn = n0 + 4 * tj + y;
+                T v = acc[x][y];
+#pragma unroll
+                for (int h = 0; h < 3; ++h) v += red[(h * RT + 4 * ti + x) * (RT + 1) + 4 * tj + y];
+                if (gm < M && gn < N) {
+                    v = alpha * v;
+                    if (beta != T(0)) v += beta * C[gm * ldc + gn];
+                    C[gm * ldc + gn] = v;
+                }
+            }
         }
     }
 }
@@ -263,13 +290,8 @@ void gemm(Ctx& c, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, lo
         ProfScope ps(c, sizeof(T) == 8 ? "rgemm_f64" : "rgemm_f32", gemm_flops(M, N, K, tri),
                      sizeof(T) * ((double)M * K + (double)K * N + 2.0 * M * N));
         dim3 g((N + RT - 1) / RT, (M + RT - 1) / RT);
-        const int sm = (int)rgemm_smem<T>();
-#define TT_RGEMM_CASE(TA_, TB_)                                                                             \
-    do {                                                                                                    \
-        static std::atomic<bool> attr{false};                                                               \
-        set_smem_once(attr, rgemm_kernel<T, TA_, TB_>, sm);                                                 \
-        rgemm_kernel<T, TA_, TB_><<<g, 256, sm, c.stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri); \
-    } while (0)
+#define TT_RGEMM_CASE(TA_, TB_) \
+    rgemm_kernel<T, TA_, TB_><<<g, 256, 0, c.stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri)
         if (!tA && !tB) TT_RGEMM_CASE(false, false);
         else if (!tA && tB) TT_RGEMM_CASE(false, true);
         else if (tA && !tB) TT_RGEMM_CASE(true, false);
