@@ -316,7 +316,8 @@ def run_ours(args):
                       "output_ranks": main["ranks"]},
            "gpu_launches": int(main["stats"]["kernel_launches"]),
            "host_syncs": int(main["stats"]["host_syncs"]),
-           "path_stats": {k: int(main["stats"][k]) for k in ("svd_calls", "certified_bonds", "fallback_orth", "series_passes")},
+           "path_stats": {k: int(main["stats"][k]) for k in ("svd_calls", "certified_bonds", "fallback_orth", "series_passes",
+                                                                          "second_pass_skips")},
            "clocks": main["clocks"]}
     # roofline of the dominant kernel family
     prof = main["prof"]

@@ -102,6 +102,9 @@ typedef struct {
                                   series (I + E)^(-1/2) of a near-identity Gram */
     uint64_t series_retries;   /* roundings redone with Cholesky passes because a
                                   series pass met a Gram too far from I */
+    uint64_t second_pass_skips; /* certified left-to-right bonds whose first
+                                   Cholesky QR pass was already orthonormal to
+                                   the required level (second pass not run) */
 } tt_stats;
 
 /* Per-kernel timing of a context (tt_ctx_set_profiling): CUDA events are

@@ -57,6 +57,10 @@ struct Rounder {
     double err2 = 0.0;       // accumulated discarded tail (squared, absolute)
     bool series = true;      // second Cholesky QR passes by the series
     bool series_used = false;
+    double last_e = 0.0;     // ||E||_F of the last series pass read by sigma_lb
+    double skip_budget = 0.0;  // certified left-to-right bonds keep their first
+                               // pass alone while the sum of their ||E||_F
+                               // stays within this budget
 
     Rounder(tt_ctx* ctx, const tt_tensor* x) : c(ctx), d(x->d), n(x->n), r(x->r) {
         const bool is64 = sizeof(T) == 8;
@@ -158,6 +162,7 @@ struct Rounder {
         bool series = false;  // the second pass was the series pass (||E||_F^2 in dsc[12])
         bool lower = true;    // Lp lower-triangular
         bool deferred = false;  // X holds Q1; the orthonormal factor is S Q1 (S in the defer slot)
+        bool series_pending = false;  // E measured, S / R2 / Lp not formed yet (lazy orth)
     };
 
     // The series pass is of order 3: valid while the Taylor remainders of
@@ -170,7 +175,32 @@ struct Rounder {
     // Lp receives L with X_old = L Q (rows) or X_old = Q L^T (cols), lower-
     // triangular unless the second pass was the series pass (o.lower).
     // Lf[i], Ti[i] keep the factors of each pass.
-    Orth orth(bool rows, int a, long K, T*& X, T* defer = nullptr) {
+    // Completes a series second pass whose E (in Ti[1]) and ||E||_F^2 (in
+    // dsc[12]) are in place: S over Ti[1], R2 in Lf[1], X <- S X (rows) or
+    // X S (cols) unless deferred, Lp = L1 R2.
+    void finish_series(bool rows, int a, long K, T*& X, T* defer, Orth& o) {
+        c->stats.series_passes++;
+        series_used = true;
+        mm(false, false, a, a, a, Ti[1], a, Ti[1], a, Lf[1], a);
+        mm(false, false, a, a, a, Lf[1], a, Ti[1], a, Tmp, a);
+        poly_pair<T>(*c, a, 3, Ti[1], Lf[1], Tmp, Lf[1], dsc + 12, dsc + 11);
+        if (defer) {
+            // X keeps Q1; S Q1 is formed by the caller's later products
+            // (rows only: S acts on the row index)
+            TT_CUDA(cudaMemcpyAsync(defer, Ti[1], sizeof(T) * (size_t)a * a, cudaMemcpyDeviceToDevice, c->stream));
+            o.deferred = true;
+        } else {
+            apply(rows, a, K, X, Ti[1], false);
+        }
+        mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Lp, a, TRI_A_LOWER);
+        o.series_pending = false;
+        o.lower = false;
+    }
+
+    // lazy: stop a series second pass after measuring E (the caller reads
+    // ||E||_F with its next synchronization and either completes the pass
+    // with finish_series or keeps the first pass's factor alone)
+    Orth orth(bool rows, int a, long K, T*& X, T* defer = nullptr, bool lazy = false) {
         const double sq = sqrt((double)a);
         const double drop_fb = 8.0 * ug_fb * sq;
         const double ratio_fast = tc ? 10.0 * ug_fast : 100.0 * ug_fast;
@@ -203,24 +233,10 @@ struct Rounder {
                     // the device, read with the statuses), not here: no
                     // synchronization; a rounding where it was too large
                     // is redone with Cholesky passes.
-                    c->stats.series_passes++;
-                    series_used = true;
                     near_identity<T>(*c, a, G, Ti[1], dsc + 12);
-                    mm(false, false, a, a, a, Ti[1], a, Ti[1], a, Lf[1], a);
-                    mm(false, false, a, a, a, Lf[1], a, Ti[1], a, Tmp, a);
-                    poly_pair<T>(*c, a, 3, Ti[1], Lf[1], Tmp, Lf[1], dsc + 12, dsc + 11);
-                    if (defer) {
-                        // X keeps Q1; S Q1 is formed by the caller's later
-                        // products (rows only: S acts on the row index)
-                        TT_CUDA(cudaMemcpyAsync(defer, Ti[1], sizeof(T) * (size_t)a * a, cudaMemcpyDeviceToDevice,
-                                                c->stream));
-                        o.deferred = true;
-                    } else {
-                        apply(rows, a, K, X, Ti[1], false);
-                    }
-                    mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Lp, a, TRI_A_LOWER);
                     o.series = true;
-                    o.lower = false;
+                    o.series_pending = true;
+                    if (!lazy) finish_series(rows, a, K, X, defer, o);
                     return o;
                 }
                 chol_inv<T, T>(*c, a, G, Lf[1], Ti[1], 0.0, drop_fb, next_st());
@@ -269,7 +285,10 @@ struct Rounder {
             // sigma_min((I + E)^(1/2)) >= sqrt(1 - ||E||_2); less the series
             // remainder and the rounding of the stored factor.  An invalid
             // series pass gives no bound (the rounding is redone anyway).
+            // The same bound holds for Q1 itself (sigma(Q1) in
+            // [sqrt(1 - e), sqrt(1 + e)]) when the pass is not completed.
             const double e = sqrt(h[12]);
+            last_e = e;
             if (!series_valid(e)) return 0.0;
             lb = std::max(0.0, sqrt(1.0 - e) - (2.0 + sqrt((double)a)) * ug_fb);
         }
@@ -426,8 +445,27 @@ struct Rounder {
             const int b = r[k + 1];
             const long NR = (long)n[k + 1] * r[k + 2];
             if (m >= b) {
-                Orth o = orth(false, b, m, core[k]);
+                Orth o = orth(false, b, m, core[k], nullptr, true);
                 const double lb = sigma_lb(b, o);
+                if (o.series_pending) {
+                    if (lb > 2.0 * eps && lb > 0.0 && last_e <= skip_budget) {
+                        // certified, and Q1 is orthonormal to ||E||_F: the
+                        // bond keeps its rank with core_k = Q1 and
+                        // core_{k+1} <- L1^T core_{k+1} (X = Q1 L1^T exactly);
+                        // the second pass would only sharpen the cores'
+                        // orthonormality.  The left factor of a later bond
+                        // then has singular values within 1 +- (sum of the
+                        // skipped ||E||_F) / 2, which scales that bond's
+                        // truncation error by at most the same factor
+                        skip_budget -= last_e;
+                        c->stats.certified_bonds++;
+                        c->stats.second_pass_skips++;
+                        transpose<T>(*c, b, b, Lf[0], Tmp);
+                        absorb_next(k, b, Tmp, b, TRI_A_UPPER);
+                        continue;
+                    }
+                    finish_series(false, b, m, core[k], nullptr, o);
+                }
                 if (lb > 2.0 * eps && lb > 0.0) {
                     c->stats.certified_bonds++;
                     // core_{k+1} <- R core_{k+1}, R = Lp^T
@@ -553,6 +591,11 @@ tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_es
         if (attempt > 0) R.series = false;
         R.rl_sweep();
         const double nrm = R.core_norm(0);
+        // skipped left-to-right second passes move the rounding bound by at
+        // most delta (sum of their ||E||_F) relative: kept well below the
+        // storage precision's resolution of the result, and the singular
+        // values seen by later truncations within 2.5%
+        R.skip_budget = std::min(0.05, (sizeof(T) == 8 ? 1e-14 : 1e-7) / std::max(delta, 1e-300));
         R.lr_sweep(delta * nrm / sqrt((double)(x->d - 1)));
         if (!R.check_all_status()) {
             // a series pass met a Gram too far from I: redo with Cholesky passes
