@@ -47,6 +47,7 @@ std::vector<Ctx*> get_lanes(Ctx& root, int count) {
         l->chol_nb = root.chol_nb;
         l->use_series = root.use_series;
         l->series_force_retry = root.series_force_retry;
+        l->series_no_skip = root.series_no_skip;
         l->prof = root.prof;
         l->prof_only = root.prof_only;
     }

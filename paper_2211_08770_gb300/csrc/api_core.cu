@@ -419,10 +419,12 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     // TTGB_SERIES_PASS=0 keeps the Cholesky factorization for every second
     // Cholesky QR pass (no series pass); =retry treats every series pass as
     // invalid, so each rounding is redone with Cholesky passes (exercises
-    // the retry path)
+    // the retry path); =noskip keeps every second pass
     const char* sp = getenv("TTGB_SERIES_PASS");
     if (sp && sp[0] == '0') c->use_series = false;
     if (sp && sp[0] == 'r') c->series_force_retry = true;
+    // =noskip: every second pass runs (no first pass is kept alone)
+    if (sp && sp[0] == 'n') c->series_no_skip = true;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;

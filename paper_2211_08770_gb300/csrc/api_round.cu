@@ -57,10 +57,9 @@ struct Rounder {
     double err2 = 0.0;       // accumulated discarded tail (squared, absolute)
     bool series = true;      // second Cholesky QR passes by the series
     bool series_used = false;
-    double last_e = 0.0;     // ||E||_F of the last series pass read by sigma_lb
-    double skip_budget = 0.0;  // certified left-to-right bonds keep their first
-                               // pass alone while the sum of their ||E||_F
-                               // stays within this budget
+    double skip_budget = 0.0;  // second passes are skipped (first pass kept
+                               // alone) while the sum of their ||E||_F stays
+                               // within this budget (0: never, e.g. for norms)
 
     Rounder(tt_ctx* ctx, const tt_tensor* x) : c(ctx), d(x->d), n(x->n), r(x->r) {
         const bool is64 = sizeof(T) == 8;
@@ -162,7 +161,9 @@ struct Rounder {
         bool series = false;  // the second pass was the series pass (||E||_F^2 in dsc[12])
         bool lower = true;    // Lp lower-triangular
         bool deferred = false;  // X holds Q1; the orthonormal factor is S Q1 (S in the defer slot)
-        bool series_pending = false;  // E measured, S / R2 / Lp not formed yet (lazy orth)
+        bool series_pending = false;  // E measured, S / R2 / Lp not formed yet
+        double e = 0.0;               // ||E||_F of a series pass
+        double lb = -1.0;             // certificate bound formed by orth (lr, series), else < 0
     };
 
     // The series pass is of order 3: valid while the Taylor remainders of
@@ -197,10 +198,16 @@ struct Rounder {
         o.lower = false;
     }
 
-    // lazy: stop a series second pass after measuring E (the caller reads
-    // ||E||_F with its next synchronization and either completes the pass
-    // with finish_series or keeps the first pass's factor alone)
-    Orth orth(bool rows, int a, long K, T*& X, T* defer = nullptr, bool lazy = false) {
+    // The first pass's product and the second pass's Gram (and E, and for
+    // the left-to-right sweep the first factor's certificate norms) are
+    // launched before the first factorization's health is known: one
+    // synchronization reads all of it.  An unhealthy first pass restores
+    // the original X (kept in `spare` by the apply) and takes the shifted
+    // path.  With the series on, a pass whose ||E||_F fits *budget keeps the
+    // first pass alone (right-to-left: no certificate needed; `lr`: the
+    // caller decides after the certificate, o.series_pending); otherwise the
+    // series pass completes (finish_series).
+    Orth orth(bool rows, int a, long K, T*& X, T* defer = nullptr, double* budget = nullptr, bool lr = false) {
         const double sq = sqrt((double)a);
         const double drop_fb = 8.0 * ug_fb * sq;
         const double ratio_fast = tc ? 10.0 * ug_fast : 100.0 * ug_fast;
@@ -212,31 +219,62 @@ struct Rounder {
             // pivot / own diagonal, which Cholesky QR is invariant to
             // (column or row scaling does not change it)
             chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 0.0, drop_fb, s0);
-            CholStatus h = read_st(s0);
+            apply(rows, a, K, X, Ti[0]);
+            // the second pass's Gram: a TF32 Gram of the nearly
+            // orthonormal X measures E to about u_tf32 / sqrt(K), so
+            // it leaves Q orthonormal to that (not to FP32 level); the
+            // factorization X = L Q itself stays exact to FP32 rounding
+            // (S and R come from the same E).  On tensor cores for long
+            // unfoldings (K >= kTc2MinK: defect <= 8e-6), else FP32.
+            gram_into(rows, K >= kTc2MinK, a, K, X);
+            if (series) near_identity<T>(*c, a, G, Ti[1], dsc + 12);
+            if (lr && series) {
+                TT_CUDA(cudaMemsetAsync(dsc, 0, 2 * sizeof(double), c->stream));
+                inv_and_identity_defect<T>(*c, a, Lf[0], Ti[0], dsc);
+            }
+            CholStatus h;
+            double hd[13] = {0};
+            TT_CUDA(cudaMemcpyAsync(&h, s0, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+            TT_CUDA(cudaMemcpyAsync(hd, dsc, 13 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            c->sync();
+            if (h.nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in a Gram matrix");
             if (h.ndrop == 0 && h.min_ratio >= ratio_fast) {
-                apply(rows, a, K, X, Ti[0]);
-                // the second pass's Gram: a TF32 Gram of the nearly
-                // orthonormal X measures E to about u_tf32 / sqrt(K), so
-                // it leaves Q orthonormal to that (not to FP32 level); the
-                // factorization X = L Q itself stays exact to FP32 rounding
-                // (S and R come from the same E).  On tensor cores for long
-                // unfoldings (K >= kTc2MinK: defect <= 8e-6), else FP32.
-                gram_into(rows, K >= kTc2MinK, a, K, X);
                 o.npass = 2;
                 o.nchol = 1;
                 if (series) {
                     // G = I + E with E small: Q <- (I + E)^(-1/2) Q and
                     // R = (I + E)^(1/2) from the cubic series in E (two
                     // a x a products instead of a Cholesky factorization;
-                    // the factor is symmetric, not triangular).  ||E||_F is
-                    // checked at the end of the rounding (one maximum on
-                    // the device, read with the statuses), not here: no
-                    // synchronization; a rounding where it was too large
-                    // is redone with Cholesky passes.
-                    near_identity<T>(*c, a, G, Ti[1], dsc + 12);
+                    // the factor is symmetric, not triangular).  The
+                    // series' validity is checked at the end of the
+                    // rounding (one maximum on the device, read with the
+                    // statuses); a rounding where ||E||_F was too large is
+                    // redone with Cholesky passes.
+                    const double e = sqrt(hd[12]);
                     o.series = true;
                     o.series_pending = true;
-                    if (!lazy) finish_series(rows, a, K, X, defer, o);
+                    o.e = e;
+                    if (lr) {
+                        // sigma_min(Q1) >= sqrt(1 - e), sigma_min of the
+                        // completed pass's factor likewise (less the series
+                        // remainder and the stored factor's rounding)
+                        const double lb1 = std::max(hd[0] > 0.0 ? 1.0 / sqrt(hd[0]) : 0.0, 1.0 - sqrt(hd[1]));
+                        o.lb = series_valid(e) ? lb1 * std::max(0.0, sqrt(1.0 - e) - (2.0 + sq) * ug_fb) : 0.0;
+                        return o;
+                    }
+                    if (budget && series_valid(e) && e <= *budget) {
+                        // Q1 is orthonormal to e: keep it (X = L1 Q1 to
+                        // storage rounding); later truncations see
+                        // singular values within 1 +- (sum of skipped e)/2
+                        *budget -= e;
+                        c->stats.second_pass_skips++;
+                        TT_CUDA(cudaMemcpyAsync(Lp, Lf[0], sizeof(T) * (size_t)a * a, cudaMemcpyDeviceToDevice,
+                                                c->stream));
+                        o.series_pending = false;
+                        o.lower = true;
+                        return o;
+                    }
+                    finish_series(rows, a, K, X, defer, o);
                     return o;
                 }
                 chol_inv<T, T>(*c, a, G, Lf[1], Ti[1], 0.0, drop_fb, next_st());
@@ -245,6 +283,8 @@ struct Rounder {
                 o.nchol = 2;
                 return o;
             }
+            // the first pass's product is discarded: the original X
+            std::swap(X, spare);
         }
         // shifted Cholesky QR, then two passes with dependent rows dropped
         c->stats.fallback_orth++;
@@ -288,7 +328,6 @@ struct Rounder {
             // The same bound holds for Q1 itself (sigma(Q1) in
             // [sqrt(1 - e), sqrt(1 + e)]) when the pass is not completed.
             const double e = sqrt(h[12]);
-            last_e = e;
             if (!series_valid(e)) return 0.0;
             lb = std::max(0.0, sqrt(1.0 - e) - (2.0 + sqrt((double)a)) * ug_fb);
         }
@@ -422,7 +461,7 @@ struct Rounder {
                 fill_identity<T>(*c, (int)K, core[k], K);
                 r[k] = (int)K;
             } else {
-                const Orth o = orth(true, a, K, core[k], Pend + (size_t)k * rmax * rmax);
+                const Orth o = orth(true, a, K, core[k], Pend + (size_t)k * rmax * rmax, &skip_budget);
                 pend[k] = o.deferred;
                 mm(false, false, M, a, a, core[k - 1], a, Lp, a, spare, a, o.lower ? TRI_B_LOWER : 0);
                 std::swap(core[k - 1], spare);
@@ -445,10 +484,10 @@ struct Rounder {
             const int b = r[k + 1];
             const long NR = (long)n[k + 1] * r[k + 2];
             if (m >= b) {
-                Orth o = orth(false, b, m, core[k], nullptr, true);
-                const double lb = sigma_lb(b, o);
+                Orth o = orth(false, b, m, core[k], nullptr, nullptr, true);
+                const double lb = o.lb >= 0.0 ? o.lb : sigma_lb(b, o);
                 if (o.series_pending) {
-                    if (lb > 2.0 * eps && lb > 0.0 && last_e <= skip_budget) {
+                    if (lb > 2.0 * eps && lb > 0.0 && o.e <= skip_budget) {
                         // certified, and Q1 is orthonormal to ||E||_F: the
                         // bond keeps its rank with core_k = Q1 and
                         // core_{k+1} <- L1^T core_{k+1} (X = Q1 L1^T exactly);
@@ -457,7 +496,7 @@ struct Rounder {
                         // then has singular values within 1 +- (sum of the
                         // skipped ||E||_F) / 2, which scales that bond's
                         // truncation error by at most the same factor
-                        skip_budget -= last_e;
+                        skip_budget -= o.e;
                         c->stats.certified_bonds++;
                         c->stats.second_pass_skips++;
                         transpose<T>(*c, b, b, Lf[0], Tmp);
@@ -589,13 +628,15 @@ tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_es
     for (int attempt = 0;; ++attempt) {
         Rounder<T> R(ctx, x);
         if (attempt > 0) R.series = false;
+        // skipped second passes (either sweep) leave cores orthonormal to
+        // their ||E||_F; the norm and every truncation then see singular
+        // values within 1 +- (sum of skipped ||E||_F) / 2, which moves the
+        // rounding bound by at most delta times that sum: kept well below
+        // the storage precision's resolution of the result, and within 2.5%
+        R.skip_budget = (ctx->series_no_skip || ctx->series_force_retry) ? 0.0
+                                            : std::min(0.05, (sizeof(T) == 8 ? 1e-14 : 1e-7) / std::max(delta, 1e-300));
         R.rl_sweep();
         const double nrm = R.core_norm(0);
-        // skipped left-to-right second passes move the rounding bound by at
-        // most delta (sum of their ||E||_F) relative: kept well below the
-        // storage precision's resolution of the result, and the singular
-        // values seen by later truncations within 2.5%
-        R.skip_budget = std::min(0.05, (sizeof(T) == 8 ? 1e-14 : 1e-7) / std::max(delta, 1e-300));
         R.lr_sweep(delta * nrm / sqrt((double)(x->d - 1)));
         if (!R.check_all_status()) {
             // a series pass met a Gram too far from I: redo with Cholesky passes

@@ -257,6 +257,7 @@ struct Ctx {
     int chol_nb = 0;              // block size of chol_inv (0: the per-order table)
     bool use_series = true;       // series second pass of Cholesky QR when it is accurate
     bool series_force_retry = false;  // treat series passes as invalid (tests the retry)
+    bool series_no_skip = false;      // run every second pass (tests the series pass itself)
 
     // event profiling of launches (off by default)
     bool prof = false;
