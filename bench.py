@@ -445,11 +445,13 @@ def time_serve(T, dev, prec, count, rate, workers):
 
 
 def _src_hash(source=None):
-    """sha1 (12 hex digits) of one file of the CUDA sources, or of all."""
+    """sha1 (12 hex digits) of some files of the CUDA sources (a name or a
+    list of names), or of all."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2211_08770_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)) if source is None else [source]:
+    names = sorted(os.listdir(csrc)) if source is None else ([source] if isinstance(source, str) else list(source))
+    for fn in names:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]

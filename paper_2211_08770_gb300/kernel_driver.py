@@ -4,6 +4,7 @@ profiling it in isolation (e.g. under ncu):
     python -m paper_2211_08770_gb300.kernel_driver gemm   # apply Q = T X, 400 x 25600 x 400 (FP32)
     python -m paper_2211_08770_gb300.kernel_driver gram   # tensor-core Gram X X^T, n = 400, K = 25600
     python -m paper_2211_08770_gb300.kernel_driver chol   # Cholesky + inverse, n = 256 (FP32)
+    python -m paper_2211_08770_gb300.kernel_driver chol400  # the blocked r = 400 factorization
     python -m paper_2211_08770_gb300.kernel_driver rgemm  # r x r product, 400 x 400 x 400 (FP32)
 
 The shapes are the interior bond of the single-rounding workload (20 summed
@@ -37,7 +38,8 @@ def main(which, r=400, K=25600, n=256):
         Cm = torch.empty_like(A)
         for _ in range(3):
             T.tt_gemm_f32(c, False, r, r, r, A.data_ptr(), r, B.data_ptr(), r, Cm.data_ptr(), r, 0)
-    elif which == "chol":
+    elif which in ("chol", "chol400"):
+        n = 400 if which == "chol400" else n
         Xh = rng.standard_normal((n, 4 * n))
         G = torch.tensor(Xh @ Xh.T, dtype=torch.float32, device="cuda")
         L = torch.empty_like(G)
@@ -45,7 +47,7 @@ def main(which, r=400, K=25600, n=256):
         for _ in range(3):
             T.tt_cholesky_inverse(c, n, G.data_ptr(), L.data_ptr(), Ti.data_ptr())
     else:
-        raise SystemExit("usage: kernel_driver gemm|gram|chol|rgemm")
+        raise SystemExit("usage: kernel_driver gemm|gram|chol|chol400|rgemm")
     torch.cuda.synchronize()
     c.close()
     print("ok", which)
