@@ -3,14 +3,19 @@
 //
 // Right-to-left sweep: each right unfolding X (r_{k-1} x n_k r_k) is
 // factored X = L Q with Q row-orthonormal by Cholesky QR passes: Gram
-// G = X X^T, G = L L^T, Q = L^{-1} X, twice (CholQR2) when the first
-// Cholesky is healthy, otherwise three passes of which the first is shifted
-// (G + s I), with numerically dependent rows dropped.  The second pass's
-// Gram is I + E with E of the order of the first pass's rounding; when
-// ||E||_F is small enough for a Taylor series of order <= 3 to reach the
-// storage precision, that pass is Q <- (I + E)^(-1/2) Q with the factor
-// (I + E)^(1/2) (symmetric), instead of a second Cholesky factorization.
-// L is absorbed into core k-1.  ||x|| = ||core_1||_F.
+// G = X X^T, G = L L^T, Q = L^{-1} X.  When the first Cholesky is healthy,
+// the Gram of its Q is I + E with E of the order of the first pass's
+// rounding.  The second pass is then either skipped (the first pass's
+// Q is kept, orthonormal to ||E||_F, while the summed ||E||_F of the kept
+// passes stays within a budget that bounds their effect on the rounding by
+// a small multiple of the storage precision), or Q <- (I + E)^(-1/2) Q with
+// the factor (I + E)^(1/2) from the cubic Taylor series (valid while its
+// remainder is below the storage precision; checked once per rounding), or
+// a second Cholesky pass when the series is off.  An unhealthy first pass
+// gives three passes of which the first is shifted (G + s I), with
+// numerically dependent rows dropped.  L is absorbed into core k-1; the
+// series transform of the right-to-left sweep is folded into the
+// left-to-right sweep's absorb.  ||x|| = ||core_1||_F.
 // Left-to-right sweep: each left unfolding X (r_{k-1} n_k x r_k) is factored
 // X = Q R the same way (on columns); the bond keeps its rank when a
 // certified lower bound of sigma_min(R) exceeds 2 eps, else R is decomposed
