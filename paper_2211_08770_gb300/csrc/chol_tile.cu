@@ -563,12 +563,16 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
     }
 }
 
-// Blocked driver pieces: shift, threshold and status of the whole matrix;
-// working copy L = lower(G) + shift I; strictly upper part of L zeroed.
+// Blocked driver preparation, one launch: every block reduces the diagonal
+// (trace and maximum: n loads, the same in every block) for the shift
+// shift_rel trace(G) and the drop threshold drop_rel (max_j G_jj + shift);
+// block 0 publishes them (ext) and initialises the status; all blocks copy
+// L = lower(G) + shift I (strictly upper part zero) and zero T.
 template <class S>
-__global__ void chol_prologue_kernel(int n, const S* __restrict__ G, double shift_rel, double drop_rel,
-                                     double* __restrict__ ext, CholStatus* __restrict__ st) {
-    __shared__ double rt[32], rm[32];
+__global__ void chol_prep_kernel(int n, const S* __restrict__ G, double shift_rel, double drop_rel,
+                                 double* __restrict__ ext, CholStatus* __restrict__ st, S* __restrict__ L,
+                                 S* __restrict__ T) {
+    __shared__ double rt[32], rm[32], sh;
     double tr = 0.0, mx = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double g = (double)G[(long)i * n + i];
@@ -593,21 +597,20 @@ __global__ void chol_prologue_kernel(int n, const S* __restrict__ G, double shif
             mx = fmax(mx, rm[w]);
         }
         const double shift = shift_rel * tr;
-        ext[0] = shift;
-        ext[1] = drop_rel * (mx + shift);
-        st->ndrop = 0;
-        st->nonfinite = 0;
-        st->min_ratio = 1e300;
-        st->trace = tr;
-        st->max_diag = mx;
+        sh = shift;
+        if (blockIdx.x == 0) {
+            ext[0] = shift;
+            ext[1] = drop_rel * (mx + shift);
+            st->ndrop = 0;
+            st->nonfinite = 0;
+            st->min_ratio = 1e300;
+            st->trace = tr;
+            st->max_diag = mx;
+        }
     }
-}
-
-template <class S>
-__global__ void chol_copy_lower_kernel(int n, const S* __restrict__ G, const double* __restrict__ ext,
-                                       S* __restrict__ L, S* __restrict__ T) {
+    __syncthreads();
+    const double shift = sh;
     const long total = (long)n * n;
-    const double shift = ext[0];
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
         const long i = e / n, j = e % n;
         S v = S(0);
@@ -615,16 +618,6 @@ __global__ void chol_copy_lower_kernel(int n, const S* __restrict__ G, const dou
         L[e] = v;
         T[e] = S(0);
     }
-}
-
-template <class S>
-__global__ void chol_finish_kernel(int n, S* __restrict__ L, CholStatus* __restrict__ st) {
-    const long total = (long)n * n;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const long i = e / n, j = e % n;
-        if (j > i) L[e] = S(0);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && st->min_ratio > 1e299) st->min_ratio = 0.0;
 }
 
 template <class S, class C>
@@ -661,10 +654,8 @@ void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, do
     } rel{c, ws, wbytes};
     double* ext = (double*)ws;
     S* W = (S*)(ws + 256);
-    chol_prologue_kernel<S><<<1, 256, 0, c.stream>>>(n, G, shift_rel, drop_rel, ext, st);
-    TT_LAUNCHED(c);
-    const int cb = std::min(4 * c.sm_count, (int)(((long)n * n + 255) / 256));
-    chol_copy_lower_kernel<S><<<std::max(cb, 1), 256, 0, c.stream>>>(n, G, ext, L, T);
+    const int cb = std::min(2 * c.sm_count, (int)(((long)n * n + 255) / 256));
+    chol_prep_kernel<S><<<std::max(cb, 1), 256, 0, c.stream>>>(n, G, shift_rel, drop_rel, ext, st, L, T);
     TT_LAUNCHED(c);
     const long ld = n;
     for (int j = 0; j < m; ++j) {
@@ -690,8 +681,9 @@ void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, do
         gemm<S>(c, false, false, M, b, M, S(-1), T + j1 * (ld + 1), ld, W, b, S(0), T + j1 * ld + j0, ld, 1, 0, 0, 0,
                 TRI_A_LOWER);
     }
-    chol_finish_kernel<S><<<std::max(cb, 1), 256, 0, c.stream>>>(n, L, st);
-    TT_LAUNCHED(c);
+    // L's strictly upper part is still zero: the diagonal blocks are stored
+    // with zeros above their diagonal and the trailing products write lower
+    // elements only (TRI_C_LOWER)
 }
 
 // Block size per precision and order (the one-CTA kernel when it fits).

@@ -70,8 +70,9 @@ enum : int {
     TRI_A_UPPER = 2,  // op(A)(m, k) = 0 for k < m
     TRI_B_LOWER = 4,  // op(B)(k, n) = 0 for k < n
     TRI_B_UPPER = 8,  // op(B)(k, n) = 0 for k > n
-    TRI_C_LOWER = 16, // only the lower triangle of C is wanted: output tiles
-                      // strictly above the diagonal are not computed
+    TRI_C_LOWER = 16, // only the lower triangle of C is computed and written:
+                      // output tiles strictly above the diagonal are skipped
+                      // and elements above it are left unchanged
 };
 
 // the k-range [kb, ke) an output tile (rows m0.., cols n0..) needs; an

@@ -97,6 +97,7 @@ gemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda,
         for (int j = 0; j < 4; ++j) {
             const long gn = n0 + tx + 16 * j;
             if (gn >= N) continue;
+            if (MODE != 1 && (tri & TRI_C_LOWER) && gn > gm) continue;  // lower triangle only
             if (MODE == 0) {
                 T v = alpha * acc[i][j];
                 if (beta != T(0)) v += beta * (T)C[gm * ldc + gn];
@@ -217,7 +218,7 @@ rgemm_kernel(int M, int N, long K, T alpha, const T* __restrict__ A, long lda, c
                 T v = acc[x][y];
 #pragma unroll
                 for (int h = 0; h < 3; ++h) v += red[(h * RT + 4 * ti + x) * (RT + 1) + 4 * tj + y];
-                if (gm < M && gn < N) {
+                if (gm < M && gn < N && !((tri & TRI_C_LOWER) && gn > gm)) {
                     v = alpha * v;
                     if (beta != T(0)) v += beta * C[gm * ldc + gn];
                     C[gm * ldc + gn] = v;

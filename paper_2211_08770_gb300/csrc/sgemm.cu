@@ -172,7 +172,11 @@ sgemm_kernel(int M, int N, long K, float alpha, const float* __restrict__ A, lon
                     o[e] = alpha * v[e];
                     if (beta != 0.f && gn + e < N) o[e] = fmaf(beta, cp[e], o[e]);
                 }
-                if (gn + 3 < N && cvec) {
+                if ((tri & TRI_C_LOWER) && gn + 3 > gm) {  // lower triangle only
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (gn + e < N && gn + e <= gm) cp[e] = o[e];
+                } else if (gn + 3 < N && cvec) {
                     *reinterpret_cast<float4*>(cp) = make_float4(o[0], o[1], o[2], o[3]);
                 } else {
 #pragma unroll
