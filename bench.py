@@ -258,8 +258,9 @@ def run_ours(args):
 
     def time_e2e(precision, steps):
         """The public API end to end from page-locked host memory: upload of
-        the 20 input TTs (storage dtype), tt_add, tt_round, download of the
-        rounded TT into page-locked buffers; every step."""
+        the 20 input TTs (storage dtype), tt_add, and tt_round_to_host (the
+        rounded cores copied into page-locked buffers as the sweep finishes
+        them); every step."""
         ctx = T.Ctx(local, precision, stream=stream.cuda_stream)
         dt = torch.float64 if precision == "fp64" else torch.float32
         es = 8 if precision == "fp64" else 4
@@ -282,8 +283,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             X = [T.tt_tensor_create_storage(ctx, c) for c in hin]
             s = T.tt_add(ctx, al, X)
-            y, _ = T.tt_round(ctx, s, DELTA)
-            cores = y.download_storage(hout)
+            y, _, cores = T.tt_round_to_host(ctx, s, DELTA, hout)
             t1 = time.perf_counter()
             d2h = sum(c.size for c in cores) * es
             for v in X + [s, y]:
@@ -293,7 +293,7 @@ def run_ours(args):
         ctx.close()
         value, _ = job_throughput(world, len(times), sum(times), dist, dev)
         return dict(value=value, unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
-                    host_memory="page-locked, storage dtype (tt_tensor_create_storage / tt_tensor_download_storage)")
+                    host_memory="page-locked, storage dtype (tt_tensor_create_storage / tt_round_to_host)")
 
     prec = args.precision
     # Every family's launches are timed on a short separate pass (two events

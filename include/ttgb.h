@@ -224,6 +224,17 @@ tt_status tt_norm(tt_ctx* ctx, const tt_tensor* x, double* out);
 tt_status tt_round(tt_ctx* ctx, const tt_tensor* x, double delta,
                    tt_tensor** out, double* err_est);
 
+/* tt_round that also copies the rounded cores to host memory in the storage
+ * type: host_cores[k] must hold at least r[k]*n[k]*r[k+1] elements of x's
+ * core k (rounding never raises a rank); on return it holds the rounded
+ * core k, whose ranks *out reports.  Each core is copied as soon as the
+ * left-to-right sweep has finished it, on a second stream, so from
+ * page-locked memory the copies overlap the rest of the sweep; the call
+ * returns when every copy is complete.  *out is the same device result as
+ * tt_round's. */
+tt_status tt_round_to_host(tt_ctx* ctx, const tt_tensor* x, double delta, tt_tensor** out,
+                           double* err_est, void* const* host_cores);
+
 /* Rounds count independent tensors, each at its own delta[i] (TT-round of
  * Section 2.3 applied to every x[i]; the paper has no batched form).  The
  * roundings run concurrently on the context's lanes (tt_ctx_set_concurrency):

@@ -79,7 +79,16 @@ cudaEvent_t Ctx::event() {
     return e;
 }
 
+cudaStream_t Ctx::copies() {
+    if (!copy_stream) TT_CUDA(cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking));
+    return copy_stream;
+}
+
 Ctx::~Ctx() {
+    if (copy_stream) {
+        cudaStreamSynchronize(copy_stream);
+        cudaStreamDestroy(copy_stream);
+    }
     for (Ctx* l : lanes) {
         cudaStreamSynchronize(l->stream);
         delete static_cast<tt_ctx*>(l);  // lanes are allocated as tt_ctx

@@ -104,7 +104,30 @@ struct Rounder {
             TT_CUDA(cudaMemcpyAsync(core[k], x->cores[k], sizeof(T) * x->core_elems(k), cudaMemcpyDeviceToDevice,
                                     c->stream));
     }
-    ~Rounder() { if (ws) c->release(ws, ws_bytes); }
+    ~Rounder() {
+        // host copies still reading the workspace's cores finish first
+        if (copied) cudaStreamSynchronize(c->copy_stream);
+        for (cudaEvent_t e : copy_events) c->ev_pool.push_back(e);
+        if (ws) c->release(ws, ws_bytes);
+    }
+
+    // Host destinations of the output cores (storage type, null: none):
+    // each core is copied as soon as the left-to-right sweep has finished
+    // it, on the context's copy stream, overlapping the rest of the sweep.
+    void* const* host_out = nullptr;
+    bool copied = false;
+    std::vector<cudaEvent_t> copy_events;
+    void stream_core(int k) {
+        if (!host_out) return;
+        cudaStream_t cs = c->copies();
+        cudaEvent_t ev = c->event();
+        copy_events.push_back(ev);
+        TT_CUDA(cudaEventRecord(ev, c->stream));
+        TT_CUDA(cudaStreamWaitEvent(cs, ev, 0));
+        const size_t bytes = sizeof(T) * (size_t)r[k] * n[k] * r[k + 1];
+        TT_CUDA(cudaMemcpyAsync(host_out[k], core[k], bytes, cudaMemcpyDeviceToHost, cs));
+        copied = true;
+    }
 
     // bytes of the workspace carved in the constructor (d + 1 core buffers,
     // 12 + d r x r matrices, Jacobi work, singular values, scalars, statuses)
@@ -485,6 +508,7 @@ struct Rounder {
 
     void lr_sweep(double eps) {
         for (int k = 0; k + 1 < d; ++k) {
+            if (k > 0) stream_core(k - 1);  // final since the last iteration
             const int m = r[k] * n[k];
             const int b = r[k + 1];
             const long NR = (long)n[k + 1] * r[k + 2];
@@ -569,6 +593,8 @@ struct Rounder {
                 r[k + 1] = rp;
             }
         }
+        if (d >= 2) stream_core(d - 2);
+        stream_core(d - 1);
     }
 
     // one synchronization: the device wait flag (tensor-core and Jacobi
@@ -624,14 +650,19 @@ tt_tensor* finish_round(Rounder<T>& R, const tt_tensor* x, double nrm, double* e
 }
 
 template <class T>
-tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est) {
+tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est, void* const* host_out = nullptr) {
     ctx->stats.roundings++;
     if (x->d == 1) {
         if (err_est) *err_est = 0.0;
-        return copy_tensor(ctx, x);
+        tt_tensor* y = copy_tensor(ctx, x);
+        if (host_out)
+            TT_CUDA(cudaMemcpyAsync(host_out[0], y->cores[0], sizeof(T) * y->core_elems(0), cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+        return y;
     }
     for (int attempt = 0;; ++attempt) {
         Rounder<T> R(ctx, x);
+        R.host_out = host_out;
         if (attempt > 0) R.series = false;
         // skipped second passes (either sweep) leave cores orthonormal to
         // their ||E||_F; the norm and every truncation then see singular
@@ -687,11 +718,11 @@ size_t round_footprint(const tt_tensor* x, tt_precision prec) {
     return ws + out;
 }
 
-tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est) {
+tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est, void* const* host_out) {
     check_tensor(ctx, x);
     if (!(delta >= 0.0) || !isfinite(delta)) throw_status(TT_ERR_ARG, "delta must be finite and >= 0");
-    if (ctx->prec == TT_FP64) return round_t<double>(ctx, x, delta, err_est);
-    return round_t<float>(ctx, x, delta, err_est);
+    if (ctx->prec == TT_FP64) return round_t<double>(ctx, x, delta, err_est, host_out);
+    return round_t<float>(ctx, x, delta, err_est, host_out);
 }
 
 double norm_internal(tt_ctx* ctx, const tt_tensor* x) {
@@ -717,6 +748,25 @@ tt_status tt_round(tt_ctx* ctx, const tt_tensor* x, double delta, tt_tensor** ou
     if (!ctx || !out) throw_status(TT_ERR_ARG, "NULL argument");
     *out = nullptr;
     *out = round_internal(ctx, x, delta, err_est);
+    TT_API_END
+}
+
+tt_status tt_round_to_host(tt_ctx* ctx, const tt_tensor* x, double delta, tt_tensor** out, double* err_est,
+                           void* const* host_cores) {
+    TT_API_BEGIN
+    if (!ctx || !out || !host_cores) throw_status(TT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    check_tensor(ctx, x);
+    for (int k = 0; k < x->d; ++k)
+        if (!host_cores[k]) throw_status(TT_ERR_ARG, "NULL host core");
+    tt_tensor* y = round_internal(ctx, x, delta, err_est, host_cores);
+    try {
+        ctx->sync();  // the d = 1 copy runs on the context's stream
+    } catch (...) {
+        free_tensor(y);
+        throw;
+    }
+    *out = y;
     TT_API_END
 }
 

@@ -260,6 +260,9 @@ struct Ctx {
     bool series_force_retry = false;  // treat series passes as invalid (tests the retry)
     bool series_no_skip = false;      // run every second pass (tests the series pass itself)
 
+    cudaStream_t copy_stream = nullptr;  // device-to-host copies overlapping the
+                                         // left-to-right sweep (created on first use)
+
     // event profiling of launches (off by default)
     bool prof = false;
     int prof_nest = 0;            // open ProfScopes: only the outermost records
@@ -268,6 +271,7 @@ struct Ctx {
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> ev_pool;
 
+    cudaStream_t copies();  // copy_stream, created on first use
     void* alloc(size_t bytes);
     void release(void* p, size_t bytes);
     void sync();

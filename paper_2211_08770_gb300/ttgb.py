@@ -76,6 +76,7 @@ _SIGS = {
     "tt_dot_many": (_I, [_P, _P, _I, _PP, _PD]),
     "tt_norm": (_I, [_P, _P, _PD]),
     "tt_round": (_I, [_P, _P, _D, C.POINTER(_P), _PD]),
+    "tt_round_to_host": (_I, [_P, _P, _D, C.POINTER(_P), _PD, C.POINTER(_P)]),
     "tt_round_batched": (_I, [_P, _I, _PP, _PD, _PP]),
     "tt_ctx_set_concurrency": (_I, [_P, _I]),
     "tt_ctx_get_concurrency": (_I, [_P]),
@@ -343,6 +344,28 @@ def tt_round(ctx, x, delta):
     e = C.c_double()
     _check(lib().tt_round(ctx.handle, x.handle, float(delta), C.byref(h), C.byref(e)), "tt_round")
     return TT(ctx, h), e.value
+
+
+def tt_round_to_host(ctx, x, delta, out):
+    """tt_round that also copies the rounded cores into the host arrays
+    `out` (numpy, the context's storage dtype, each at least as large as x's
+    core; page-locked memory lets the copies overlap the sweep).  Returns
+    (TT, err_est, views of out with the rounded shapes)."""
+    want = np.float64 if ctx.precision == "fp64" else np.float32
+    d, n, r = x.shape()
+    for k in range(d):
+        if out[k].dtype != want or not out[k].flags["C_CONTIGUOUS"] or out[k].size < r[k] * n[k] * r[k + 1]:
+            raise ValueError("host buffer %d: C-contiguous %s with at least %d elements" %
+                             (k, np.dtype(want).name, r[k] * n[k] * r[k + 1]))
+    ptrs = (_P * d)(*[o.ctypes.data for o in out])
+    h = _P()
+    e = C.c_double()
+    _check(lib().tt_round_to_host(ctx.handle, x.handle, float(delta), C.byref(h), C.byref(e), ptrs),
+           "tt_round_to_host")
+    y = TT(ctx, h)
+    _, _, ry = y.shape()
+    views = [out[k].reshape(-1)[: ry[k] * n[k] * ry[k + 1]].reshape(ry[k], n[k], ry[k + 1]) for k in range(d)]
+    return y, e.value, views
 
 
 def tt_round_batched(ctx, xs, deltas):

@@ -64,3 +64,33 @@ def test_storage_entry_points_round_trip(ctxs, prec, pinned):
         assert np.array_equal(g, a.astype(np.float64))
     with pytest.raises(ValueError):
         T.tt_tensor_create_storage(c, [a.astype(np.float16) for a in x])
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "mixed_tf32"])
+def test_round_to_host_matches_round_and_download(ctxs, prec, pinned):
+    # the host copies made during the sweep equal the returned device result
+    import oracle as O
+    from ttinputs import coefficients, random_tts
+    c = ctxs[prec]
+    dt = np.float64 if prec == "fp64" else np.float32
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    xs = random_tts(31, 4, 6, 12, 5)
+    x = O.tt_add(list(coefficients(32, 4)), xs)
+    t = T.tt_tensor_create(c, x)
+    _, n, r = t.shape()
+    sizes = [r[k] * n[k] * r[k + 1] for k in range(len(n))]
+    if pinned:
+        out = [torch.full((m,), float("nan"), dtype=tdt, pin_memory=True).numpy() for m in sizes]
+    else:
+        out = [np.full(m, np.nan, dtype=dt) for m in sizes]
+    y, err, views = T.tt_round_to_host(c, t, 1e-6, out)
+    dev = y.download_storage([np.empty(m, dtype=dt) for m in sizes])
+    for v, w in zip(views, dev):
+        assert v.shape == w.shape and np.array_equal(v, w)
+    assert O.tt_diff_norm([v.astype(np.float64) for v in views], x) <= (1e-6 + (1e-12 if prec == "fp64" else 1e-6)) * O.tt_norm(x)
+    # d = 1 is a copy
+    one = T.tt_tensor_create(c, [np.ascontiguousarray(x[0][:, :, :1])])
+    y1, _, v1 = T.tt_round_to_host(c, one, 1e-6, [np.empty(n[0], dtype=dt) if not pinned else
+                                                   torch.empty(n[0], dtype=tdt, pin_memory=True).numpy()])
+    assert np.array_equal(v1[0].reshape(-1), x[0][:1, :, :1].reshape(-1).astype(dt))
