@@ -94,3 +94,25 @@ def test_round_to_host_matches_round_and_download(ctxs, prec, pinned):
     y1, _, v1 = T.tt_round_to_host(c, one, 1e-6, [np.empty(n[0], dtype=dt) if not pinned else
                                                    torch.empty(n[0], dtype=tdt, pin_memory=True).numpy()])
     assert np.array_equal(v1[0].reshape(-1), x[0][:1, :, :1].reshape(-1).astype(dt))
+
+
+def test_round_to_host_after_a_retried_rounding(monkeypatch):
+    # a rounding redone after its series passes are judged invalid (forced)
+    # still leaves the final result in the host buffers
+    import oracle as O
+    from ttinputs import coefficients, random_tts
+    monkeypatch.setenv("TTGB_SERIES_PASS", "retry")
+    c = T.Ctx(0, "mixed_tf32")
+    try:
+        x = O.tt_add(list(coefficients(34, 5)), random_tts(33, 5, 5, 16, 6))
+        t = T.tt_tensor_create(c, x)
+        _, n, r = t.shape()
+        sizes = [r[k] * n[k] * r[k + 1] for k in range(len(n))]
+        out = [torch.full((m,), float("nan"), dtype=torch.float32, pin_memory=True).numpy() for m in sizes]
+        y, _, views = T.tt_round_to_host(c, t, 1e-6, out)
+        assert c.stats()["series_retries"] == 1
+        dev = y.download_storage([np.empty(m, dtype=np.float32) for m in sizes])
+        for v, w in zip(views, dev):
+            assert np.array_equal(v, w)
+    finally:
+        c.close()
