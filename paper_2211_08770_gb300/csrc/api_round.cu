@@ -335,13 +335,14 @@ struct Rounder {
     // rigorous lower bound of sigma_min(L_0 ... L_{np-1}) from the factors and
     // their inverses: prod_i max(1/||T_i||_F, 1 - ||L_i - I||_F); 0 on drops;
     // times the bound of a series pass's factor
+    // (the series passes' bound is formed by orth itself, with its one read)
     double sigma_lb(int a, const Orth& o) {
         const int np = o.nchol;
         TT_CUDA(cudaMemsetAsync(dsc, 0, 2 * np * sizeof(double), c->stream));
         for (int i = 0; i < np; ++i) inv_and_identity_defect<T>(*c, a, Lf[i], Ti[i], dsc + 2 * i);
-        std::vector<double> h(13);
+        std::vector<double> h(2 * np);
         std::vector<CholStatus> hs(nst);
-        TT_CUDA(cudaMemcpyAsync(h.data(), dsc, 13 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        TT_CUDA(cudaMemcpyAsync(h.data(), dsc, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         TT_CUDA(cudaMemcpyAsync(hs.data(), st, nst * sizeof(CholStatus), cudaMemcpyDeviceToHost, c->stream));
         c->sync();
         for (int i = nst - np; i < nst; ++i) {
@@ -349,16 +350,6 @@ struct Rounder {
             if (hs[i].ndrop) return 0.0;
         }
         double lb = 1.0;
-        if (o.series) {
-            // sigma_min((I + E)^(1/2)) >= sqrt(1 - ||E||_2); less the series
-            // remainder and the rounding of the stored factor.  An invalid
-            // series pass gives no bound (the rounding is redone anyway).
-            // The same bound holds for Q1 itself (sigma(Q1) in
-            // [sqrt(1 - e), sqrt(1 + e)]) when the pass is not completed.
-            const double e = sqrt(h[12]);
-            if (!series_valid(e)) return 0.0;
-            lb = std::max(0.0, sqrt(1.0 - e) - (2.0 + sqrt((double)a)) * ug_fb);
-        }
         for (int i = 0; i < np; ++i) {
             double b1 = h[2 * i] > 0 ? 1.0 / sqrt(h[2 * i]) : 0.0;
             double b2 = 1.0 - sqrt(h[2 * i + 1]);
