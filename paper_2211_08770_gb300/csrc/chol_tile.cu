@@ -13,8 +13,10 @@
 //    factoring the next diagonal tile first (lookahead), so the serial chain
 //    of diagonal factorizations overlaps the bulk of the flops; finished
 //    block columns of L are stored while the next ones are computed;
-//  - in-place inversion by doubling: merge inverted neighbours with
-//    T21 = -T22 (L21 T11), one output tile per warp.
+//  - the inverse by block rows in place of the stored rows of L, interleaved
+//    with the panels: row p is T_pJ = -T_pp sum_K L_pK T_KJ, formed by the
+//    warps the trailing update leaves idle, so only the last row's chain of
+//    tile products follows the factorization.
 // (Solving the panel by forward substitution instead, with the diagonal
 // inverses formed later in parallel, measured slower: the substitution's
 // dependent chain per row outweighs the shorter diagonal step.)
@@ -146,6 +148,40 @@ __device__ __forceinline__ void tile_fma<float>(float (&acc)[32], const float (&
     }
 }
 
+// columns [16 h, 16 h + 16) of the product only: acc[c] += sum_k a[k] B(k, 16 h + c)
+// (two warps share one output tile; the same per-element rounding as tile_fma)
+template <class C>
+__device__ __forceinline__ void tile_fma_half(C (&acc)[16], const C (&a)[32], const C* B, int h) {
+    using TT = TileT<C>;
+    constexpr int HC = TT::NCH / 2;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const typename TT::V* row = reinterpret_cast<const typename TT::V*>(B + k * 32);
+#pragma unroll
+        for (int j = 0; j < HC; ++j) TT::fma(a[k], row[(h * HC + j) ^ (k & (TT::NCH - 1))], acc + j * TT::W);
+    }
+}
+template <>
+__device__ __forceinline__ void tile_fma_half<float>(float (&acc)[16], const float (&a)[32], const float* B, int h) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const float4* row = reinterpret_cast<const float4*>(B + k * 32);
+        unsigned long long ap;
+        asm("mov.b64 %0, {%1, %1};" : "=l"(ap) : "f"(a[k]));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 v = row[(4 * h + j) ^ (k & 7)];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                unsigned long long cc, bp;
+                asm("mov.b64 %0, {%1, %2};" : "=l"(cc) : "f"(acc[4 * j + 2 * e]), "f"(acc[4 * j + 2 * e + 1]));
+                asm("mov.b64 %0, {%1, %2};" : "=l"(bp) : "f"(e ? v.z : v.x), "f"(e ? v.w : v.y));
+                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(cc) : "l"(ap), "l"(bp));
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[4 * j + 2 * e]), "=f"(acc[4 * j + 2 * e + 1]) : "l"(cc));
+            }
+        }
+    }
+}
 __device__ __forceinline__ int tri(int I, int J) { return I * (I + 1) / 2 + J; }  // slot of lower tile (I, J)
 
 struct FactorState {
@@ -240,40 +276,32 @@ __device__ __noinline__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, C* 
     __syncwarp();
 }
 
-// the n x n block from the lower tiles (zeros above the diagonal), one
-// 16-byte chunk per item
-template <class S, class C, int NT>
-__device__ void store_lower(int n, int P, const C* Lt, S* out, long ld) {
+// row r of tile (I, J) of an n x n matrix from a lane's registers, columns
+// [16 h0, 16 h0 + 16 NH) (x holds them from x[0]), clipped to n
+template <class S, class C, int NH>
+__device__ __forceinline__ void gstore_row(S* out, long ld, int n, int I, int J, int r, const C* x, int h0) {
+    const int gi = I * 32 + r, gj0 = J * 32 + 16 * h0;
+    if (gi >= n) return;
+    S* o = out + (long)gi * ld + gj0;
     using TT = TileT<C>;
-    const bool vec = ((ld % TT::W) == 0) && ((((uintptr_t)out) & 15) == 0);
-    const int nitem = P * P * 32 * TT::NCH;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < nitem; e += NT) {
-        const int tile = e / (32 * TT::NCH), r = (e / TT::NCH) & 31, ch = e % TT::NCH;
-        const int I = tile / P, J = tile % P;
-        const int gi = I * 32 + r, gj0 = J * 32 + ch * TT::W;
-        if (gi >= n || gj0 >= n) continue;
-        C v[TT::W];
-        if (I >= J) {
-            TT::unpack(*reinterpret_cast<const typename TT::V*>(Lt + (long)tri(I, J) * 1024 + r * 32 +
-                                                                  ((ch ^ (r & (TT::NCH - 1))) * TT::W)),
-                       v);
-            if (I == J) {
+    if (sizeof(S) == sizeof(C) && gj0 + 16 * NH <= n && ((ld % TT::W) == 0) && ((((uintptr_t)o) & 15) == 0)) {
 #pragma unroll
-                for (int w = 0; w < TT::W; ++w)
-                    if (ch * TT::W + w > r) v[w] = C(0);
-            }
-        } else {
+        for (int j = 0; j < 16 * NH / TT::W; ++j)
+            *reinterpret_cast<typename TT::V*>(o + j * TT::W) = TT::pack(x + j * TT::W);
+    } else {
 #pragma unroll
-            for (int w = 0; w < TT::W; ++w) v[w] = C(0);
-        }
-        if (vec && gj0 + TT::W <= n) {
-            *reinterpret_cast<typename TT::V*>(out + (long)gi * ld + gj0) = TT::pack(v);
-        } else {
-#pragma unroll
-            for (int w = 0; w < TT::W; ++w)
-                if (gj0 + w < n) out[(long)gi * ld + gj0 + w] = (S)v[w];
-        }
+        for (int c = 0; c < 16 * NH; ++c)
+            if (gj0 + c < n) o[c] = (S)x[c];
+    }
+}
+
+// zeros of the n x n lower-triangular inverse above its diagonal tiles (the
+// diagonal tiles are stored whole), one warp per row, by warps [w0, w0 + nw)
+template <class S>
+__device__ void zero_upper(int n, S* out, long ld, int w, int nw, int lane) {
+    for (int gi = w; gi < n; gi += nw) {
+        S* o = out + (long)gi * ld;
+        for (int gj = (gi / 32 + 1) * 32 + lane; gj < n; gj += 32) o[gj] = S(0);
     }
 }
 
@@ -333,6 +361,32 @@ struct TileArgs {
     const double* ext;
     CholStatus* st;
 };
+
+// T_pJ = sum_{K=J}^{p-1} M_pK T_KJ for J < p: M_pK = -T_pp L_pK in tile
+// slot (p, K), T_KJ in slot (K, J), T_JJ in TD; one warp, lane r's row r in
+// acc (a block row of the forward substitution L T = I)
+template <class C>
+__device__ __forceinline__ void inv_row_tile(C (&acc)[32], int p, int J, const C* Lt, const C* TD, int lane) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = C(0);
+    for (int K = J; K < p; ++K) {
+        C x[32];
+        load_row<C>(x, Lt + (long)tri(p, K) * 1024, lane);
+        tile_fma<C>(acc, x, K == J ? TD + (long)J * 1024 : Lt + (long)tri(K, J) * 1024);
+    }
+}
+
+// columns [16 h, 16 h + 16) of the same tile
+template <class C>
+__device__ __forceinline__ void inv_row_half(C (&acc)[16], int p, int J, int h, const C* Lt, const C* TD, int lane) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = C(0);
+    for (int K = J; K < p; ++K) {
+        C x[32];
+        load_row<C>(x, Lt + (long)tri(p, K) * 1024, lane);
+        tile_fma_half<C>(acc, x, K == J ? TD + (long)J * 1024 : Lt + (long)tri(K, J) * 1024, h);
+    }
+}
 
 __device__ __forceinline__ void atomic_min_nonneg(double* addr, double v) {
     // non-negative doubles order like their bit patterns
@@ -438,11 +492,40 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
     __syncthreads();
 
     FactorState fs{0, 0, 1e300};
-    // ---- Cholesky, right-looking by panels, diagonal factor one panel ahead
+    // ---- Cholesky, right-looking by panels, diagonal factor one panel ahead,
+    // and the inverse T = L^{-1} one block row per panel, in place of the
+    // rows of L that are final and stored: row p from
+    //   M_pK = -T_pp L_pK  (K < p, over L_pK, during the panel solve), then
+    //   T_pJ = sum_{K=J}^{p-1} M_pK T_KJ  (J < p, during the trailing update),
+    // the tile T_pJ by one warp, held in registers across the barrier that
+    // ends the panel and stored at the start of the next one (the in-place
+    // reads of row p are complete by then).  The serial chain left after the
+    // last panel is P - 1 half-tile products.
+    // worker warps: those that do not share warp 0's scheduler (warp mod 4
+    // != 0), so that the serial chain of diagonal factorizations issues
+    // without contention while the workers update the trailing matrix
+    constexpr int NWK = NW - NW / 4;
+    static_assert(TileT<C>::PMAX - 1 <= NWK, "one inverse tile per worker and a worker for the trailing update");
+    C held[32];
+    int held_slot = -1, held_J = 0;
+    // T leaves the CTA as its tiles become final: the zeros above the
+    // diagonal tiles now, T_pp and the tiles of row p - 1 at the start of
+    // panel p, the last row at the end
     if (warp == 0) factor_diag<C>(n, 0, Lt, DiT, TD, colbuf, od, tau, &fs);
+    else zero_upper<S>(n, A.T, A.ldt, warp - 1, NW - 1, lane);
     __syncthreads();
     for (int p = 0; p < P; ++p) {
         const int R = P - 1 - p;
+        if (held_slot >= 0) {
+            store_row<C>(Lt + (long)held_slot * 1024, lane, held);
+            gstore_row<S, C, 2>(A.T, A.ldt, n, p - 1, held_J, lane, held, 0);
+            held_slot = -1;
+        }
+        if (warp == R) {  // T_pp (a warp the panel solve and M_pK leave free)
+            C x[32];
+            load_row<C>(x, TD + (long)p * 1024, lane);
+            gstore_row<S, C, 2>(A.T, A.ldt, n, p, p, lane, x, 0);
+        }
         // panel solve: L_Ip = A_Ip T_pp^T, natural copy in place and transposed copy in PT
         for (int I = p + 1 + warp; I < P; I += NW) {
             C* tile = Lt + (long)tri(I, p) * 1024;
@@ -454,11 +537,31 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
             store_row<C>(tile, lane, acc);
             store_col<C>(PT + (long)(I - p - 1) * 1024, lane, acc);
         }
+        // M_pK = -T_pp L_pK, in place (the warps from the top)
+        {
+            const int K = NW - 1 - warp;
+            if (K < p) {
+                C* tile = Lt + (long)tri(p, K) * 1024;
+                C a[32], acc[32];
+                load_row<C>(a, TD + (long)p * 1024, lane);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) a[k] = -a[k];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[j] = C(0);
+                tile_fma<C>(acc, a, tile);
+                __syncwarp();
+                store_row<C>(tile, lane, acc);
+            }
+        }
         __syncthreads();
         if (R == 0) break;
-        // trailing update A_IK -= L_Ip L_Kp^T for p < K <= I; warp 0 first
-        // takes (p+1, p+1) and factors it, the other warps the rest
+        // trailing update A_IK -= L_Ip L_Kp^T for p < K <= I: warp 0 first
+        // takes (p+1, p+1) and factors it; the workers take the trailing
+        // tiles (workers 0 .. NWK-1-p) and row p of T (tile J by worker
+        // NWK-1-J)
         const int ntask = R * (R + 1) / 2;
+        const int wk = (warp & 3) ? warp - (warp >> 2) - 1 : -1;
+        const int ntw = NWK - p;
         if (warp == 0) {
             C* tile = Lt + (long)tri(p + 1, p + 1) * 1024;
             C a[32], acc[32];
@@ -470,84 +573,51 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
             store_row<C>(tile, lane, acc);
             __syncwarp();
             factor_diag<C>(n, p + 1, Lt, DiT, TD, colbuf, od, tau, &fs);
-        }
-        // tasks 1..ntask-1 in (I, K) order over I = p+1.., K = p+1..I; task 0 is (p+1, p+1)
-        for (int t = 1 + (NW > 1 ? warp - 1 : 0); t < ntask; t += (NW > 1 ? NW - 1 : 1)) {
-            if (NW > 1 && warp == 0) break;
-            int ii = 0;
-            while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-            const int kk = t - ii * (ii + 1) / 2;
-            const int I = p + 1 + ii, K = p + 1 + kk;
-            C* tile = Lt + (long)tri(I, K) * 1024;
-            C a[32], acc[32];
-            load_row<C>(acc, tile, lane);
-            load_row<C>(a, Lt + (long)tri(I, p) * 1024, lane);
+        } else if (wk >= 0 && wk < ntw) {
+            // tasks 1..ntask-1 in (I, K) order over I = p+1.., K = p+1..I; task 0 is (p+1, p+1)
+            for (int t = wk + 1; t < ntask; t += ntw) {
+                int ii = 0;
+                while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+                const int kk = t - ii * (ii + 1) / 2;
+                const int I = p + 1 + ii, K = p + 1 + kk;
+                C* tile = Lt + (long)tri(I, K) * 1024;
+                C a[32], acc[32];
+                load_row<C>(acc, tile, lane);
+                load_row<C>(a, Lt + (long)tri(I, p) * 1024, lane);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) a[k] = -a[k];
-            tile_fma<C>(acc, a, PT + (long)(K - p - 1) * 1024);
-            store_row<C>(tile, lane, acc);
+                for (int k = 0; k < 32; ++k) a[k] = -a[k];
+                tile_fma<C>(acc, a, PT + (long)(K - p - 1) * 1024);
+                store_row<C>(tile, lane, acc);
+            }
+        } else if (wk >= 0) {
+            const int J = NWK - 1 - wk;
+            if (J < p) {
+                inv_row_tile<C>(held, p, J, Lt, TD, lane);
+                held_slot = tri(p, J);
+                held_J = J;
+            }
         }
-        // block column p of L is final: the warps other than 0 store it
-        // while warp 0 factors the next diagonal tile
-        if (NW == 1 || warp > 0) store_lcol<S, C>(n, P, p, Lt, A.L, A.ldl, NW > 1 ? tid - 32 : tid, NW > 1 ? NT - 32 : NT);
+        // block column p of L is final: the workers store it while warp 0
+        // factors the next diagonal tile
+        if (wk >= 0) store_lcol<S, C>(n, P, p, Lt, A.L, A.ldl, wk * 32 + lane, NWK * 32);
         __syncthreads();
     }
-    // the last block column of L
-    store_lcol<S, C>(n, P, P - 1, Lt, A.L, A.ldl, tid, NT);
-    __syncthreads();
-
-    // ---- in-place inversion by doubling: the diagonal tiles hold T_JJ, then
-    // level s merges inverted neighbours [a, a+s) and [a+s, b) with
-    //   U = L21 T11 (over L21), then T21 = -T22 U (over U),
-    // every output tile one warp, held in registers across the barrier
-    // that precedes its store (so the in-place reads are complete).  The
-    // serial depth is 2 (P - 1) tile products instead of P (P + 1) / 2.
-    static_assert(TileT<C>::PMAX * TileT<C>::PMAX <= 4 * NW, "one inversion task per warp");
-    for (int e = tid; e < P * 1024; e += NT) Lt[(long)tri(e >> 10, e >> 10) * 1024 + (e & 1023)] = TD[e];
-    __syncthreads();
-    for (int sz = 1; sz < P; sz *= 2) {
-        // this warp's task (merge start a, output tile I, J), if any
-        int a0 = -1, I = 0, J = 0;
-        {
-            int t = warp;
-            for (int a = 0; a + sz < P; a += 2 * sz) {
-                const int sr = min(sz, P - a - sz);
-                if (t < sr * sz) {
-                    a0 = a;
-                    I = a + sz + t / sz;
-                    J = a + t % sz;
-                    break;
-                }
-                t -= sr * sz;
-            }
-        }
-        for (int phase = 0; phase < 2; ++phase) {
-            C acc[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] = C(0);
-            if (a0 >= 0) {
-                // phase 0: U_IJ = sum_{K=J}^{a0+sz-1} L_IK T_KJ
-                // phase 1: T_IJ = -sum_{K=a0+sz}^{I} T_IK U_KJ
-                const int k0 = phase == 0 ? J : a0 + sz;
-                const int k1 = phase == 0 ? a0 + sz - 1 : I;
-                for (int K = k0; K <= k1; ++K) {
-                    C x[32];
-                    load_row<C>(x, Lt + (long)tri(I, K) * 1024, lane);
-                    if (phase == 1) {
-#pragma unroll
-                        for (int k = 0; k < 32; ++k) x[k] = -x[k];
-                    }
-                    tile_fma<C>(acc, x, Lt + (long)tri(K, J) * 1024);
-                }
-            }
-            __syncthreads();
-            if (a0 >= 0) store_row<C>(Lt + (long)tri(I, J) * 1024, lane, acc);
-            __syncthreads();
+    // the last block row of T, straight to global memory, and the last block
+    // column of L; with warps to spare, tile J by warps 2J and 2J+1, a half
+    // of its columns each
+    constexpr bool HALF = 2 * (TileT<C>::PMAX - 1) <= NW;
+    C lrow[HALF ? 16 : 32];
+    const int Jl = HALF ? warp >> 1 : warp, hl = HALF ? warp & 1 : 0;
+    if (Jl < P - 1) {
+        if constexpr (HALF) {
+            inv_row_half<C>(lrow, P - 1, Jl, hl, Lt, TD, lane);
+            gstore_row<S, C, 1>(A.T, A.ldt, n, P - 1, Jl, lane, lrow, hl);
+        } else {
+            inv_row_tile<C>(lrow, P - 1, Jl, Lt, TD, lane);
+            gstore_row<S, C, 2>(A.T, A.ldt, n, P - 1, Jl, lane, lrow, 0);
         }
     }
-
-    // ---- T out
-    store_lower<S, C, NT>(n, P, Lt, A.T, A.ldt);
+    store_lcol<S, C>(n, P, P - 1, Lt, A.L, A.ldl, tid, NT);
     if (tid == 0) {
         if (A.ext) {
             if (fs.ndrop) atomicAdd(&A.st->ndrop, fs.ndrop);
