@@ -758,18 +758,18 @@ void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, do
 
 // Block size per precision and order (the one-CTA kernel when it fits).
 // Measured on a GB300 (microseconds, every candidate NB), fastest kept:
-//   FP32: one CTA up to 256 (n = 256: 137); n = 288-320: NB 160 (161, 179);
-//   n = 352-400: NB 224 (203, 239); n = 448-512: NB 192 (274, 300);
-//   n = 640-800: NB 160 (389, 508).
-//   FP64: one CTA up to 160 (n = 160: 1069); above, NB 64 (n = 256: 1466,
-//   400: 2505, 800: 5799).
+//   FP32: one CTA up to 256 (n = 256: 117); n = 288-320: NB 160 (145, 157);
+//   n = 352-448: NB 224 (179, 206, 226); n = 512: NB 256 (270);
+//   n = 640-800: NB 224 (339, 459).
+//   FP64: one CTA up to 160; above, NB 128 (n = 256: 1334, 400: 2322,
+//   512: 2920, 800: 5058; NB 64 was 4-10% slower).
 int default_nb(int es, int n, int nmax) {
     if (n <= nmax) return n;
-    if (es == 8) return 64;
+    if (es == 8) return 128;
     if (n <= 320) return 160;
-    if (n <= 416) return 224;
-    if (n <= 544) return 192;
-    return 160;
+    if (n <= 480) return 224;
+    if (n <= 544) return 256;
+    return 224;
 }
 
 }  // namespace
