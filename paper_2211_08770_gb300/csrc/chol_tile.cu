@@ -184,13 +184,10 @@ __device__ __forceinline__ void tile_fma_half<float>(float (&acc)[16], const flo
 }
 __device__ __forceinline__ int tri(int I, int J) { return I * (I + 1) / 2 + J; }  // slot of lower tile (I, J)
 
-struct FactorState {
-    int ndrop, nonfin;
-    double minratio;
-};
-
 // Warp 0: factor the diagonal tile q in place (rank drop below tau), write
-// the transposed inverse to DiT and the inverse to TD (natural layout).
+// the transposed inverse to DiT and the inverse to TD (natural layout), and
+// the pivots to pivs[32 q ..] (the status is formed from them once, at the
+// end of the kernel: its FP64 ratios and reductions stay off this chain).
 // Lane r holds row r in registers.  Step c: the pivot comes from lane c,
 // column c is scaled, published in col[] and subtracted from the rows below
 // (16-byte broadcast reads of col; entries above the diagonal are zeroed at
@@ -198,8 +195,7 @@ struct FactorState {
 // slower).  Kept out of line: inlined into the kernel, the compiler
 // schedules this dependent chain several times slower.
 template <class C>
-__device__ __noinline__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, C* col, const double* od, double tau,
-                                         FactorState* fs) {
+__device__ __noinline__ void factor_diag(int q, C* Lt, C* DiT, C* TD, C* col, C* pivs, double tau) {
     using TT = TileT<C>;
     const int lane = threadIdx.x & 31;
     C* tile = Lt + (long)tri(q, q) * 1024;
@@ -207,8 +203,7 @@ __device__ __noinline__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, C* 
     load_row<C>(a, tile, lane);
     C invs[32];
     const C tau_c = (C)tau;
-    C mypiv = C(0);      // lane c keeps pivot c: the status is formed after
-    bool mykeep = true;  // the loop, off the pivot chain
+    C mypiv = C(0);  // lane c keeps pivot c
     // next pivot, updated by lane c+1 from its own multiplier: the same FMA
     // the column broadcast below applies to it, formed before the broadcast
     // so the pivot chain (shuffle, rsqrt, multiply) skips the shared-memory
@@ -222,10 +217,7 @@ __device__ __noinline__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, C* 
         // pivot chain in FP32 (2 ulp; Cholesky's backward error is O(n u))
         const C inv = keep ? TT::rsqrt(piv) : C(0);
         invs[c] = inv;
-        if (lane == c) {
-            mypiv = piv;
-            mykeep = keep;
-        }
+        if (lane == c) mypiv = piv;
         const C l = (lane > c) ? a[c] * inv : C(0);
         if (c + 1 < 32) pnext = fma(-l, l, a[c + 1]);
         a[c] = (lane == c) ? piv * inv : l;
@@ -243,23 +235,11 @@ __device__ __noinline__ void factor_diag(int n, int q, C* Lt, C* DiT, C* TD, C* 
         __syncwarp();
     }
     store_row<C>(tile, lane, a);
-    {
-        const int j = q * 32 + lane;
-        const bool valid = j < n;
-        const unsigned nonfin = __ballot_sync(FULL, valid && !isfinite(mypiv));
-        const unsigned drop = __ballot_sync(FULL, valid && !mykeep);
-        double ratio = (valid && mykeep) ? (od[j] > 0.0 ? (double)mypiv / od[j] : 0.0) : 1e300;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ratio = fmin(ratio, __shfl_xor_sync(FULL, ratio, o));
-        if (lane == 0) {
-            if (nonfin) fs->nonfin = 1;
-            fs->ndrop += __popc(drop);
-            fs->minratio = fmin(fs->minratio, ratio);
-        }
-    }
+    pivs[q * 32 + lane] = mypiv;
     __syncwarp();
     // inverse: lane c solves column c, x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii,
     // L_ik read back from the tile by broadcast loads, two partial sums
+    // (loading row i in 16-byte chunks instead measured 3-4x slower)
     C x[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
@@ -400,6 +380,7 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
     __shared__ double od[TileT<C>::PMAX * 32];
     __shared__ double red[2 * NW];
     __shared__ __align__(16) C colbuf[32];
+    __shared__ C pivs[TileT<C>::PMAX * 32];
     const int n = A.n;
     const int P = (n + 31) / 32;
     const int ntile = P * (P + 1) / 2;
@@ -491,7 +472,6 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
     }
     __syncthreads();
 
-    FactorState fs{0, 0, 1e300};
     // ---- Cholesky, right-looking by panels, diagonal factor one panel ahead,
     // and the inverse T = L^{-1} one block row per panel, in place of the
     // rows of L that are final and stored: row p from
@@ -511,7 +491,7 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
     // T leaves the CTA as its tiles become final: the zeros above the
     // diagonal tiles now, T_pp and the tiles of row p - 1 at the start of
     // panel p, the last row at the end
-    if (warp == 0) factor_diag<C>(n, 0, Lt, DiT, TD, colbuf, od, tau, &fs);
+    if (warp == 0) factor_diag<C>(0, Lt, DiT, TD, colbuf, pivs, tau);
     else zero_upper<S>(n, A.T, A.ldt, warp - 1, NW - 1, lane);
     __syncthreads();
     for (int p = 0; p < P; ++p) {
@@ -572,7 +552,7 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
             tile_fma<C>(acc, a, PT);
             store_row<C>(tile, lane, acc);
             __syncwarp();
-            factor_diag<C>(n, p + 1, Lt, DiT, TD, colbuf, od, tau, &fs);
+            factor_diag<C>(p + 1, Lt, DiT, TD, colbuf, pivs, tau);
         } else if (wk >= 0 && wk < ntw) {
             // tasks 1..ntask-1 in (I, K) order over I = p+1.., K = p+1..I; task 0 is (p+1, p+1)
             for (int t = wk + 1; t < ntask; t += ntw) {
@@ -618,17 +598,38 @@ __global__ void __launch_bounds__(NT) chol_tile_kernel(TileArgs<S> A) {
         }
     }
     store_lcol<S, C>(n, P, P - 1, Lt, A.L, A.ldl, tid, NT);
-    if (tid == 0) {
-        if (A.ext) {
-            if (fs.ndrop) atomicAdd(&A.st->ndrop, fs.ndrop);
-            if (fs.nonfin) atomicOr(&A.st->nonfinite, 1);
-            atomic_min_nonneg(&A.st->min_ratio, fs.minratio);
-        } else {
-            A.st->ndrop = fs.ndrop;
-            A.st->nonfinite = fs.nonfin;
-            A.st->min_ratio = fs.minratio > 1e299 ? 0.0 : fs.minratio;
-            A.st->trace = tr;
-            A.st->max_diag = mx;
+    // status from the pivots (warp 0 wrote them): dropped (not finite, not
+    // above tau, not positive) and non-finite counts, and the smallest
+    // ratio of a kept pivot to its original diagonal entry
+    if (warp == 0) {
+        const C tau_c = (C)tau;
+        int ndrop = 0, nonfin = 0;
+        double minratio = 1e300;
+        for (int j = lane; j < n; j += 32) {
+            const C pv = pivs[j];
+            const bool keep = isfinite(pv) && pv > tau_c && pv > C(0);
+            nonfin |= !isfinite(pv);
+            ndrop += !keep;
+            if (keep) minratio = fmin(minratio, od[j] > 0.0 ? (double)pv / od[j] : 0.0);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ndrop += __shfl_xor_sync(FULL, ndrop, o);
+            nonfin |= __shfl_xor_sync(FULL, nonfin, o);
+            minratio = fmin(minratio, __shfl_xor_sync(FULL, minratio, o));
+        }
+        if (lane == 0) {
+            if (A.ext) {
+                if (ndrop) atomicAdd(&A.st->ndrop, ndrop);
+                if (nonfin) atomicOr(&A.st->nonfinite, 1);
+                atomic_min_nonneg(&A.st->min_ratio, minratio);
+            } else {
+                A.st->ndrop = ndrop;
+                A.st->nonfinite = nonfin;
+                A.st->min_ratio = minratio > 1e299 ? 0.0 : minratio;
+                A.st->trace = tr;
+                A.st->max_diag = mx;
+            }
         }
     }
 }
