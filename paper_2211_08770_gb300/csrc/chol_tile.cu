@@ -4,8 +4,9 @@
 // orthogonalization step).
 //
 // Order n <= 256 (FP32) or 160 (FP64): one CTA holds the whole lower
-// triangle in shared memory as 32 x 32 tiles and never touches global memory
-// between loading G and storing L and T, so no step waits on L2 latency:
+// triangle in shared memory as 32 x 32 tiles and reads global memory only to
+// load G (L and T leave by plain stores as their tiles become final), so no
+// step waits on L2 latency:
 //  - right-looking Cholesky by 32-column panels: warp 0 factors and inverts
 //    the diagonal tile in registers (one out-of-line, unrolled function);
 //    the tiles below are multiplied by the transposed tile inverse; the
@@ -16,7 +17,9 @@
 //  - the inverse by block rows in place of the stored rows of L, interleaved
 //    with the panels: row p is T_pJ = -T_pp sum_K L_pK T_KJ, formed by the
 //    warps the trailing update leaves idle, so only the last row's chain of
-//    tile products follows the factorization.
+//    tile products follows the factorization;
+//  - the status (dropped pivots, non-finite pivots, smallest pivot ratio) is
+//    formed once at the end from the stored pivots, off the diagonal chain.
 // (Solving the panel by forward substitution instead, with the diagonal
 // inverses formed later in parallel, measured slower: the substitution's
 // dependent chain per row outweighs the shorter diagonal step.)
