@@ -180,6 +180,44 @@ def test_tt_loo_orders_in_delta():
     assert loo["cgs"] > loo["mgs2"] and loo["gram"] > loo["mgs2"]
 
 
+def _conditioned_tt_family(kappa, m=8, n=8, d=3, seed=5):
+    # a_i = sum_j M_ji b_j with b_j orthonormal rank-1 TTs (orthonormal factor
+    # columns, distinct in the first mode) and M with singular values
+    # logspaced from 1 to 1/kappa: the dense matrix [a_1 .. a_m] has
+    # condition number kappa exactly
+    rng = np.random.default_rng(seed)
+    Us = [np.linalg.qr(rng.standard_normal((n, n)))[0] for _ in range(d)]
+    perms = [np.arange(m)] + [rng.permutation(m) for _ in range(d - 1)]
+    B = [[Us[k][:, perms[k][j]].reshape(1, n, 1) for k in range(d)] for j in range(m)]
+    V = np.linalg.qr(rng.standard_normal((m, m)))[0]
+    W = np.linalg.qr(rng.standard_normal((m, m)))[0]
+    M = (V * np.logspace(0, -np.log10(kappa), m)) @ W.T
+    return [O.tt_add(list(M[:, i]), B) for i in range(m)]
+
+
+def test_tt_loo_orders_in_kappa():
+    # Section 3.4 in TT format with delta far below the round-off effects: the
+    # schemes keep their matrix orders in kappa (CGS and Gram ~ u kappa^2,
+    # MGS ~ u kappa, CGS2 / MGS2 ~ u; Householder ~ delta).  Growth from
+    # kappa = 1e2 to 1e4 is checked, not constants.
+    u = 2.0 ** -53
+    delta = 1e-10
+    loo = {}
+    for kappa in (1e2, 1e4):
+        A = _conditioned_tt_family(kappa)
+        Ad = np.column_stack([O.tt_full(a).ravel() for a in A])
+        assert np.linalg.cond(Ad) == pytest.approx(kappa, rel=1e-6)
+        loo[kappa] = {s: O.loss_of_orthogonality(O.orthogonalize(s, A, delta)[0]) for s in O.SCHEMES}
+    lo, hi = loo[1e2], loo[1e4]
+    for s in ("cgs2", "mgs2"):
+        assert lo[s] < 1e2 * u and hi[s] < 1e2 * u, (s, lo[s], hi[s])
+    assert lo["householder"] < 1e2 * delta and hi["householder"] < 1e2 * delta
+    assert 1e1 < hi["mgs"] / lo["mgs"] < 1e3                     # ~ kappa: x 1e2
+    assert hi["cgs"] / lo["cgs"] > 1e3 and hi["gram"] / lo["gram"] > 1e3  # ~ kappa^2: x 1e4
+    assert hi["cgs"] > 1e2 * hi["mgs"]
+    assert 1e-2 * u * 1e4 < hi["mgs"] < 1e2 * u * 1e4
+
+
 @pytest.mark.parametrize("scheme", ["cgs", "mgs", "cgs2", "mgs2"])
 @pytest.mark.parametrize("policy", ["paper", "every_update"])
 def test_gs_step_iterated_is_the_scheme(scheme, policy):
