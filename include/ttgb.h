@@ -52,12 +52,17 @@ typedef enum {
 
 /* Arithmetic of a context.
  * TT_FP64:       cores, GEMMs, Cholesky, SVD and norms in FP64.
- * TT_MIXED_TF32: cores stored in FP32; Gram matrices of the CholQR passes on
- *                tcgen05 tensor cores in TF32 with FP32 accumulation; the
- *                GEMMs that produce core values (apply / absorb) in split
- *                TF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation); small r x r
- *                factorizations in FP32; norm, thresholds, tail sums and the
- *                truncation SVD in FP64.
+ * TT_MIXED_TF32: cores stored in FP32; the first pass's Gram matrix of every
+ *                Cholesky QR (and the second pass's for unfoldings of length
+ *                >= 4096) on tcgen05 tensor cores in TF32 with FP32
+ *                accumulation; the GEMMs that produce core values (apply
+ *                Q = L^{-1} X, absorb core L) on CUDA cores in FP32 by
+ *                default (the split-TF32 tensor-core GEMM of tt_gemm_f32 is
+ *                opt-in: environment variable TTGB_TC_GEMM=3 or 2 when the
+ *                context is created); small r x r factorizations in FP32;
+ *                norm, thresholds and tail sums in FP64; truncation SVDs in
+ *                FP64 (FP32 column Jacobi with an FP64-measured residual
+ *                guard for ranks >= 96).
  * TT_FP32:       cores and every GEMM in FP32 on CUDA cores (no tensor
  *                cores); small factorizations as TT_MIXED_TF32. */
 typedef enum { TT_FP64 = 0, TT_MIXED_TF32 = 1, TT_FP32 = 2 } tt_precision;
@@ -236,7 +241,7 @@ tt_status tt_round_to_host(tt_ctx* ctx, const tt_tensor* x, double delta, tt_ten
                            double* err_est, void* const* host_cores);
 
 /* Rounds count independent tensors, each at its own delta[i] (TT-round of
- * Section 2.3 applied to every x[i]; the paper has no batched form).  The
+ * Section 2 applied to every x[i]; the paper has no batched form).  The
  * roundings run concurrently on the context's lanes (tt_ctx_set_concurrency):
  * child contexts with their own non-blocking streams, each driven by one
  * host thread (the calling thread drives lane 0), taking instances in
@@ -322,10 +327,10 @@ tt_status tt_set_sign_rule(tt_ctx* ctx, tt_sign_rule rule);
 /* ---- allocation-free variant ------------------------------------------- */
 
 /* <x, y> in FP64 without allocating any device memory, for callers that
- * cannot call cudaMalloc: code that runs while a CUDA graph is being
- * captured, hosts whose device memory is all handed to their own pool, or
- * latency-critical loops that must avoid cudaMalloc's implicit
- * synchronization.  The paper has no counterpart; this is the contraction of
+ * cannot call cudaMalloc: hosts that hand all device memory to their own
+ * pool up front (so a library allocation would fail or break their
+ * accounting), and latency-critical loops that must not pay cudaMalloc's
+ * implicit device synchronization.  The paper has no counterpart; this is the contraction of
  * tt_dot (W_k = sum_i X_k(i)^T W_{k-1} Y_k(i)) with its work arrays in a
  * static device array of 2^20 doubles (8 MiB) that every GPU loading the
  * library holds until the process exits.
@@ -351,7 +356,7 @@ tt_status tt_dot_f64_noalloc(void* cuda_stream, int d, const int* n, const int* 
 /* ---- request server ---------------------------------------------------- */
 
 /* A request loop over one context (the paper has no counterpart: it is the
- * serving form of TT-round, Section 2.3, and of one outer iteration of the
+ * serving form of TT-round, Section 2, and of one outer iteration of the
  * Gram-Schmidt schemes, Algorithms 1-4, as an Arnoldi-type caller issues
  * them).  Requests of uneven order, mode size and rank are submitted at any
  * time from any host thread and run concurrently on `workers` lanes (child

@@ -14,7 +14,7 @@ beyond what the paper's definitions and algorithms state.
 Pinned functions and their pins live in ``tests/test_oracle_*.py``.
 """
 from .tt import (  # noqa: F401
-    tt_full, tt_entry, tt_add, tt_scale, tt_dot, tt_norm, tt_orthogonalize_rl,
+    tt_full, tt_add, tt_scale, tt_dot, tt_norm, tt_orthogonalize_rl,
     tt_round, tt_diff_norm, bond_singular_values, tt_ranks, canonical_phi,
     canonical_e, compression_ratio, compression_gain,
 )

@@ -31,15 +31,6 @@ def tt_full(cores):
     return out.reshape(shape)
 
 
-def tt_entry(cores, idx):
-    """One entry x(i_1, ..., i_d) as the product of the slice matrices
-    X_k(i_k) = core_k(:, i_k, :) (Section 2).  idx is 0-based."""
-    v = np.ones((1, 1))
-    for c, i in zip(cores, idx):
-        v = v @ c[:, i, :]
-    return float(v[0, 0])
-
-
 def tt_scale(cores, alpha):
     """alpha * x: scales the last core (any single core would do)."""
     out = [c.copy() for c in cores]

@@ -1,4 +1,4 @@
-// Batched TT-rounding: many independent roundings (Section 2.3 applied to
+// Batched TT-rounding: many independent roundings (TT-round of Section 2 applied to
 // a list of tensors) run concurrently on lanes, each lane a child context
 // with its own non-blocking stream, workspace and host worker thread.
 //

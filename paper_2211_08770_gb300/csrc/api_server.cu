@@ -1,4 +1,4 @@
-// Request server: TT-round (Section 2.3) and single outer iterations of the
+// Request server: TT-round (Section 2) and single outer iterations of the
 // Gram-Schmidt schemes (Algorithms 1-4) served from a queue by worker
 // lanes, with admission by device footprint and resident bases.
 //
@@ -48,6 +48,10 @@ struct Request {
     std::string msg;
     tt_tensor* out = nullptr;
     std::vector<double> coef;
+    // the first k vectors of the basis, copied when the request is admitted
+    // (under the server's mutex): the worker never reads the list of bases,
+    // which tt_server_add_basis may grow at the same time
+    std::vector<const tt_tensor*> basis_vecs;
 };
 
 size_t tensor_bytes(const tt_tensor* x, size_t es) {
@@ -66,7 +70,8 @@ struct tt_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> queue;
     std::map<uint64_t, Request*> reqs;
-    std::vector<std::vector<tt_tensor*>> bases;
+    // a deque: appending a basis moves none of the existing ones
+    std::deque<std::vector<tt_tensor*>> bases;
     size_t budget = 0, in_use = 0, peak = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -119,11 +124,9 @@ struct tt_server {
             if (q->kind == TT_REQ_ROUND) {
                 q->out = round_internal(l, q->x, q->delta, nullptr);
             } else {
-                const std::vector<tt_tensor*>& B = bases[q->basis];
-                std::vector<const tt_tensor*> Q(B.begin(), B.begin() + q->k);
                 q->coef.assign(q->k + 1, 0.0);
-                q->out = orth_step_internal(l, q->scheme, q->delta, TT_ROUND_PAPER, q->x, q->k, Q.data(),
-                                            q->coef.data(), nullptr);
+                q->out = orth_step_internal(l, q->scheme, q->delta, TT_ROUND_PAPER, q->x, q->k,
+                                            q->basis_vecs.data(), q->coef.data(), nullptr);
             }
             lane->sync();  // the result is complete on the device
             rehome(q->out, *root);
@@ -157,6 +160,10 @@ struct tt_server {
                 peak = std::max(peak, in_use);
                 q->running = true;
                 q->t_start = mono_now();
+                if (q->kind == TT_REQ_ORTH_STEP) {
+                    const std::vector<tt_tensor*>& B = bases[q->basis];
+                    q->basis_vecs.assign(B.begin(), B.begin() + q->k);
+                }
             }
             run(lane, q);
             {

@@ -1,6 +1,6 @@
 // Cholesky factorization with rank drop and explicit inverse of the factor:
 // G + s I = L L^T, T = L^{-1}, the small r x r step of Cholesky QR in both
-// sweeps of TT-round (Section 2.3; the Cholesky QR reading of the
+// sweeps of TT-round (Section 2; the Cholesky QR reading of the
 // orthogonalization step).
 //
 // Order n <= 256 (FP32) or 160 (FP64): one CTA holds the whole lower

@@ -1,4 +1,4 @@
-// Truncation SVD of the left-to-right sweep of TT-round (Section 2.3): the
+// Truncation SVD of the left-to-right sweep of TT-round (Section 2): the
 // singular values and vectors of the small R factor, by one-sided (Hestenes)
 // Jacobi in FP64: plane rotations orthogonalize the rows of W = R until
 // W = Sigma V^T, the rotations accumulating in U^T.

@@ -1,7 +1,7 @@
 // Allocation-free TT inner product for callers that must not allocate device
-// memory: code running inside a CUDA graph being captured, a host that has
-// already handed all device memory to its own pool, or a real-time loop
-// where cudaMalloc's implicit synchronization is not acceptable.
+// memory: a host that has already handed all device memory to its own pool
+// (a library allocation would fail or break its accounting), or a real-time
+// loop where cudaMalloc's implicit device synchronization is not acceptable.
 //
 // The contraction W_k = sum_i X_k(i)^T W_{k-1} Y_k(i) needs two work arrays
 // (W and V); here they live in one file-scope device array of fixed size,
@@ -28,20 +28,26 @@ static __device__ __align__(256) double g_dot_scratch[NOALLOC_ELEMS];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 double* g_scratch_ptr[MAX_DEVICES] = {};
+int g_sm_count[MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device.  The array's
-// name is only a host-side stand-in in host code, so the address is looked
-// up once per device with that device current.
-double* scratch_for_current_device() {
+// Device address of the scratch array on the current device, and that
+// device's SM count (the GEMMs size their grids by it).  The array's name
+// is only a host-side stand-in in host code, so the address is looked up
+// once per device with that device current.
+double* scratch_for_current_device(int* sm_count) {
     int dev = -1;
     TT_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= MAX_DEVICES) throw_status(TT_ERR_ARG, "device ordinal out of range");
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
+        int sms = 0;
+        TT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         TT_CUDA(cudaGetSymbolAddress(&p, g_dot_scratch));
+        g_sm_count[dev] = sms;
         g_scratch_ptr[dev] = static_cast<double*>(p);
     }
+    *sm_count = g_sm_count[dev];
     return g_scratch_ptr[dev];
 }
 
@@ -70,10 +76,12 @@ extern "C" tt_status tt_dot_f64_noalloc(void* cuda_stream, int d, const int* n, 
             throw_status(TT_ERR_ARG, "tt_dot_f64_noalloc: W (" + std::to_string(wmax) + ") + V (" +
                                          std::to_string(vmax) + ") doubles exceed the static scratch of " +
                                          std::to_string(NOALLOC_ELEMS) + " doubles");
-        double* scratch = scratch_for_current_device();
+        int sms = 0;
+        double* scratch = scratch_for_current_device(&sms);
         // a context object on the stack: no device memory, profiling off
         Ctx c;
         c.stream = (cudaStream_t)cuda_stream;
+        c.sm_count = sms;
         double* W = scratch;
         double* V = scratch + wmax;
         fill_identity<double>(c, 1, W, 1);  // W_0 = 1

@@ -199,3 +199,71 @@ def test_poisson_load_small(ctxs):
     assert out["completed"] == len(reqs) and not out["errors"]
     assert 0 < out["p50_ms"] <= out["p99_ms"]
     srv.close()
+
+
+def test_result_alone_equals_result_in_mix_mixed(ctxs):
+    # the mixed path in the mix and alone: each result within the mixed
+    # tolerance of the input (delta + 1e-6, relative), so two runs of one
+    # request differ by at most twice that; ranks within one (a split-K sum
+    # may round differently next to the threshold)
+    c = ctxs["mixed_tf32"]
+    Q = _basis()
+    reqs = _requests(47, 16)
+    mix = T.Server(c, workers=6)
+    bid = mix.add_basis([T.tt_tensor_create(c, q) for q in Q])
+    got_mix = _serve(c, mix, bid, reqs)
+    assert mix.stats()["completed"] == len(reqs)
+    mix.close()
+    alone = T.Server(c, workers=1)
+    bid1 = alone.add_basis([T.tt_tensor_create(c, q) for q in Q])
+    got_alone = _serve(c, alone, bid1, reqs, one_by_one=True)
+    alone.close()
+    for q, (ym, cm), (ya, ca) in zip(reqs, got_mix, got_alone):
+        tol = q["delta"] + 1e-6
+        nx = O.tt_norm(q["cores"])
+        assert all(abs(a - b) <= 1 for a, b in zip(O.tt_ranks(ym), O.tt_ranks(ya)))
+        if q["kind"] == "round":
+            assert O.tt_diff_norm(ym, q["cores"]) <= tol * nx
+            assert O.tt_diff_norm(ya, q["cores"]) <= tol * nx
+            assert O.tt_diff_norm(ym, ya) <= 2 * tol * nx
+        else:
+            assert np.abs(np.array(cm) - np.array(ca)).max() <= 2 * tol * nx
+            assert O.tt_diff_norm(ym, ya) <= 20 * tol * nx / ca[-1]
+
+
+def test_add_basis_while_steps_run(ctxs):
+    # tt_server_add_basis grows the list of bases while workers run
+    # orthogonalization steps against basis 0: each step reads the basis
+    # vectors it was admitted with, and every result equals the same step
+    # served alone
+    import threading
+    c = ctxs["fp64"]
+    Q = _basis()
+    srv = T.Server(c, workers=6)
+    qs = [T.tt_tensor_create(c, q) for q in Q]
+    bid = srv.add_basis(qs)
+    rng = np.random.default_rng(48)
+    xs = [random_tt(rng, N, [1, 3, 4, 4, 3, 1]) for _ in range(24)]
+    hx = [T.tt_tensor_create(c, x) for x in xs]
+    added = []
+    stop = threading.Event()
+
+    def grow():
+        while not stop.is_set() and len(added) < 64:
+            added.append(srv.add_basis(qs))
+
+    th = threading.Thread(target=grow)
+    th.start()
+    try:
+        tickets = [srv.submit_orth(h, bid, 12, "cgs2" if i % 2 else "mgs2", 1e-9) for i, h in enumerate(hx)]
+        res = [srv.wait(t, coef_cap=13) for t in tickets]
+    finally:
+        stop.set()
+        th.join()
+    assert len(added) > 0 and len(set(added)) == len(added)
+    for i, (y, cf, _) in enumerate(res):
+        q_ref, col_ref, _ = O.gs_step(xs[i], Q, 1e-9, "cgs2" if i % 2 else "mgs2")
+        got = y.cores()
+        assert O.tt_diff_norm(got, q_ref) <= 1e-12
+        assert np.abs(np.array(cf) - col_ref).max() <= 1e-12 * O.tt_norm(xs[i])
+    srv.close()

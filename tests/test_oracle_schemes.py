@@ -267,3 +267,36 @@ def test_gs_step_first_vector():
     assert col[0] == O.tt_norm(y)
     for c1, c2 in zip(q, O.tt_scale(y, 1.0 / col[0])):
         assert np.array_equal(c1, c2)
+
+
+def _unit_rank1(rng, n):
+    vs = [rng.standard_normal(k) for k in n]
+    vs = [v / np.linalg.norm(v) for v in vs]
+    return [v.reshape(1, -1, 1) for v in vs]
+
+
+def test_loss_of_orthogonality_closed_forms():
+    # eq. LOO is the spectral norm of I - Q^T Q, with the Gram entries taken
+    # from TT dots.  Three sets whose spectral norm is known in closed form
+    # and differs from the Frobenius norm, the largest entry and the largest
+    # signed eigenvalue, so that any of those mistakes fails:
+    rng = np.random.default_rng(77)
+    n = [4, 5, 3]
+    v = _unit_rank1(rng, n)
+    # (a) three copies of one unit vector: I - J_3 has eigenvalues -2, 1, 1,
+    #     so the LOO is 2 (Frobenius sqrt(6), largest entry 1, max eig 1)
+    assert abs(O.loss_of_orthogonality([v, v, v]) - 2.0) <= 1e-14
+    # (b) q_1 = e_1, q_2 = (e_1 + e_2)/sqrt(2): I - G = [[0, -c], [-c, 0]]
+    #     with c = 1/sqrt(2); eigenvalues +-c, LOO = c (Frobenius 1)
+    e1, e2 = O.canonical_e(1, n), O.canonical_e(2, n)
+    q2 = O.tt_scale(O.tt_add([1.0, 1.0], [e1, e2]), 1.0 / np.sqrt(2.0))
+    assert abs(O.loss_of_orthogonality([e1, q2]) - 1.0 / np.sqrt(2.0)) <= 1e-15
+    # (c) an orthonormal pair scaled by 2 and 1/2 plus a third orthonormal
+    #     vector: I - G = diag(-3, 3/4, 0), LOO = 3 (max eig 3/4)
+    e3 = O.canonical_e(7, n)
+    got = O.loss_of_orthogonality([O.tt_scale(e1, 2.0), O.tt_scale(e2, 0.5), e3])
+    assert abs(got - 3.0) <= 1e-14
+    # (d) an exactly orthonormal set of rank-2 TTs: LOO at round-off
+    Q = [O.tt_scale(O.tt_add([1.0, s], [O.canonical_e(j, n), O.canonical_e(j + 20, n)]), 1 / np.sqrt(2.0))
+         for j, s in ((1, 1.0), (2, -1.0), (3, 1.0))]
+    assert O.loss_of_orthogonality(Q) <= 1e-15

@@ -1,9 +1,10 @@
 """The allocation-free TT dot (tt_dot_f64_noalloc) against the regular entry
 point tt_dot, through the C ABI, on two calls in a row.
 
-This entry point serves callers that cannot allocate device memory (graph
-capture in progress, hosts whose device memory belongs to their own pool,
-latency-critical loops); its work arrays live in a static device array.
+This entry point serves callers that cannot allocate device memory (hosts
+whose device memory all belongs to their own pool, latency-critical loops
+that must not pay cudaMalloc's implicit synchronization); its work arrays
+live in a static device array.
 The file is named to be collected last, and it passes both on its own in a
 fresh process and after the rest of the suite.
 """
