@@ -29,8 +29,14 @@ WORKLOAD = "sum of 20 random TTs (d=10, n=64, ranks 20, N(0,1) cores, alpha~U(-1
 
 # nominal / measured peaks (MEASURED_PEAKS.json when present)
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+SM_COUNT = None  # read from the device (cudaDevAttrMultiProcessorCount) by run_ours
+
+
+def fp32_alu_peak(peaks):
+    """FP32 CUDA-core peak in TFLOP/s: SMs x 128 FP32 lanes x 2 (FMA) x the
+    maximum SM clock, with the SM count queried from the device."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
 def load_peaks():
@@ -50,16 +56,16 @@ def roofline_for(fam, prof, peaks, src):
         return "tensor", prof["flops"] / secs / 1e12, peak, "TFLOP/s", (
             "%s sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25" % src)
     if fam in ("gemm_f32", "gram_f32", "sgemm_f32", "sgram_f32"):
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        return "alu", prof["flops"] / secs / 1e12, peak, "TFLOP/s", "152 SMs x 128 FP32 lanes x 2 x max SM clock"
+        return "alu", prof["flops"] / secs / 1e12, fp32_alu_peak(peaks), "TFLOP/s", (
+            "%d SMs (queried) x 128 FP32 lanes x 2 x max SM clock" % SM_COUNT)
     if fam in ("gemm_f64", "gram_f64"):
         return "alu", prof["flops"] / secs / 1e12, 1.25, "TFLOP/s", "nominal GB300 FP64 rate"
     if fam == "chol_inv":
         # the r x r Cholesky + inverse: single-CTA (latency-bound) factors of the
         # diagonal blocks plus CUDA-core GEMMs; the roofline is the FP32 ALU of the GPU
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        return "alu", prof["flops"] / secs / 1e12, peak, "TFLOP/s", (
-            "152 SMs x 128 FP32 lanes x 2 x max SM clock (the kernel is latency-bound on few SMs)")
+        return "alu", prof["flops"] / secs / 1e12, fp32_alu_peak(peaks), "TFLOP/s", (
+            "%d SMs (queried) x 128 FP32 lanes x 2 x max SM clock (the kernel is latency-bound on few SMs)"
+            % SM_COUNT)
     return "hbm", prof["bytes"] / secs / 1e9, peaks["hbm_gbs"], "GB/s", "%s HBM copy bandwidth" % src
 
 
@@ -191,8 +197,10 @@ def run_ours(args):
     import numpy as np
     import torch
 
+    global SM_COUNT
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
+    SM_COUNT = torch.cuda.get_device_properties(local).multi_processor_count
     dist = None
     dev = "cuda:%d" % local
     if world > 1:
@@ -295,6 +303,34 @@ def run_ours(args):
         return dict(value=value, unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
                     host_memory="page-locked, storage dtype (tt_tensor_create_storage / tt_round_to_host)")
 
+    def accuracy(precision):
+        """||x - round(x)|| / ||x|| of one rounding of the workload on the
+        given path (outside the timed region), x being the exact FP64 sum of
+        the FP64 inputs.  Measured with the FP64 GPU path (TT sum with -1 and
+        the norm by right-to-left orthogonalization, no cancellation)."""
+        ctx = T.Ctx(local, precision, stream=stream.cuda_stream)
+        X = [T.tt_tensor_create(ctx, c) for c in xs]
+        s = T.tt_add(ctx, al, X)
+        y, est = T.tt_round(ctx, s, DELTA)
+        cores = y.cores()
+        st = ctx.stats()
+        for v in X + [s, y]:
+            v.free()
+        ctx.close()
+        c64 = T.Ctx(local, "fp64", stream=stream.cuda_stream)
+        X64 = [T.tt_tensor_create(c64, c) for c in xs]
+        x64 = T.tt_add(c64, al, X64)
+        y64 = T.tt_tensor_create(c64, cores)
+        diff = T.tt_add(c64, [1.0, -1.0], [x64, y64])
+        err = T.tt_norm(c64, diff) / T.tt_norm(c64, x64)
+        for v in X64 + [x64, y64, diff]:
+            v.free()
+        c64.close()
+        return {"rel_error": err, "rel_error_over_delta": err / DELTA, "err_est": est,
+                "bound": "delta + 1e-6 (FP32 storage)" if precision != "fp64" else "delta",
+                "second_pass_skips": int(st["second_pass_skips"]), "series_passes": int(st["series_passes"]),
+                "measured_by": "FP64 GPU path: ||x - x~|| from the TT sum x - x~ and its norm"}
+
     prec = args.precision
     # Every family's launches are timed on a short separate pass (two events
     # per launch cost host time, which shows in a step of ~300 launches); the
@@ -318,7 +354,8 @@ def run_ours(args):
            "host_syncs": int(main["stats"]["host_syncs"]),
            "path_stats": {k: int(main["stats"][k]) for k in ("svd_calls", "certified_bonds", "fallback_orth", "series_passes",
                                                                           "second_pass_skips")},
-           "clocks": main["clocks"]}
+           "clocks": main["clocks"],
+           "accuracy": accuracy(prec)}
     # roofline of the dominant kernel family
     prof = main["prof"]
     if prof and dom in prof:
@@ -346,7 +383,8 @@ def run_ours(args):
         f = time_path("fp64", args.fp64_steps, 1, profile=False)
         fv = world * args.fp64_steps / (f["tot_ms"] / 1e3)
         out["fp64_path"] = {"value": fv, "unit": UNIT, "ms_per_step": f["tot_ms"] / args.fp64_steps,
-                            "steps": args.fp64_steps, "output_ranks": f["ranks"]}
+                            "steps": args.fp64_steps, "output_ranks": f["ranks"], "clocks": f["clocks"],
+                            "accuracy": accuracy("fp64")}
         out["speedup_vs_fp64"] = value / fv
     out["e2e"] = time_e2e(prec, args.e2e_steps)
     if args.batch_count > 0:
@@ -464,7 +502,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed_tf32", choices=["mixed_tf32", "fp32", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--no-fp64", action="store_true")

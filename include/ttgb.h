@@ -139,6 +139,18 @@ tt_status tt_ctx_get_stats(const tt_ctx* ctx, tt_stats* out);
 void      tt_ctx_reset_stats(tt_ctx* ctx);
 tt_precision tt_ctx_precision(const tt_ctx* ctx);
 
+/* Limit, in SM clock cycles, of the bounded mbarrier waits of the
+ * tensor-core row Gram (tt_gram_f32 with use_tensor_cores = 1, and the
+ * Gram steps of TT-round that run on it); 0 restores the default of 4e9
+ * cycles (about 2 s).  Every wait of that kernel gives up after the limit:
+ * the kernel stops issuing work, lets the copies it already issued land and
+ * waits for its MMAs (those two waits keep the default limit), frees its
+ * tensor memory and returns; the call then fails with TT_ERR_TIMEOUT and
+ * the context stays usable.  A limit far below the kernel's normal wait
+ * times forces that path, for testing it.  Lanes created afterwards copy
+ * the setting.  TT_ERR_ARG for a negative limit. */
+tt_status tt_ctx_set_tc_wait_limit(tt_ctx* ctx, long long cycles);
+
 /* Enables (on != 0) or disables event timing of the library's launches. */
 tt_status tt_ctx_set_profiling(tt_ctx* ctx, int on);
 /* Restricts event timing to one kernel family (its name as reported by

@@ -22,3 +22,6 @@ from .schemes import (  # noqa: F401
     SCHEMES, tt_cgs, tt_mgs, tt_cgs2, tt_mgs2, tt_gram, tt_householder,
     tth_vec, apply_h_vec, loss_of_orthogonality, orthogonalize, gs_step,
 )
+from .operators import (  # noqa: F401
+    laplace_1d, laplacian_ttm, ttm_full, tt_matvec, tt_round_rank, ones_tt, krylov_inputs, loo_curve,
+)

@@ -475,6 +475,12 @@ tt_status tt_ctx_set_profiling(tt_ctx* ctx, int on) {
     return TT_OK;
 }
 
+tt_status tt_ctx_set_tc_wait_limit(tt_ctx* ctx, long long cycles) {
+    if (!ctx || cycles < 0) return TT_ERR_ARG;
+    ctx->tc_wait_limit = cycles;
+    return TT_OK;
+}
+
 tt_status tt_ctx_set_profiling_family(tt_ctx* ctx, const char* family) {
     if (!ctx) return TT_ERR_ARG;
     ctx->prof_only = family ? family : "";

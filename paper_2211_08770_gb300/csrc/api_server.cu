@@ -211,6 +211,7 @@ tt_status tt_server_create(tt_ctx* ctx, int workers, size_t footprint_budget, tt
         l->use_tc = ctx->use_tc;
         l->use_tc_gemm = ctx->use_tc_gemm;
         l->tc_gemm_split = ctx->tc_gemm_split;
+        l->tc_wait_limit = ctx->tc_wait_limit;
         cudaError_t e = cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaMalloc(&l->tc_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(l->tc_err, 0, sizeof(int));

@@ -243,6 +243,7 @@ struct Ctx {
     bool use_tc_gemm = false;
     int tc_gemm_split = 3;    // 3: hi + mid + lo (6 products), 2: hi + lo (3 products)
     int* tc_err = nullptr;  // device flag: a bounded wait of a tensor-core kernel ran out
+    long long tc_wait_limit = 0;  // SM cycles of the row Gram's bounded waits (0: ~2 s)
     // lifetime: one reference for the owner plus one per live tensor; the
     // context is deleted when the last reference goes
     std::atomic<long> refs{1};

@@ -8,8 +8,10 @@
 // G.  Warp 0 issues TMA loads of 128 x 32 FP32 boxes (128-byte swizzle) into
 // a 5-stage ring; warp 1 allocates 128 TMEM columns and issues 4 MMAs of
 // 128 x 128 x 8 per stage; warps 2-5 read the accumulator back with
-// tcgen05.ld.  Every mbarrier wait is bounded; a timeout sets *err and the
-// CTA winds down (TMEM is always freed).
+// tcgen05.ld.  Every mbarrier wait is bounded (the context's limit, about
+// 2 s by default); a timeout sets *err and the CTA winds down: it stops
+// issuing work, lets the copies already issued land and waits for its MMAs
+// (both with the long limit), and always frees TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -40,7 +42,7 @@ struct __align__(8) GramSmem {
 
 __global__ void __launch_bounds__(192, 1)
 gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int ntiles, long kchunk_steps,
-                 float* __restrict__ G, int* __restrict__ err) {
+                 float* __restrict__ G, int* __restrict__ err, long long limit) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned operand ring, control block after it
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -87,7 +89,7 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int nt
             for (int it = 0; it < nsteps; ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (it / STAGES) & 1;
-                if (!tc::mbar_wait_bounded(&ctl->empty[s], ph ^ 1, WAIT_LIMIT)) { ok = false; break; }
+                if (!tc::mbar_wait_bounded(&ctl->empty[s], ph ^ 1, limit)) { ok = false; break; }
                 unsigned char* a = ring + s * 2 * TILE_BYTES;
                 tc::mbar_arrive_expect_tx(&ctl->full[s], bytes);
                 const int kx = (int)((ks0 + it) * TK);
@@ -95,12 +97,15 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int nt
                 if (!diag) tc::tma_load_2d(a + TILE_BYTES, &tmap, &ctl->full[s], kx, tj * TB);
                 ++issued;
             }
-            if (!ok) {
-                atomicExch(err, 1);
-                // let the copies already issued land before the CTA can exit
-                for (int it = max(0, issued - STAGES); it < issued; ++it)
-                    tc::mbar_wait_bounded(&ctl->full[it % STAGES], (it / STAGES) & 1, WAIT_LIMIT);
-            }
+            if (!ok) atomicExch(err, 1);
+            // every copy issued lands before the CTA can exit, also when the
+            // MMA warp gave up consuming them: issuing step it + STAGES
+            // waited for step it to be consumed (its copy landed), so only
+            // the last STAGES issued can still be in flight.  A completed
+            // phase answers at once; the wait keeps the long limit whatever
+            // the context's limit is.
+            for (int it = max(0, issued - STAGES); it < issued; ++it)
+                tc::mbar_wait_bounded(&ctl->full[it % STAGES], (it / STAGES) & 1, WAIT_LIMIT);
         }
     } else if (warp == 1) {
         if (lane == 0 && nsteps > 0) {
@@ -108,7 +113,7 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int nt
             for (int it = 0; it < nsteps; ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (it / STAGES) & 1;
-                if (!tc::mbar_wait_bounded(&ctl->full[s], ph, WAIT_LIMIT)) { ok = false; break; }
+                if (!tc::mbar_wait_bounded(&ctl->full[s], ph, limit)) { ok = false; break; }
                 tc::tc_fence_after();
                 const uint32_t a_addr = tc::smem_u32(ring + s * 2 * TILE_BYTES);
                 const uint32_t b_addr = diag ? a_addr : a_addr + TILE_BYTES;
@@ -127,7 +132,7 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int nt
         // epilogue warps 2..5: TMEM lane quarter = warp % 4
         const int q = warp & 3;
         // warp-uniform decisions: tcgen05.ld needs the whole warp converged
-        const bool got = __all_sync(0xffffffffu, tc::mbar_wait_bounded(&ctl->done, 0, 2 * WAIT_LIMIT));
+        const bool got = __all_sync(0xffffffffu, tc::mbar_wait_bounded(&ctl->done, 0, 2 * limit));
         int e = 0;
         if (lane == 0) e = *(volatile int*)err;
         e = __shfl_sync(0xffffffffu, e, 0);
@@ -383,9 +388,10 @@ bool gram_rows_tc_tf32(Ctx& c, int n, long K, const float* X, long ldx, float* G
     static std::atomic<bool> attr{false};
     set_smem_once(attr, gram_tf32_kernel, (int)smem);
     int* err = c.tc_err;
+    const long long limit = c.tc_wait_limit > 0 ? c.tc_wait_limit : WAIT_LIMIT;
     TT_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n * n, c.stream));
     ProfScope ps(c, "gram_tf32_tc", (double)n * (n + 1) * (double)K, 4.0 * (double)n * K + 4.0 * n * n);
-    gram_tf32_kernel<<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, K, ntiles, kchunk, G, err);
+    gram_tf32_kernel<<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, K, ntiles, kchunk, G, err, limit);
     TT_LAUNCHED(c);
     return true;
 }

@@ -60,6 +60,7 @@ _SIGS = {
     "tt_ctx_precision": (_I, [_P]),
     "tt_ctx_set_profiling": (_I, [_P, _I]),
     "tt_ctx_set_profiling_family": (_I, [_P, C.c_char_p]),
+    "tt_ctx_set_tc_wait_limit": (_I, [_P, C.c_longlong]),
     "tt_ctx_get_profile": (_I, [_P, C.POINTER(_Prof), _I, _PI]),
     "tt_ctx_reset_profile": (None, [_P]),
     "tt_tensor_create": (_I, [_P, _I, _PI, _PI, C.POINTER(_PD), C.POINTER(_P)]),
@@ -175,6 +176,11 @@ class Ctx:
         _check(lib().tt_ctx_get_profile(self._h, buf, 64, C.byref(k)), "tt_ctx_get_profile")
         return {buf[i].name.decode(): dict(launches=int(buf[i].launches), total_ms=buf[i].total_ms,
                                            flops=buf[i].flops, bytes=buf[i].bytes) for i in range(min(64, k.value))}
+
+    def set_tc_wait_limit(self, cycles):
+        """SM-cycle limit of the tensor-core row Gram's bounded waits (0: the
+        default, about 2 s)."""
+        _check(lib().tt_ctx_set_tc_wait_limit(self._h, int(cycles)), "tt_ctx_set_tc_wait_limit")
 
     def set_sign_rule(self, rule):
         _check(lib().tt_set_sign_rule(self._h, SIGN[rule]), "tt_set_sign_rule")

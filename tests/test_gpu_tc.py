@@ -137,3 +137,37 @@ def test_cholesky_inverse_drops_dependent_rows(n, nb, dep, monkeypatch):
     Q = Th[keep] @ X
     assert np.allclose(Q @ Q.T, np.eye(n - len(dep)), atol=1e-10)
     c.close()
+
+
+def test_tc_gram_bounded_wait_runs_out_and_context_recovers(ctx):
+    # A one-cycle limit makes the row Gram's mbarrier waits give up before
+    # the first TMA copy lands: the kernel records the timeout, lets its
+    # issued copies land, waits for its MMAs, frees TMEM and returns; the
+    # call reports TT_ERR_TIMEOUT.  With the default limit restored the same
+    # context computes the Gram, and a TT-round on it succeeds.
+    n, K = 256, 32768
+    g = torch.Generator(device="cpu").manual_seed(99)
+    Xh = torch.randn(n, K, generator=g, dtype=torch.float32)
+    X = Xh.cuda()
+    G = torch.zeros((n, n), device="cuda", dtype=torch.float32)
+    ctx.set_tc_wait_limit(1)
+    try:
+        with pytest.raises(T.TTError) as e:
+            T.tt_gram_f32(ctx, n, K, X.data_ptr(), K, G.data_ptr(), True)
+        assert e.value.name == "TT_ERR_TIMEOUT"
+    finally:
+        ctx.set_tc_wait_limit(0)
+    T.tt_gram_f32(ctx, n, K, X.data_ptr(), K, G.data_ptr(), True)
+    torch.cuda.synchronize()
+    Xd = Xh.numpy().astype(np.float64)
+    ref = Xd @ Xd.T
+    mask = _lower_tiles_mask(n, 128)
+    dg = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    assert (np.abs(G.cpu().numpy().astype(np.float64) - ref)[mask] / dg[mask]).max() <= 4e-3
+    with pytest.raises(T.TTError):
+        ctx.set_tc_wait_limit(-1)
+    import oracle as O
+    from ttinputs import random_tts
+    x = O.tt_add([1.0, -0.5], random_tts(5, 2, 4, 64, 24))
+    y, _ = T.tt_round(ctx, T.tt_tensor_create(ctx, x), 1e-6)
+    assert O.tt_diff_norm(y.cores(), x) <= 2e-6 * O.tt_norm(x)
