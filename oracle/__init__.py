@@ -25,3 +25,7 @@ from .schemes import (  # noqa: F401
 from .operators import (  # noqa: F401
     laplace_1d, laplacian_ttm, ttm_full, tt_matvec, tt_round_rank, ones_tt, krylov_inputs, loo_curve,
 )
+from .variants import (  # noqa: F401
+    right_sketch_contractions, tt_round_randomized, right_grams, tt_round_gram_svd, householder_apply,
+    householder_q,
+)
