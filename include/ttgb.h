@@ -276,6 +276,87 @@ tt_status tt_round_batched(tt_ctx* ctx, int count, const tt_tensor* const* x,
 tt_status tt_ctx_set_concurrency(tt_ctx* ctx, int lanes);
 int       tt_ctx_get_concurrency(const tt_ctx* ctx);
 
+/* TT-round(x, delta) with every TT-rank also capped at max_rank (the
+ * rounding of the Krylov process of Section 4, where the accuracy is
+ * replaced by a maximum TT-rank): each left-to-right bond keeps
+ * min(max_rank, minimal rank within eps) singular values, so the error
+ * bound delta ||x|| holds only when the cap does not bind; err_est reports
+ * the discarded root-sum-square relative to ||x|| either way.  max_rank = 0
+ * is tt_round; max_rank < 0 gives TT_ERR_ARG. */
+tt_status tt_round_capped(tt_ctx* ctx, const tt_tensor* x, double delta, int max_rank,
+                          tt_tensor** out, double* err_est);
+
+/* TT-round(x, delta) from Gram matrices, without orthogonalizing the cores
+ * (a GEMM-only variant of Section 2's TT-round): one right-to-left sweep of
+ * contractions gives the Gram G_R of the right part of x at every bond;
+ * then bond by bond, left to right, the Gram G_L of the current left
+ * unfolding (the cores to its left are orthonormal by then), Cholesky
+ * factors G_L = A A^T and G_R = B B^T (numerically zero pivots dropped),
+ * the SVD A^T B = U S V^T (Jacobi, FP64 arithmetic), the truncation rank
+ * from S at eps = delta ||x|| / sqrt(d - 1) (at most max_rank if > 0),
+ * core_k <- core_k A^{-T} U_r and core_{k+1} <- S_r V_r^T B^{-1} core_{k+1}.
+ * Squaring the condition numbers limits the accuracy to about
+ * sqrt(r u) ||x|| (u the storage precision's unit round-off: FP64 contexts
+ * resolve delta >= 1e-7 or so, FP32 ones delta >= 1e-3); err_est as
+ * tt_round's.  Errors as tt_round; max_rank < 0 gives TT_ERR_ARG. */
+tt_status tt_round_gram_svd(tt_ctx* ctx, const tt_tensor* x, double delta, int max_rank,
+                            tt_tensor** out, double* err_est);
+
+/* Randomized TT-rounding (randomize-then-orthogonalize; Section 2 cites it
+ * for large tensors): omega is a TT with x's modes and ranks l_k whose
+ * entries are the method's random draws (the caller draws them, e.g.
+ * iid N(0,1)).  W_k = contraction of the right parts of x and omega at bond
+ * k; then left to right the sketch Z = X_k^L W_{k+1} is orthonormalized
+ * (a shifted Cholesky QR pass and two unshifted ones, so that Q spans
+ * range(Z) whatever its conditioning), core_k <- Q and core_{k+1} <-
+ * (Q^T X_k^L) core_{k+1}.  The ranks become min(l_k, rows of Z); with
+ * probability near one the result is within a small factor of the best
+ * approximation of those ranks once l_k exceeds the target rank by a few
+ * (oversampling).  delta > 0: the result is then TT-rounded at delta.
+ * TT_ERR_SHAPE when omega's modes differ from x's. */
+tt_status tt_round_randomized(tt_ctx* ctx, const tt_tensor* x, const tt_tensor* omega, double delta,
+                              tt_tensor** out);
+
+/* ---- TT-matrices (Section 4) ------------------------------------------- */
+
+/* A TT-matrix (TT-operator) M with M((i_1..i_d), (j_1..j_d)) =
+ * M_1(i_1, j_1) ... M_d(i_d, j_d), core k stored [R_{k-1}][m_k][n_k][R_k]
+ * row-major (R_k fastest; m_k output, n_k input mode size), R_0 = R_d = 1,
+ * in the context's storage type.  Library-owned; released with
+ * tt_operator_free.  The paper's experiments apply the Dirichlet Laplacian
+ * in this form to build their inputs (Section 4). */
+typedef struct tt_operator tt_operator;
+
+/* Copies host FP64 cores (host_cores[k]: R[k]*m[k]*n[k]*R[k+1] doubles) to
+ * the device (narrowed to FP32 for FP32 contexts).  TT_ERR_ARG for d < 1,
+ * R_0 != 1, R_d != 1, or a size or rank < 1. */
+tt_status tt_operator_create(tt_ctx* ctx, int d, const int* m, const int* n, const int* R,
+                             const double* const* host_cores, tt_operator** out);
+/* The d-dimensional Dirichlet Laplacian on n points per mode,
+ * sum_k I x .. x L x .. x I with L = tridiag(-1, 2, -1) (grid scaling
+ * dropped), as a TT-matrix of ranks 2: cores [L I], [[I 0], [L I]], [I; L]. */
+tt_status tt_operator_laplacian(tt_ctx* ctx, int d, int n, tt_operator** out);
+/* d, m[0..d-1], n[0..d-1], R[0..d] (each may be NULL; caller-sized). */
+tt_status tt_operator_shape(const tt_operator* op, int* d, int* m, int* n, int* R);
+/* Copies the cores to host FP64 arrays (layout as tt_operator_create). */
+tt_status tt_operator_download(tt_ctx* ctx, const tt_operator* op, double* const* host_cores);
+void      tt_operator_free(tt_operator* op);
+
+/* y = M x: core k of y is y_k((a, p), i, (b, q)) = sum_j M_k(a, i, j, b)
+ * x_k(p, j, q), mode sizes m_k and ranks R_k r_k (the operator's rank
+ * index slowest).  One thread per output element, FP64 accumulation.
+ * TT_ERR_SHAPE when the orders or the input modes differ. */
+tt_status tt_matvec(tt_ctx* ctx, const tt_operator* M, const tt_tensor* x, tt_tensor** out);
+
+/* The input family of the paper's experiments (Section 4): from x_1,
+ * a_j = y_j / ||y_j|| with y_j = tt_round_capped(x_j, delta, max_rank), and
+ * x_{j+1} = -M a_j, for j = 1..m; out[0..m-1] receive a_1..a_m.  The paper
+ * takes x_1 the all-ones tensor, M the Dirichlet Laplacian, delta = 0 and
+ * max_rank = 1.  M must be square on x_1's modes (TT_ERR_SHAPE);
+ * TT_ERR_BREAKDOWN if some y_j is zero. */
+tt_status tt_krylov_basis(tt_ctx* ctx, const tt_operator* M, const tt_tensor* x1, int m, double delta,
+                          int max_rank, tt_tensor** out);
+
 /* ---- orthogonalization (Section 3) ------------------------------------ */
 
 /* Orthogonalizes A[0..m-1] with `scheme` (Algorithms 1-5, 8) at rounding
@@ -290,6 +371,29 @@ tt_status tt_orthogonalize(tt_ctx* ctx, tt_scheme scheme, double delta,
                            tt_round_policy policy, int m,
                            const tt_tensor* const* A, tt_tensor** Q,
                            double* R, int* n_rounds);
+
+/* The canonical basis TT-vector e_j (Section 3.3): rank 1, a single 1 at
+ * the multi-index phi(j) with i_1 running fastest; j is 0-based
+ * (0 <= j < prod n, else TT_ERR_ARG). */
+tt_status tt_canonical(tt_ctx* ctx, int d, const int* n, long j, tt_tensor** out);
+
+/* TT-Householder keeping only the Householder TT-vectors (Sections 4.4 and
+ * 5: the basis q_k need not be formed): the first loop of Algorithm 8 with
+ * its 3m roundings; U[0..m-1] receive u_1..u_m (library-allocated), R
+ * (host, m*m, column-major) the upper triangular factor, n_rounds (may be
+ * NULL) the roundings made.  Other arguments and errors as
+ * tt_orthogonalize with TT_HOUSEHOLDER. */
+tt_status tt_householder_vectors(tt_ctx* ctx, double delta, tt_round_policy policy, int m,
+                                 const tt_tensor* const* A, tt_tensor** U, double* R, int* n_rounds);
+
+/* Applies the reflections H_j = I - 2 u_j u_j^T of U[0..k-1] (Algorithm 7
+ * each): transpose = 0 gives Q x = H_1 H_2 ... H_k x (H_k applied first),
+ * transpose != 0 gives Q^T x = H_k ... H_1 x (H_1 first).  delta >= 0
+ * TT-rounds after every reflection; delta < 0 rounds nothing (ranks add).
+ * q_j of Algorithm 8 is tt_round(tt_householder_apply(U, j, e_j, 0, -1)).
+ * k = 0 returns a copy of x. */
+tt_status tt_householder_apply(tt_ctx* ctx, int k, const tt_tensor* const* U, const tt_tensor* x,
+                               int transpose, double delta, tt_tensor** out);
 
 /* ---- building block ---------------------------------------------------- */
 

@@ -38,7 +38,7 @@ tt_tensor* tt_add_internal(tt_ctx* ctx, int m, const double* alpha, const tt_ten
 tt_tensor* scale_internal(tt_ctx* ctx, const tt_tensor* x, double alpha);
 void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out);
 tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est,
-                          void* const* host_out = nullptr);
+                          void* const* host_out = nullptr, int max_rank = 0);
 double norm_internal(tt_ctx* ctx, const tt_tensor* x);
 // moves a tensor made on a lane to its root (see get_lanes)
 void rehome(tt_tensor* t, Ctx& root);

@@ -65,6 +65,8 @@ struct Rounder {
     double skip_budget = 0.0;  // second passes are skipped (first pass kept
                                // alone) while the sum of their ||E||_F stays
                                // within this budget (0: never, e.g. for norms)
+    int max_rank = 0;          // rank cap of the left-to-right truncation (0: none)
+    bool capped(int b) const { return max_rank > 0 && b > max_rank; }
 
     Rounder(tt_ctx* ctx, const tt_tensor* x) : c(ctx), d(x->d), n(x->n), r(x->r) {
         const bool is64 = sizeof(T) == 8;
@@ -109,6 +111,7 @@ struct Rounder {
         if (copied) cudaStreamSynchronize(c->copy_stream);
         for (cudaEvent_t e : copy_events) c->ev_pool.push_back(e);
         if (ws) c->release(ws, ws_bytes);
+        if (ws64) c->release(ws64, ws64_bytes);
     }
 
     // Host destinations of the output cores (storage type, null: none):
@@ -317,6 +320,10 @@ struct Rounder {
         // shifted Cholesky QR, then two passes with dependent rows dropped
         c->stats.fallback_orth++;
         o.shifted = true;
+        if constexpr (sizeof(T) == 4) {
+            fallback_fp64(rows, a, K, X, o);
+            return o;
+        }
         gram_into(rows, false, a, K, X);
         chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 8.0 * ug_fb * sq, 0.0, next_st());
         apply(rows, a, K, X, Ti[0]);
@@ -330,6 +337,70 @@ struct Rounder {
         o.npass = 3;
         o.nchol = 3;
         return o;
+    }
+
+    // FP64 work buffers of the fallback orthogonalization of FP32 data,
+    // allocated on its first use in a rounding
+    char* ws64 = nullptr;
+    size_t ws64_bytes = 0;
+    double *x64 = nullptr, *s64 = nullptr, *G64 = nullptr, *P64 = nullptr, *L64[3] = {}, *T64[3] = {};
+    static size_t fallback64_bytes(int rmax, size_t cap) {
+        auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+        return 2 * al(cap * sizeof(double)) + 8 * al((size_t)rmax * rmax * sizeof(double));
+    }
+    void ensure_ws64() {
+        if (ws64) return;
+        auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+        const size_t rr = (size_t)rmax * rmax;
+        ws64_bytes = fallback64_bytes(rmax, cap);
+        ws64 = (char*)c->alloc(ws64_bytes);
+        char* p = ws64;
+        x64 = (double*)p; p += al(cap * sizeof(double));
+        s64 = (double*)p; p += al(cap * sizeof(double));
+        G64 = (double*)p; p += al(rr * sizeof(double));
+        P64 = (double*)p; p += al(rr * sizeof(double));
+        for (int i = 0; i < 3; ++i) { L64[i] = (double*)p; p += al(rr * sizeof(double)); }
+        for (int i = 0; i < 3; ++i) { T64[i] = (double*)p; p += al(rr * sizeof(double)); }
+    }
+
+    // The fallback for FP32 data in FP64 arithmetic: X widened to FP64,
+    // shifted Cholesky QR (s = 8 sqrt(a) u_64 trace G) and two unshifted
+    // passes dropping only FP64-level zero pivots, Q narrowed back into X and
+    // the factors into Lp (and Lf/Ti for the certificate).  Cholesky QR in
+    // FP32 loses the content of an unfolding below about sqrt(u_32) of its
+    // norm, which for the cancelling sums of the Gram-Schmidt schemes is a
+    // large part of the result; in FP64 the loss is at the FP32 storage
+    // rounding itself (X = L Q to u_32 ||X||).
+    void fallback_fp64(bool rows, int a, long K, T*& X, Orth& o) {
+        ensure_ws64();
+        const double u64 = 1.1102230246251565e-16;
+        const double sq = sqrt((double)a);
+        const long nel = (long)a * K;
+        convert<T, double>(*c, nel, X, x64);
+        double* Xd = x64;
+        double* Sd = s64;
+        for (int p = 0; p < 3; ++p) {
+            gram<double, double>(*c, rows, a, K, Xd, rows ? K : a, G64);
+            chol_inv<double, double>(*c, a, G64, L64[p], T64[p], p == 0 ? 8.0 * u64 * sq : 0.0,
+                                     p == 0 ? 0.0 : 8.0 * u64 * sq, next_st());
+            if (rows)
+                gemm<double>(*c, false, false, a, (int)K, a, 1.0, T64[p], a, Xd, K, 0.0, Sd, K, 1, 0, 0, 0, TRI_A_LOWER);
+            else
+                gemm<double>(*c, false, true, (int)K, a, a, 1.0, Xd, a, T64[p], a, 0.0, Sd, a, 1, 0, 0, 0, TRI_B_UPPER);
+            std::swap(Xd, Sd);
+        }
+        convert<double, T>(*c, nel, Xd, X);
+        gemm<double>(*c, false, false, a, a, a, 1.0, L64[0], a, L64[1], a, 0.0, P64, a, 1, 0, 0, 0,
+                     TRI_A_LOWER | TRI_B_LOWER);
+        gemm<double>(*c, false, false, a, a, a, 1.0, P64, a, L64[2], a, 0.0, G64, a, 1, 0, 0, 0,
+                     TRI_A_LOWER | TRI_B_LOWER);
+        convert<double, T>(*c, (long)a * a, G64, Lp);
+        for (int i = 0; i < 3; ++i) {
+            convert<double, T>(*c, (long)a * a, L64[i], Lf[i]);
+            convert<double, T>(*c, (long)a * a, T64[i], Ti[i]);
+        }
+        o.npass = 3;
+        o.nchol = 3;
     }
 
     // rigorous lower bound of sigma_min(L_0 ... L_{np-1}) from the factors and
@@ -438,8 +509,9 @@ struct Rounder {
                 TT_CUDA(cudaMemcpyAsync(&res2, dsc + 14, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
                 c->sync();
                 const double noise2 = 16.0 * p * ug_fb * ug_fb * r2;
-                if (res2 <= eps * eps + noise2 || rp >= p || attempt >= 6) break;
+                if (res2 <= eps * eps + noise2 || rp >= p || attempt >= 6 || (max_rank > 0 && rp >= max_rank)) break;
                 rp = std::min(p, rp + std::max(1, rp / 8));
+                if (max_rank > 0) rp = std::min(rp, max_rank);
             }
             err2 += res2;
             if (qmul) {
@@ -454,18 +526,23 @@ struct Rounder {
         }
     }
 
-    // truncation rank from sorted singular values (FP64, host)
+    // truncation rank from sorted singular values (FP64, host): the minimal
+    // rank whose discarded tail is within eps, then at most max_rank
     int trunc_rank(const std::vector<double>& s, double eps) {
         const int p = (int)s.size();
+        if (p < 1) return 1;
         std::vector<double> tail(p + 1, 0.0);
         for (int i = p - 1; i >= 0; --i) tail[i] = tail[i + 1] + s[i] * s[i];
         const double e2 = eps * eps;
-        for (int rr = 1; rr <= p; ++rr)
-            if (tail[rr] <= e2) {
-                err2 += tail[rr];
-                return rr;
+        int rr = p;
+        for (int t = 1; t <= p; ++t)
+            if (tail[t] <= e2) {
+                rr = t;
+                break;
             }
-        return std::max(1, p);
+        if (max_rank > 0 && rr > max_rank) rr = max_rank;
+        err2 += tail[rr];
+        return rr;
     }
 
     void rl_sweep() {
@@ -505,9 +582,11 @@ struct Rounder {
             const long NR = (long)n[k + 1] * r[k + 2];
             if (m >= b) {
                 Orth o = orth(false, b, m, core[k], nullptr, nullptr, true);
-                const double lb = o.lb >= 0.0 ? o.lb : sigma_lb(b, o);
+                // a capped bond is truncated whatever its spectrum: no certificate
+                const bool cap = capped(b);
+                const double lb = cap ? 0.0 : (o.lb >= 0.0 ? o.lb : sigma_lb(b, o));
                 if (o.series_pending) {
-                    if (lb > 2.0 * eps && lb > 0.0 && o.e <= skip_budget) {
+                    if (!cap && lb > 2.0 * eps && lb > 0.0 && o.e <= skip_budget) {
                         // certified, and Q1 is orthonormal to ||E||_F: the
                         // bond keeps its rank with core_k = Q1 and
                         // core_{k+1} <- L1^T core_{k+1} (X = Q1 L1^T exactly);
@@ -555,11 +634,12 @@ struct Rounder {
                 chol_inv<T, T>(*c, m, G, Lf[0], Ti[0], 0.0, 8.0 * ug_fb * sqrt((double)m), s);
                 Orth o1{1, 0, false};
                 o1.nchol = 1;
-                double lb = sigma_lb(m, o1);
+                const bool cap = capped(m);
+                double lb = cap ? 0.0 : sigma_lb(m, o1);
                 CholStatus hs0 = read_st(s);
                 const double noise = 16.0 * ug_fb * sqrt((double)m) * hs0.trace;
                 const double lb2 = lb * lb - noise;
-                if (lb > 0.0 && lb2 > 4.0 * eps * eps) {
+                if (!cap && lb > 0.0 && lb2 > 4.0 * eps * eps) {
                     c->stats.certified_bonds++;
                     absorb_next(k, m, X, b, 0);
                     fill_identity<T>(*c, m, core[k], m);
@@ -641,7 +721,8 @@ tt_tensor* finish_round(Rounder<T>& R, const tt_tensor* x, double nrm, double* e
 }
 
 template <class T>
-tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est, void* const* host_out = nullptr) {
+tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est, void* const* host_out = nullptr,
+                   int max_rank = 0) {
     ctx->stats.roundings++;
     if (x->d == 1) {
         if (err_est) *err_est = 0.0;
@@ -654,6 +735,7 @@ tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_es
     for (int attempt = 0;; ++attempt) {
         Rounder<T> R(ctx, x);
         R.host_out = host_out;
+        R.max_rank = max_rank;
         if (attempt > 0) R.series = false;
         // skipped second passes (either sweep) leave cores orthonormal to
         // their ||E||_F; the norm and every truncation then see singular
@@ -705,15 +787,18 @@ size_t round_footprint(const tt_tensor* x, tt_precision prec) {
         out += (x->core_elems(k) * es + 255) & ~size_t(255);  // ranks never grow
     }
     const size_t ws = es == 8 ? Rounder<double>::workspace_bytes(x->d, rmax, cap, es)
-                              : Rounder<float>::workspace_bytes(x->d, rmax, cap, es);
+                              : Rounder<float>::workspace_bytes(x->d, rmax, cap, es) +
+                                    Rounder<float>::fallback64_bytes(rmax, cap);
     return ws + out;
 }
 
-tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est, void* const* host_out) {
+tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est, void* const* host_out,
+                          int max_rank) {
     check_tensor(ctx, x);
     if (!(delta >= 0.0) || !isfinite(delta)) throw_status(TT_ERR_ARG, "delta must be finite and >= 0");
-    if (ctx->prec == TT_FP64) return round_t<double>(ctx, x, delta, err_est, host_out);
-    return round_t<float>(ctx, x, delta, err_est, host_out);
+    if (max_rank < 0) throw_status(TT_ERR_ARG, "max_rank must be >= 0");
+    if (ctx->prec == TT_FP64) return round_t<double>(ctx, x, delta, err_est, host_out, max_rank);
+    return round_t<float>(ctx, x, delta, err_est, host_out, max_rank);
 }
 
 double norm_internal(tt_ctx* ctx, const tt_tensor* x) {
@@ -739,6 +824,15 @@ tt_status tt_round(tt_ctx* ctx, const tt_tensor* x, double delta, tt_tensor** ou
     if (!ctx || !out) throw_status(TT_ERR_ARG, "NULL argument");
     *out = nullptr;
     *out = round_internal(ctx, x, delta, err_est);
+    TT_API_END
+}
+
+tt_status tt_round_capped(tt_ctx* ctx, const tt_tensor* x, double delta, int max_rank, tt_tensor** out,
+                          double* err_est) {
+    TT_API_BEGIN
+    if (!ctx || !out) throw_status(TT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    *out = round_internal(ctx, x, delta, err_est, nullptr, max_rank);
     TT_API_END
 }
 

@@ -227,17 +227,19 @@ tt_tensor* tth_vec(Driver& D, const tt_tensor* a, const std::vector<TensorGuard>
     return normalize(D, w.p, &nw);
 }
 
-// Algorithm 8
-void householder(Driver& D, int m, const tt_tensor* const* A, std::vector<TensorGuard>& Q, double* R) {
+// Algorithm 8, first loop: the Householder TT-vectors u_1..u_m and R (the
+// reflections of the a_j); E receives the canonical e_1..e_m
+void householder_vectors(Driver& D, int m, const tt_tensor* const* A, std::vector<TensorGuard>& E,
+                         std::vector<TensorGuard>& U, double* R) {
     const std::vector<int>& n = A[0]->n;
     double prodn = 1.0;
     for (int v : n) prodn *= v;
     if (prodn < m) throw_status(TT_ERR_ARG, "prod(n) must be >= m for the canonical basis");
-    std::vector<TensorGuard> E(m);
+    E.resize(m);
     for (int j = 0; j < m; ++j) E[j].reset(canonical(D.c, n, j));
     std::vector<Cur> a(m);
     for (int j = 0; j < m; ++j) a[j].p = A[j];
-    std::vector<TensorGuard> U(m);
+    U.resize(m);
     Cur w;
     w.set_owned(D.round(A[0]));
     std::vector<double> r(m);
@@ -250,6 +252,12 @@ void householder(Driver& D, int m, const tt_tensor* const* A, std::vector<Tensor
         }
         if (i < m - 1) w.set_owned(D.round(a[i + 1].p));
     }
+}
+
+// Algorithm 8: the vectors and R, then q_i = H_1 ... H_i e_i, rounded
+void householder(Driver& D, int m, const tt_tensor* const* A, std::vector<TensorGuard>& Q, double* R) {
+    std::vector<TensorGuard> E, U;
+    householder_vectors(D, m, A, E, U, R);
     for (int i = 0; i < m; ++i) {
         Cur q;
         q.p = E[i].get();
@@ -274,6 +282,64 @@ tt_tensor* orth_step_internal(tt_ctx* ctx, tt_scheme scheme, double delta, tt_ro
 }  // namespace ttgb
 
 using namespace ttgb;
+
+extern "C" tt_status tt_canonical(tt_ctx* ctx, int d, const int* n, long j, tt_tensor** out) {
+    TT_API_BEGIN
+    if (!ctx || !out || d < 1 || !n) throw_status(TT_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    double prodn = 1.0;
+    for (int k = 0; k < d; ++k) {
+        if (n[k] < 1) throw_status(TT_ERR_ARG, "mode size < 1");
+        prodn *= n[k];
+    }
+    if (j < 0 || (double)j >= prodn) throw_status(TT_ERR_ARG, "index beyond prod(n)");
+    *out = canonical(ctx, std::vector<int>(n, n + d), j);
+    TT_API_END
+}
+
+extern "C" tt_status tt_householder_vectors(tt_ctx* ctx, double delta, tt_round_policy policy, int m,
+                                            const tt_tensor* const* A, tt_tensor** U, double* R, int* n_rounds) {
+    TT_API_BEGIN
+    if (!ctx || !A || !U || !R || m < 1) throw_status(TT_ERR_ARG, "bad arguments");
+    for (int i = 0; i < m; ++i) U[i] = nullptr;
+    if (!(delta >= 0.0) || !isfinite(delta)) throw_status(TT_ERR_ARG, "delta must be finite and >= 0");
+    if (policy != TT_ROUND_PAPER && policy != TT_ROUND_EVERY_UPDATE) throw_status(TT_ERR_ARG, "bad policy");
+    for (int i = 0; i < m; ++i) {
+        check_tensor(ctx, A[i]);
+        check_same_modes(A[0], A[i]);
+    }
+    Driver D{ctx, delta, policy, 0};
+    std::vector<TensorGuard> E, Ug;
+    std::vector<double> Rh((size_t)m * m, 0.0);
+    householder_vectors(D, m, A, E, Ug, Rh.data());
+    for (size_t e = 0; e < Rh.size(); ++e) R[e] = Rh[e];
+    for (int i = 0; i < m; ++i) U[i] = Ug[i].release();
+    if (n_rounds) *n_rounds = D.nrounds;
+    TT_API_END
+}
+
+extern "C" tt_status tt_householder_apply(tt_ctx* ctx, int k, const tt_tensor* const* U, const tt_tensor* x,
+                                          int transpose, double delta, tt_tensor** out) {
+    TT_API_BEGIN
+    if (!ctx || !out || k < 0 || (k > 0 && !U)) throw_status(TT_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    check_tensor(ctx, x);
+    for (int j = 0; j < k; ++j) {
+        check_tensor(ctx, U[j]);
+        check_same_modes(x, U[j]);
+    }
+    if (isnan(delta) || isinf(delta)) throw_status(TT_ERR_ARG, "delta must be finite");
+    Driver D{ctx, delta, TT_ROUND_PAPER, 0};
+    Cur y;
+    y.p = x;
+    for (int t = 0; t < k; ++t) {
+        const int j = transpose ? t : k - 1 - t;
+        y.set_owned(apply_h(D, y.p, U[j]));
+        if (delta >= 0.0) y.set_owned(D.round(y.p));
+    }
+    *out = y.own.get() ? y.own.release() : copy_tensor(ctx, x);
+    TT_API_END
+}
 
 extern "C" tt_status tt_orthogonalize(tt_ctx* ctx, tt_scheme scheme, double delta, tt_round_policy policy, int m,
                                       const tt_tensor* const* A, tt_tensor** Q, double* R, int* n_rounds) {

@@ -78,6 +78,19 @@ _SIGS = {
     "tt_norm": (_I, [_P, _P, _PD]),
     "tt_round": (_I, [_P, _P, _D, C.POINTER(_P), _PD]),
     "tt_round_to_host": (_I, [_P, _P, _D, C.POINTER(_P), _PD, C.POINTER(_P)]),
+    "tt_round_capped": (_I, [_P, _P, _D, _I, C.POINTER(_P), _PD]),
+    "tt_operator_create": (_I, [_P, _I, _PI, _PI, _PI, C.POINTER(_PD), C.POINTER(_P)]),
+    "tt_operator_laplacian": (_I, [_P, _I, _I, C.POINTER(_P)]),
+    "tt_operator_shape": (_I, [_P, _PI, _PI, _PI, _PI]),
+    "tt_operator_download": (_I, [_P, _P, C.POINTER(_PD)]),
+    "tt_operator_free": (None, [_P]),
+    "tt_matvec": (_I, [_P, _P, _P, C.POINTER(_P)]),
+    "tt_krylov_basis": (_I, [_P, _P, _P, _I, _D, _I, _PP]),
+    "tt_round_gram_svd": (_I, [_P, _P, _D, _I, C.POINTER(_P), _PD]),
+    "tt_round_randomized": (_I, [_P, _P, _P, _D, C.POINTER(_P)]),
+    "tt_canonical": (_I, [_P, _I, _PI, C.c_long, C.POINTER(_P)]),
+    "tt_householder_vectors": (_I, [_P, _D, _I, _I, _PP, _PP, _PD, _PI]),
+    "tt_householder_apply": (_I, [_P, _I, _PP, _P, _I, _D, C.POINTER(_P)]),
     "tt_round_batched": (_I, [_P, _I, _PP, _PD, _PP]),
     "tt_ctx_set_concurrency": (_I, [_P, _I]),
     "tt_ctx_get_concurrency": (_I, [_P]),
@@ -350,6 +363,127 @@ def tt_round(ctx, x, delta):
     e = C.c_double()
     _check(lib().tt_round(ctx.handle, x.handle, float(delta), C.byref(h), C.byref(e)), "tt_round")
     return TT(ctx, h), e.value
+
+
+def tt_round_capped(ctx, x, delta, max_rank):
+    h = _P()
+    e = C.c_double()
+    _check(lib().tt_round_capped(ctx.handle, x.handle, float(delta), int(max_rank), C.byref(h), C.byref(e)),
+           "tt_round_capped")
+    return TT(ctx, h), e.value
+
+
+class Operator:
+    """Handle of a device TT-matrix (tt_operator*) owned by the library."""
+
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def shape(self):
+        d = C.c_int()
+        _check(lib().tt_operator_shape(self._h, C.byref(d), None, None, None), "tt_operator_shape")
+        m = (C.c_int * d.value)()
+        n = (C.c_int * d.value)()
+        R = (C.c_int * (d.value + 1))()
+        _check(lib().tt_operator_shape(self._h, None, m, n, R), "tt_operator_shape")
+        return d.value, list(m), list(n), list(R)
+
+    def cores(self):
+        """Downloads the cores as float64 arrays (R_{k-1}, m_k, n_k, R_k)."""
+        d, m, n, R = self.shape()
+        out = [np.empty((R[k], m[k], n[k], R[k + 1])) for k in range(d)]
+        ptrs = (_PD * d)(*[o.ctypes.data_as(_PD) for o in out])
+        _check(lib().tt_operator_download(self.ctx.handle, self._h, ptrs), "tt_operator_download")
+        return out
+
+    def free(self):
+        if self._h:
+            lib().tt_operator_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def tt_operator_create(ctx, cores):
+    cores = [np.ascontiguousarray(c, dtype=np.float64) for c in cores]
+    d = len(cores)
+    m = (C.c_int * d)(*[c.shape[1] for c in cores])
+    n = (C.c_int * d)(*[c.shape[2] for c in cores])
+    R = (C.c_int * (d + 1))(*([c.shape[0] for c in cores] + [cores[-1].shape[3]]))
+    ptrs = (_PD * d)(*[c.ctypes.data_as(_PD) for c in cores])
+    h = _P()
+    _check(lib().tt_operator_create(ctx.handle, d, m, n, R, ptrs, C.byref(h)), "tt_operator_create")
+    return Operator(ctx, h)
+
+
+def tt_operator_laplacian(ctx, d, n):
+    h = _P()
+    _check(lib().tt_operator_laplacian(ctx.handle, int(d), int(n), C.byref(h)), "tt_operator_laplacian")
+    return Operator(ctx, h)
+
+
+def tt_matvec(ctx, op, x):
+    h = _P()
+    _check(lib().tt_matvec(ctx.handle, op.handle, x.handle, C.byref(h)), "tt_matvec")
+    return TT(ctx, h)
+
+
+def tt_krylov_basis(ctx, op, x1, m, delta=0.0, max_rank=1):
+    out = (_P * m)()
+    _check(lib().tt_krylov_basis(ctx.handle, op.handle, x1.handle, int(m), float(delta), int(max_rank), out),
+           "tt_krylov_basis")
+    return [TT(ctx, _P(out[j])) for j in range(m)]
+
+
+def tt_round_gram_svd(ctx, x, delta, max_rank=0):
+    h = _P()
+    e = C.c_double()
+    _check(lib().tt_round_gram_svd(ctx.handle, x.handle, float(delta), int(max_rank), C.byref(h), C.byref(e)),
+           "tt_round_gram_svd")
+    return TT(ctx, h), e.value
+
+
+def tt_round_randomized(ctx, x, omega, delta=0.0):
+    h = _P()
+    _check(lib().tt_round_randomized(ctx.handle, x.handle, omega.handle, float(delta), C.byref(h)),
+           "tt_round_randomized")
+    return TT(ctx, h)
+
+
+def tt_canonical(ctx, n, j):
+    """e_j (0-based j, i_1 fastest) as a rank-1 TT."""
+    d = len(n)
+    nn = (C.c_int * d)(*n)
+    h = _P()
+    _check(lib().tt_canonical(ctx.handle, d, nn, int(j), C.byref(h)), "tt_canonical")
+    return TT(ctx, h)
+
+
+def tt_householder_vectors(ctx, A, delta, policy="paper"):
+    m = len(A)
+    U = (_P * m)()
+    R = (C.c_double * (m * m))()
+    nr = C.c_int()
+    _check(lib().tt_householder_vectors(ctx.handle, float(delta), POLICY[policy], m, _handles(A), U, R,
+                                        C.byref(nr)), "tt_householder_vectors")
+    Rm = np.array(R[:]).reshape(m, m).T.copy()
+    return [TT(ctx, _P(U[i])) for i in range(m)], Rm, nr.value
+
+
+def tt_householder_apply(ctx, U, x, transpose=False, delta=-1.0):
+    h = _P()
+    _check(lib().tt_householder_apply(ctx.handle, len(U), _handles(U) if U else None, x.handle,
+                                      1 if transpose else 0, float(delta), C.byref(h)), "tt_householder_apply")
+    return TT(ctx, h)
 
 
 def tt_round_to_host(ctx, x, delta, out):

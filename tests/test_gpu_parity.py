@@ -14,6 +14,8 @@ from ttinputs import random_tt, random_tts, coefficients, rank_profile
 
 pytestmark = pytest.mark.gpu
 
+U32 = 2.0 ** -24  # unit round-off of FP32 storage
+
 T = pytest.importorskip("paper_2211_08770_gb300.ttgb")
 
 
@@ -304,18 +306,16 @@ def test_schemes_mixed_loo_and_accuracy(ctxs, scheme):
         Qg, Rg, ng = T.tt_orthogonalize(c, scheme, [up(c, a) for a in A], 1e-5)
         assert ng == no
         loo = T.loss_of_orthogonality(c, Qg)
-        # Section 3.4: LOO = O(delta) for the stable schemes.  A reduced-
-        # precision rounding may keep one singular value fewer or more than
-        # the oracle next to the threshold (ranks within one), which moves a
-        # rounded vector by up to delta ||x|| (the TT-round contract), so the
-        # slack is a small multiple of delta, not delta itself.  Householder
-        # (eq. HH-LOO: a constant times u, here delta): every q_i passes
-        # through the i reflectors built from rounded Householder vectors,
-        # each such rounding may move a reflector by O(delta), so its
-        # constant grows with the basis size m
-        c = len(A) if scheme == "householder" else 2
-        assert loo <= max(10 * loo_o, 1e-6) + c * 1e-5, (prec, loo, loo_o)
-        assert np.allclose(Rg, Ro, atol=1e-4)
+        # within 10x of the oracle's loss of orthogonality, or at the level
+        # an m-vector basis stored in FP32 reaches by itself (10 m u_32; the
+        # oracle's FP64 LOO is far below it here): the stable schemes' LOO is
+        # a constant times the unit round-off (Section 3.4), whose FP32 value
+        # is the floor of any FP32-stored basis
+        m = len(A)
+        assert loo <= max(10 * loo_o, 10 * m * U32), (prec, loo, loo_o)
+        # R: each rounding moves a vector by at most delta (relative), and the
+        # inputs and dots carry FP32 storage rounding
+        assert np.max(np.abs(Rg - Ro)) <= (1e-5 + 10 * m * U32) * np.max(np.abs(Ro))
 
 
 def test_errors(ctxs):
