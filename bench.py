@@ -389,6 +389,12 @@ def run_ours(args):
     out["e2e"] = time_e2e(prec, args.e2e_steps)
     if args.batch_count > 0:
         out["batched"] = time_batched(T, local, prec, args.batch_count, not args.no_fp64)
+    if args.orth_budget > 0:
+        out["orth"] = time_orth(T, local, args.orth_m, args.orth_budget)
+    if args.paper_budget > 0:
+        out["paper_experiments"] = time_paper_experiments(T, local, args.paper_budget)
+    if not args.no_variants:
+        out["variants"] = time_variants(T, local, al, xs, stream)
     if args.serve_count > 0:
         out["serve"] = time_serve(T, local, prec, args.serve_count, args.serve_rate, args.serve_workers)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -446,6 +452,186 @@ def time_batched(T, dev, prec, count, with_fp64):
         res["fp64_value"] = f["value"]
         res["speedup_vs_fp64"] = m["value"] / f["value"]
     return res
+
+
+def _gpu_loo(T, ctx, Q):
+    """||I - Q^T Q||_2 per basis prefix from GPU TT dots (host eigenvalues)."""
+    import numpy as np
+    m = len(Q)
+    G = np.zeros((m, m))
+    for i in range(m):
+        v = T.tt_dot_many(ctx, Q[i], Q[: i + 1])
+        G[i, : i + 1] = v
+        G[: i + 1, i] = v
+    return [float(np.max(np.abs(np.linalg.eigvalsh(np.eye(k) - G[:k, :k])))) for k in range(1, m + 1)]
+
+
+def time_orth(T, dev, m, budget_s):
+    """The recursive ill-conditioned family (order 8, mode 32, rank-10 f_k,
+    a_k = c a_{k-1} + (1 - c) f_k with c = 0.999, formed on the GPU by TT
+    sums) orthogonalized by TT-MGS2 and TT-CGS2 (rounding after every update,
+    delta = 1e-6), mixed and FP64, within a time budget: each arm runs on the
+    first 10, 20, ... inputs (up to m) while the next run is predicted to fit
+    (the cost grows like m^5: m^2 roundings of ranks ~10 m)."""
+    import numpy as np
+    import torch
+    from ttinputs import cfg_orth_recursive
+    t_start = time.perf_counter()
+    F = cfg_orth_recursive(0, m=m)
+    res = {"workload": "recursive family a_k = 0.999 a_(k-1) + 0.001 f_k, d=8, n=32, f_k rank 10 N(0,1); "
+                       "round after every update, delta=1e-6", "runs": []}
+    arms = [(p, s) for p in ("mixed_tf32", "fp64") for s in ("mgs2", "cgs2")]
+    for ai, (prec, scheme) in enumerate(arms):
+        ctx = T.Ctx(dev, prec)
+        Fg = [T.tt_tensor_create(ctx, f) for f in F]
+        A = [Fg[0]]
+        for k in range(1, m):
+            A.append(T.tt_add(ctx, [0.999, 0.001], [A[-1], Fg[k]]))
+        sizes, last, prev = [], None, None
+        for mm in [v for v in (10, 20, 30, 40, 50, 60, 80, 100) if v <= m]:
+            left = budget_s - (time.perf_counter() - t_start)
+            share = left / (len(arms) - ai)  # what this arm may still spend
+            if prev and prev[1] * (mm / prev[0]) ** 5 > share:
+                break
+            ctx.reset_stats()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Q, R, nr = T.tt_orthogonalize(ctx, scheme, A[:mm], 1e-6, "every_update")
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            prev = (mm, dt)
+            sizes.append({"m": mm, "seconds": round(dt, 3)})
+            if last:
+                for q in last[0]:
+                    q.free()
+            last = (Q, nr, dt, ctx.stats(), mm)
+        if last:
+            Q, nr, dt, st, mm = last
+            loo = _gpu_loo(T, ctx, Q)
+            c64 = T.Ctx(dev, "fp64")
+            Ah = [T.tt_tensor_create(c64, a.cores()) for a in A[:mm]]
+            G = np.array([T.tt_dot_many(c64, a, Ah) for a in Ah])
+            ev = np.linalg.eigvalsh(0.5 * (G + G.T))
+            c64.close()
+            res["runs"].append({"precision": prec, "scheme": scheme, "m": mm, "seconds": dt, "roundings": nr,
+                                "roundings_per_s": nr / dt, "loo": loo[-1],
+                                "loo_curve_every_5": [float("%.3g" % v) for v in loo[4::5]],
+                                "kappa": float(np.sqrt(max(ev[-1], 0) / max(ev[0], 1e-300))),
+                                "max_rank": max(max(q.ranks) for q in Q), "svd_calls": int(st["svd_calls"]),
+                                "fallback_orth": int(st["fallback_orth"]), "gpu_launches": int(st["kernel_launches"]),
+                                "host_syncs": int(st["host_syncs"]), "sizes_timed": sizes})
+            for q in Q:
+                q.free()
+        ctx.close()
+    res["seconds_total"] = time.perf_counter() - t_start
+    return res
+
+
+def time_paper_experiments(T, dev, budget_s):
+    """The paper's own inputs (Section 4): Krylov vectors of the ones tensor
+    under the Dirichlet Laplacian TT-matrix, each rounded to TT-rank 1 and
+    normalised, generated on the GPU; the six schemes at delta in {1e-3,
+    1e-5, 1e-8}, FP64 and mixed, order 3 (n = 15, m = 20) and order 6
+    (n = 15, m = 35, within the budget); the loss of orthogonality at the
+    last basis size, its curve, and the largest TT-rank of the basis."""
+    import torch
+    t_start = time.perf_counter()
+    out = {"inputs": "Krylov: x_1 = ones, a_j = normalised rank-1 TT-round of x_j, x_(j+1) = -Laplacian a_j", "runs": []}
+    for d, n, m in ((3, 15, 20), (6, 15, 35)):
+        for prec in ("fp64", "mixed_tf32"):
+            ctx = T.Ctx(dev, prec)
+            op = T.tt_operator_laplacian(ctx, d, n)
+            ones = T.tt_tensor_create(ctx, [__import__("numpy").ones((1, n, 1)) for _ in range(d)])
+            t0 = time.perf_counter()
+            A = T.tt_krylov_basis(ctx, op, ones, m, 0.0, 1)
+            torch.cuda.synchronize()
+            t_gen = time.perf_counter() - t0
+            for delta in (1e-3, 1e-5, 1e-8):
+                for scheme in ("cgs", "mgs", "cgs2", "mgs2", "gram", "householder"):
+                    if time.perf_counter() - t_start > budget_s:
+                        out["truncated_by_budget"] = True
+                        break
+                    k = m
+                    t0 = time.perf_counter()
+                    while True:
+                        try:
+                            Q, R, nr = T.tt_orthogonalize(ctx, scheme, A[:k], delta)
+                            break
+                        except T.TTError as e:
+                            if e.name != "TT_ERR_NOT_SPD" or k <= 1:
+                                raise
+                            k -= 1
+                    dt = time.perf_counter() - t0
+                    loo = _gpu_loo(T, ctx, Q)
+                    out["runs"].append({"d": d, "n": n, "m": k, "precision": prec, "delta": delta, "scheme": scheme,
+                                        "seconds": dt, "roundings": nr, "loo_last": loo[-1],
+                                        "loo_curve": [float("%.3g" % v) for v in loo],
+                                        "max_rank": max(max(q.ranks) for q in Q), "krylov_seconds": t_gen})
+                    for q in Q:
+                        q.free()
+            ctx.close()
+    out["seconds_total"] = time.perf_counter() - t_start
+    return out
+
+
+def time_variants(T, dev, al, xs, stream):
+    """Rounding variants on the single-rounding workload: Gram-SVD rounding
+    (FP64), randomized rounding with a Gaussian sketch of ranks 400 (mixed,
+    exact at that rank), both against tt_round on the same input; and the
+    TT matrix-vector product of the Dirichlet Laplacian (d = 10, n = 64)
+    with the rank-400 sum (mixed), against the HBM roofline."""
+    import numpy as np
+    import torch
+    from ttinputs import random_tt
+    peaks, _ = load_peaks()
+    out = {}
+    d, n = len(xs[0]), xs[0][0].shape[1]
+
+    def timed(f, reps):
+        f()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            y = f()
+            torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps, y
+
+    c64 = T.Ctx(dev, "fp64", stream=stream.cuda_stream)
+    X64 = [T.tt_tensor_create(c64, c) for c in xs]
+    x64 = T.tt_add(c64, al, X64)
+    t_g, yg = timed(lambda: T.tt_round_gram_svd(c64, x64, DELTA)[0], 2)
+    t_r, yr = timed(lambda: T.tt_round(c64, x64, DELTA)[0], 2)
+    diff = T.tt_add(c64, [1.0, -1.0], [yg, yr])
+    out["gram_svd_fp64"] = {"roundings_per_s": 1.0 / t_g, "tt_round_fp64_roundings_per_s": 1.0 / t_r,
+                            "rel_diff_vs_tt_round": T.tt_norm(c64, diff) / T.tt_norm(c64, x64),
+                            "output_ranks": yg.ranks}
+    cm = T.Ctx(dev, "mixed_tf32", stream=stream.cuda_stream)
+    Xm = [T.tt_tensor_create(cm, c) for c in xs]
+    xm = T.tt_add(cm, al, Xm)
+    om = T.tt_tensor_create(cm, random_tt(np.random.default_rng(77), [n] * d, [1] + [400] * (d - 1) + [1]))
+    t_rand, yrand = timed(lambda: T.tt_round_randomized(cm, xm, om), 3)
+    t_det, _ = timed(lambda: T.tt_round(cm, xm, DELTA)[0], 3)
+    y64 = T.tt_tensor_create(c64, yrand.cores())
+    diff = T.tt_add(c64, [1.0, -1.0], [x64, y64])
+    out["randomized_mixed"] = {"sketch_ranks": 400, "roundings_per_s": 1.0 / t_rand,
+                               "tt_round_mixed_roundings_per_s": 1.0 / t_det,
+                               "rel_error": T.tt_norm(c64, diff) / T.tt_norm(c64, x64), "output_ranks": yrand.ranks}
+    op = T.tt_operator_laplacian(cm, d, n)
+    cm.reset_profile()
+    cm.set_profiling(True, family="matvec_f32")
+    t_mv, ymv = timed(lambda: T.tt_matvec(cm, op, xm), 5)
+    prof = cm.profile().get("matvec_f32")
+    cm.set_profiling(False)
+    if prof:
+        gbs = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
+        out["matvec_mixed"] = {"operator": "Dirichlet Laplacian TT-matrix (ranks 2), d=10, n=64",
+                               "input_ranks": xm.ranks, "output_ranks": ymv.ranks, "seconds": t_mv,
+                               "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                            "frac": gbs / peaks["hbm_gbs"], "launches": prof["launches"],
+                                            "avg_launch_ms": prof["total_ms"] / max(1, prof["launches"])}}
+    c64.close()
+    cm.close()
+    return out
 
 
 def time_serve(T, dev, prec, count, rate, workers):
@@ -513,6 +699,10 @@ def main():
     ap.add_argument("--serve-count", type=int, default=64)
     ap.add_argument("--serve-rate", type=float, default=0.0)
     ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--orth-m", type=int, default=50, help="inputs of the recursive-family orthogonalization")
+    ap.add_argument("--orth-budget", type=float, default=90.0, help="seconds for the orthogonalization runs (0: skip)")
+    ap.add_argument("--paper-budget", type=float, default=60.0, help="seconds for the paper's experiments (0: skip)")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -62,7 +62,7 @@ typedef enum {
  *                context is created); small r x r factorizations in FP32;
  *                norm, thresholds and tail sums in FP64; truncation SVDs in
  *                FP64 (FP32 column Jacobi with an FP64-measured residual
- *                guard for ranks >= 96).
+ *                guard for ranks >= 32).
  * TT_FP32:       cores and every GEMM in FP32 on CUDA cores (no tensor
  *                cores); small factorizations as TT_MIXED_TF32. */
 typedef enum { TT_FP64 = 0, TT_MIXED_TF32 = 1, TT_FP32 = 2 } tt_precision;

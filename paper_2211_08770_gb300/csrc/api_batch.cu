@@ -45,6 +45,7 @@ std::vector<Ctx*> get_lanes(Ctx& root, int count) {
         l->use_tc_gemm = root.use_tc_gemm;
         l->tc_gemm_split = root.tc_gemm_split;
         l->tc_wait_limit = root.tc_wait_limit;
+        l->use_tc_absorb = root.use_tc_absorb;
         l->chol_nb = root.chol_nb;
         l->use_series = root.use_series;
         l->series_force_retry = root.series_force_retry;

@@ -36,7 +36,11 @@ void check_same_modes(const tt_tensor* a, const tt_tensor* b);
 void check_tensor(tt_ctx* ctx, const tt_tensor* x);
 tt_tensor* tt_add_internal(tt_ctx* ctx, int m, const double* alpha, const tt_tensor* const* x);
 tt_tensor* scale_internal(tt_ctx* ctx, const tt_tensor* x, double alpha);
-void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out);
+// stacked: FP32 storage may take the stacked FP32 contraction of all pairs
+// (FP32 products and chunk sums, FP64 across chunks) instead of the FP64
+// contraction of each pair (count >= 2; FP64 storage is unaffected)
+void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out,
+                       bool stacked = false);
 tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est,
                           void* const* host_out = nullptr, int max_rank = 0);
 double norm_internal(tt_ctx* ctx, const tt_tensor* x);
@@ -45,8 +49,12 @@ void rehome(tt_tensor* t, Ctx& root);
 // One outer iteration of Algorithms 1-4 (scheme TT_CGS, TT_MGS, TT_CGS2 or
 // TT_MGS2) for a against the orthonormal Q[0..k-1]: returns the new basis
 // vector; col[0..k] receives R(0..k, k).
+// qgram (may be NULL, leading dimension ldg): the Gram matrix of Q, which
+// lets the modified schemes take all projections of a pass from one batched
+// set of dots (see gs_step).
 tt_tensor* orth_step_internal(tt_ctx* ctx, tt_scheme scheme, double delta, tt_round_policy policy,
-                              const tt_tensor* a, int k, const tt_tensor* const* Q, double* col, int* nrounds);
+                              const tt_tensor* a, int k, const tt_tensor* const* Q, double* col, int* nrounds,
+                              const double* qgram = nullptr, int ldg = 0);
 // device bytes a rounding of x may hold at once: workspace plus output
 size_t round_footprint(const tt_tensor* x, tt_precision prec);
 void round_batched_internal(tt_ctx* ctx, int count, const tt_tensor* const* x, const double* delta, tt_tensor** out);

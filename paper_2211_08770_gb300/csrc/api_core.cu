@@ -372,7 +372,152 @@ void dot_many_f32_acc64(tt_ctx* ctx, const tt_tensor* x, int count, const tt_ten
     for (int j = 0; j < count; ++j) out[j] = h[j];
 }
 
-void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out) {
+// ---------------------------------------------------------------- stacked dots
+// <x, y_j> for all j at once: the contractions of all pairs advance
+// together, core by core.  W (rx x S, FP64) holds the pairs' W_j side by
+// side (S = sum_j ry_j).  Step A: V (rx n x S', storage type) with
+// V[(a n + i), off'_j + q] = sum_b W[a, off_j + b] Y_j(b, i, q) (FP64 sums of
+// ry_j terms).  Step B: W' = X_k^L^T V, one GEMM over all pairs, so X's
+// cores are read once for all pairs (the pair-by-pair chains read them once
+// per pair, in two small launches per core each).  FP64 storage: one FP64
+// GEMM.  FP32 storage: FP32 GEMMs over chunks of kDotChunk rows of X^L whose
+// partial products are summed in FP64, so each coefficient carries FP32
+// products and FP32 sums of at most kDotChunk terms (about 1e-6 of the sum
+// of the terms' magnitudes).
+namespace {
+constexpr int kDotChunk = 256;
+
+template <class T>
+struct PairCols {
+    const T* y;     // core k of y_j
+    int ry, ry2;    // its ranks
+    int off, off2;  // its column offsets in W and V
+};
+
+template <class T>
+__global__ void stack_a_kernel(const double* __restrict__ W, int S, const PairCols<T>* __restrict__ pairs,
+                               int npairs, int rx, int n, int S2, T* __restrict__ V) {
+    const long total = (long)rx * n * S2;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int col = (int)(t % S2);
+        const long row = t / S2;
+        const int i = (int)(row % n), a = (int)(row / n);
+        int lo = 0, hi = npairs - 1;  // the pair whose columns hold col
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pairs[mid].off2 <= col) lo = mid;
+            else hi = mid - 1;
+        }
+        const PairCols<T> pc = pairs[lo];
+        const int q = col - pc.off2;
+        const double* w = W + (long)a * S + pc.off;
+        const T* y = pc.y + (long)i * pc.ry2 + q;  // Y(b, i, q) at y[b n ry2]
+        double acc = 0.0;
+        for (int b = 0; b < pc.ry; ++b) acc += w[b] * (double)y[(long)b * n * pc.ry2];
+        V[t] = (T)acc;
+    }
+}
+
+template <class T>
+__global__ void sum_chunks_kernel(const T* __restrict__ P, long chunk_elems, int nchunks, double* __restrict__ out) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < chunk_elems; e += (long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < nchunks; ++c) acc += (double)P[(long)c * chunk_elems + e];
+        out[e] = acc;
+    }
+}
+
+unsigned grid_of(const Ctx& c, long total, int threads) {
+    const long want = (total + threads - 1) / threads;
+    return (unsigned)std::max(1L, std::min(want, (long)std::max(1, c.sm_count) * 8));
+}
+}  // namespace
+
+template <class T>
+void dot_many_stacked(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out) {
+    const bool f32 = sizeof(T) == 4;
+    const int d = x->d;
+    size_t wmax = 1, vmax = 1, pmax = 1;
+    for (int k = 0; k < d; ++k) {
+        long S = 0, S2 = 0;
+        for (int j = 0; j < count; ++j) {
+            S += y[j]->r[k];
+            S2 += y[j]->r[k + 1];
+        }
+        if (S2 > (1L << 24) || S > (1L << 24)) throw_status(TT_ERR_ARG, "tt_dot_many: too many stacked columns");
+        const long K = (long)x->r[k] * x->n[k];
+        const long nch = f32 ? (K + kDotChunk - 1) / kDotChunk : 1;
+        wmax = std::max(wmax, (size_t)x->r[k] * S);
+        wmax = std::max(wmax, (size_t)x->r[k + 1] * S2);
+        vmax = std::max(vmax, (size_t)K * S2);
+        pmax = std::max(pmax, (size_t)nch * x->r[k + 1] * S2);
+    }
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t bytes =
+        2 * al(wmax * 8) + al(vmax * sizeof(T)) + al(pmax * sizeof(T)) + al((size_t)count * sizeof(PairCols<T>)) + 512;
+    char* ws = (char*)ctx->alloc(bytes);
+    struct Rel {
+        tt_ctx* c; void* p; size_t b;
+        ~Rel() { c->release(p, b); }
+    } rel{ctx, ws, bytes};
+    char* p = ws;
+    double* W = (double*)p; p += al(wmax * 8);
+    double* W2 = (double*)p; p += al(wmax * 8);
+    T* V = (T*)p; p += al(vmax * sizeof(T));
+    T* P = (T*)p; p += al(pmax * sizeof(T));
+    PairCols<T>* dpairs = (PairCols<T>*)p;
+    std::vector<PairCols<T>> hp(count);
+    {
+        // W_0 = 1 for every pair (r_0 = 1); a pageable source is staged
+        // before the call returns
+        std::vector<double> ones(count, 1.0);
+        TT_CUDA(cudaMemcpyAsync(W, ones.data(), count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    for (int k = 0; k < d; ++k) {
+        const int rx = x->r[k], rx2 = x->r[k + 1], n = x->n[k];
+        int S = 0, S2 = 0;
+        for (int j = 0; j < count; ++j) {
+            hp[j] = PairCols<T>{(const T*)y[j]->cores[k], y[j]->r[k], y[j]->r[k + 1], S, S2};
+            S += y[j]->r[k];
+            S2 += y[j]->r[k + 1];
+        }
+        // pageable source: the copy is staged before the call returns, and
+        // it lands after the previous core's step A (stream order)
+        TT_CUDA(cudaMemcpyAsync(dpairs, hp.data(), count * sizeof(PairCols<T>), cudaMemcpyHostToDevice, ctx->stream));
+        const long K = (long)rx * n;
+        {
+            ProfScope ps(*ctx, "dot_stack", 2.0 * (double)K * S2 * 4.0, sizeof(T) * (double)K * S2);
+            stack_a_kernel<T><<<grid_of(*ctx, K * S2, 256), 256, 0, ctx->stream>>>(W, S, dpairs, count, rx, n, S2, V);
+            TT_LAUNCHED(*ctx);
+        }
+        const T* X = (const T*)x->cores[k];
+        const long ce = (long)rx2 * S2;
+        int nch = 1;
+        if (f32) {
+            // W' (rx2 x S2) = X^L^T V in chunks of K, FP64 sum of the chunks
+            const long nfull = K / kDotChunk, rem = K - nfull * kDotChunk;
+            if (nfull > 0)
+                gemm<T>(*ctx, true, false, rx2, S2, kDotChunk, T(1), X, rx2, V, S2, T(0), P, S2, (int)nfull,
+                        (long)kDotChunk * rx2, (long)kDotChunk * S2, ce);
+            if (rem > 0)
+                gemm<T>(*ctx, true, false, rx2, S2, (int)rem, T(1), X + nfull * kDotChunk * rx2, rx2,
+                        V + nfull * kDotChunk * S2, S2, T(0), P + nfull * ce, S2);
+            nch = (int)(nfull + (rem > 0 ? 1 : 0));
+        } else {
+            gemm<T>(*ctx, true, false, rx2, S2, (int)K, T(1), X, rx2, V, S2, T(0), P, S2);
+        }
+        sum_chunks_kernel<T><<<grid_of(*ctx, ce, 256), 256, 0, ctx->stream>>>(P, ce, nch, W2);
+        TT_LAUNCHED(*ctx);
+        std::swap(W, W2);
+    }
+    std::vector<double> h(count);
+    TT_CUDA(cudaMemcpyAsync(h.data(), W, sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->sync();
+    for (int j = 0; j < count; ++j) out[j] = h[j];
+}
+
+void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out,
+                       bool stacked) {
     check_tensor(ctx, x);
     if (count < 0 || (count > 0 && (!y || !out))) throw_status(TT_ERR_ARG, "tt_dot_many: bad arguments");
     for (int j = 0; j < count; ++j) {
@@ -380,8 +525,14 @@ void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tens
         check_same_modes(x, y[j]);
     }
     if (count == 0) return;
-    if (ctx->prec == TT_FP64) dot_many_impl<double>(ctx, x, count, y, out);
-    else dot_many_f32_acc64(ctx, x, count, y, out);
+    if (stacked && count >= 2) {
+        if (ctx->prec == TT_FP64) dot_many_stacked<double>(ctx, x, count, y, out);
+        else dot_many_stacked<float>(ctx, x, count, y, out);
+    } else if (ctx->prec == TT_FP64) {
+        dot_many_impl<double>(ctx, x, count, y, out);
+    } else {
+        dot_many_f32_acc64(ctx, x, count, y, out);  // FP64 accumulation throughout
+    }
 }
 
 }  // namespace ttgb
@@ -417,6 +568,8 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     // ~2^-22 per product); unset or 0 keeps them on CUDA cores
     const char* tg = getenv("TTGB_TC_GEMM");
     if (tg && tg[0] == '3') c->use_tc_gemm = true;
+    // =a: only the absorbs (three-part split) on the tensor cores
+    if (tg && tg[0] == 'a') c->use_tc_absorb = true;
     if (tg && tg[0] == '2') {
         c->use_tc_gemm = true;
         c->tc_gemm_split = 2;

@@ -167,9 +167,9 @@ struct Rounder {
     // C = op(A) op(B): tensor-core split TF32 when the context allows it and
     // the layout is TMA-aligned, else the CUDA-core kernel of the storage type
     void mm(bool tA, bool tB, int M, int N, int K, const T* A, long lda, const T* B, long ldb, T* C, long ldc,
-            int tri = 0) {
+            int tri = 0, bool absorb = false) {
         if constexpr (sizeof(T) == 4) {
-            if (tc && c->use_tc_gemm && !tA &&
+            if (tc && (c->use_tc_gemm || (absorb && c->use_tc_absorb)) && !tA &&
                 gemm_tc3_tf32(*c, tB, M, N, K, (const float*)A, lda, (const float*)B, ldb, (float*)C, ldc,
                               c->tc_gemm_split))
                 return;
@@ -455,7 +455,7 @@ struct Rounder {
             tri = 0;
             pend[k + 1] = 0;
         }
-        mm(false, false, rows, (int)NR, b, M, ldm, core[k + 1], NR, spare, NR, tri);
+        mm(false, false, rows, (int)NR, b, M, ldm, core[k + 1], NR, spare, NR, tri, true);
         std::swap(core[k + 1], spare);
     }
 
@@ -467,9 +467,10 @@ struct Rounder {
     // rank raised until it is <= eps, so the rounding bound holds whatever
     // the FP32 SVD's accuracy; FP32 rotations only cost optimality of the
     // rank near the threshold.  Used for p >= kSvd32Min, where the FP64
-    // multi-CTA Jacobi takes tens of milliseconds.  qmul: core_k <- core_k U_r
+    // Jacobi (FP64 runs at 1/64 of the FP32 rate here) takes milliseconds
+    // per bond.  qmul: core_k <- core_k U_r
     // (else core_k <- U_r, when Q = I).  False: not taken (nothing done).
-    static constexpr int kSvd32Min = 96;
+    static constexpr int kSvd32Min = 32;
     static constexpr long kTc2MinK = 4096;
     bool trunc_f32(int m, int p, int b, const T* Wsrc, long ldw, const T* R, double eps, int k, long NR,
                    bool qmul) {
@@ -559,7 +560,7 @@ struct Rounder {
             } else {
                 const Orth o = orth(true, a, K, core[k], Pend + (size_t)k * rmax * rmax, &skip_budget);
                 pend[k] = o.deferred;
-                mm(false, false, M, a, a, core[k - 1], a, Lp, a, spare, a, o.lower ? TRI_B_LOWER : 0);
+                mm(false, false, M, a, a, core[k - 1], a, Lp, a, spare, a, o.lower ? TRI_B_LOWER : 0, true);
                 std::swap(core[k - 1], spare);
             }
         }

@@ -63,8 +63,14 @@ tt_tensor* normalize(Driver& D, const tt_tensor* p, double* nrm_out) {
 // Rounding follows the policy: TT_ROUND_PAPER rounds once per pass (and the
 // first vector, i = 0, is rounded in both policies); TT_ROUND_EVERY_UPDATE
 // after every axpy.
+// qgram (may be NULL): the Gram matrix <q_j', q_j> of Q (row-major, leading
+// dimension ldg).  With it, a modified pass under the paper policy computes
+// its coefficients from one batched set of dots: the running vector of
+// Algorithms 2 and 4 is p_prev - sum_{j'<j} r_j' q_j', so by linearity
+// r_j = <p_prev, q_j> - sum_{j'<j} r_j' <q_j', q_j>, and the i updates are one
+// concatenation (the same TT as the successive axpys).
 tt_tensor* gs_step(Driver& D, const tt_tensor* a, int i, const tt_tensor* const* Q, double* col, bool modified,
-                   bool twice) {
+                   bool twice, const double* qgram = nullptr, int ldg = 0) {
     for (int j = 0; j <= i; ++j) col[j] = 0.0;
     Cur prev;
     prev.p = a;
@@ -74,13 +80,17 @@ tt_tensor* gs_step(Driver& D, const tt_tensor* a, int i, const tt_tensor* const*
     for (int k = 0; k < (twice ? 2 : 1); ++k) {
         Cur p;
         p.p = prev.p;
-        if (!modified && i > 0) {
+        const bool linear_mgs = modified && qgram && D.pol == TT_ROUND_PAPER && i > 0;
+        if ((!modified || linear_mgs) && i > 0) {
             // classical: every projection is against the same vector, so the
             // i dots are one batched call; with one rounding per pass the
             // i axpys are one concatenation [p, q_0, ..., q_{i-1}] with
             // coefficients (1, -r_0, ..., -r_{i-1}), the same TT the
             // successive axpys build
-            dot_many_internal(D.c, prev.p, i, Q, rk.data());
+            dot_many_internal(D.c, prev.p, i, Q, rk.data(), true);
+            if (linear_mgs)
+                for (int j = 0; j < i; ++j)
+                    for (int jp = 0; jp < j; ++jp) rk[j] -= rk[jp] * qgram[(size_t)jp * ldg + j];
             if (D.pol == TT_ROUND_PAPER) {
                 al[0] = 1.0;
                 xs[0] = prev.p;
@@ -269,12 +279,13 @@ void householder(Driver& D, int m, const tt_tensor* const* A, std::vector<Tensor
 }  // namespace
 
 tt_tensor* orth_step_internal(tt_ctx* ctx, tt_scheme scheme, double delta, tt_round_policy policy,
-                              const tt_tensor* a, int k, const tt_tensor* const* Q, double* col, int* nrounds) {
+                              const tt_tensor* a, int k, const tt_tensor* const* Q, double* col, int* nrounds,
+                              const double* qgram, int ldg) {
     if (scheme != TT_CGS && scheme != TT_MGS && scheme != TT_CGS2 && scheme != TT_MGS2)
         throw_status(TT_ERR_ARG, "an orthogonalization step takes TT_CGS, TT_MGS, TT_CGS2 or TT_MGS2");
     Driver D{ctx, delta, policy, 0};
     tt_tensor* q = gs_step(D, a, k, Q, col, scheme == TT_MGS || scheme == TT_MGS2,
-                           scheme == TT_CGS2 || scheme == TT_MGS2);
+                           scheme == TT_CGS2 || scheme == TT_MGS2, qgram, ldg);
     if (nrounds) *nrounds = D.nrounds;
     return q;
 }

@@ -48,10 +48,17 @@ struct Request {
     std::string msg;
     tt_tensor* out = nullptr;
     std::vector<double> coef;
-    // the first k vectors of the basis, copied when the request is admitted
-    // (under the server's mutex): the worker never reads the list of bases,
-    // which tt_server_add_basis may grow at the same time
+    // the first k vectors of the basis and their Gram matrix, copied when
+    // the request is admitted (under the server's mutex): the worker never
+    // reads the list of bases, which tt_server_add_basis may grow meanwhile
     std::vector<const tt_tensor*> basis_vecs;
+    std::vector<double> basis_gram;  // k x k
+};
+
+// a resident basis: its vectors and their Gram matrix <q_i, q_j> (k x k)
+struct Basis {
+    std::vector<tt_tensor*> q;
+    std::vector<double> gram;
 };
 
 size_t tensor_bytes(const tt_tensor* x, size_t es) {
@@ -71,7 +78,7 @@ struct tt_server {
     std::deque<Request*> queue;
     std::map<uint64_t, Request*> reqs;
     // a deque: appending a basis moves none of the existing ones
-    std::deque<std::vector<tt_tensor*>> bases;
+    std::deque<Basis> bases;
     size_t budget = 0, in_use = 0, peak = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -101,7 +108,7 @@ struct tt_server {
         if (q.kind == TT_REQ_ROUND) return round_footprint(q.x, root->prec) + (1u << 20);
         // the concatenated sum x - sum_j r_j q_j: ranks add up bond by bond
         const tt_tensor* x = q.x;
-        const std::vector<tt_tensor*>& B = bases[q.basis];
+        const std::vector<tt_tensor*>& B = bases[q.basis].q;
         std::vector<int> r(x->r);
         for (int j = 0; j < q.k; ++j)
             for (int b = 1; b < x->d; ++b) r[b] += B[j]->r[b];
@@ -114,6 +121,20 @@ struct tt_server {
         // the normalised copy, and FP64 copies for the projections when FP32
         size_t b = 2 * sb + round_footprint(&S, root->prec) + sb;
         if (es == 4) b += 2 * tensor_bytes(&S, 8);
+        // the stacked dots of a pass (x at most the concatenation's ranks)
+        size_t wmax = 1, vmax = 1, pmax = 1;
+        for (int c = 0; c < x->d; ++c) {
+            size_t Sc = 0, Sc2 = 0;
+            for (int j = 0; j < q.k; ++j) {
+                Sc += B[j]->r[c];
+                Sc2 += B[j]->r[c + 1];
+            }
+            const size_t K = (size_t)r[c] * x->n[c];
+            wmax = std::max(wmax, std::max((size_t)r[c] * Sc, (size_t)r[c + 1] * Sc2));
+            vmax = std::max(vmax, K * Sc2);
+            pmax = std::max(pmax, ((K + 255) / 256) * r[c + 1] * Sc2);
+        }
+        b += 2 * wmax * 8 + (vmax + pmax) * es;
         return b + (1u << 20);
     }
 
@@ -126,7 +147,8 @@ struct tt_server {
             } else {
                 q->coef.assign(q->k + 1, 0.0);
                 q->out = orth_step_internal(l, q->scheme, q->delta, TT_ROUND_PAPER, q->x, q->k,
-                                            q->basis_vecs.data(), q->coef.data(), nullptr);
+                                            q->basis_vecs.data(), q->coef.data(), nullptr,
+                                            q->basis_gram.data(), q->k);
             }
             lane->sync();  // the result is complete on the device
             rehome(q->out, *root);
@@ -161,8 +183,12 @@ struct tt_server {
                 q->running = true;
                 q->t_start = mono_now();
                 if (q->kind == TT_REQ_ORTH_STEP) {
-                    const std::vector<tt_tensor*>& B = bases[q->basis];
-                    q->basis_vecs.assign(B.begin(), B.begin() + q->k);
+                    const Basis& B = bases[q->basis];
+                    const int kb = (int)B.q.size();
+                    q->basis_vecs.assign(B.q.begin(), B.q.begin() + q->k);
+                    q->basis_gram.resize((size_t)q->k * q->k);
+                    for (int i = 0; i < q->k; ++i)
+                        for (int j = 0; j < q->k; ++j) q->basis_gram[(size_t)i * q->k + j] = B.gram[(size_t)i * kb + j];
                 }
             }
             run(lane, q);
@@ -212,6 +238,7 @@ tt_status tt_server_create(tt_ctx* ctx, int workers, size_t footprint_budget, tt
         l->use_tc_gemm = ctx->use_tc_gemm;
         l->tc_gemm_split = ctx->tc_gemm_split;
         l->tc_wait_limit = ctx->tc_wait_limit;
+        l->use_tc_absorb = ctx->use_tc_absorb;
         cudaError_t e = cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaMalloc(&l->tc_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(l->tc_err, 0, sizeof(int));
@@ -247,11 +274,20 @@ tt_status tt_server_add_basis(tt_server* s, int k, const tt_tensor* const* q, in
         check_tensor(s->root, q[j]);
         check_same_modes(q[0], q[j]);
     }
-    std::vector<tt_tensor*> B;
+    Basis B;
     try {
-        for (int j = 0; j < k; ++j) B.push_back(copy_tensor(s->root, q[j]));
+        for (int j = 0; j < k; ++j) B.q.push_back(copy_tensor(s->root, q[j]));
+        // <q_i, q_j> once per basis: the modified schemes' projections of a
+        // step are then formed from one batched set of dots (gs_step)
+        B.gram.assign((size_t)k * k, 0.0);
+        std::vector<const tt_tensor*> qs(B.q.begin(), B.q.end());
+        std::vector<double> row(k);
+        for (int i = 0; i < k; ++i) {
+            dot_many_internal(s->root, B.q[i], i + 1, qs.data(), row.data(), true);
+            for (int j = 0; j <= i; ++j) B.gram[(size_t)i * k + j] = B.gram[(size_t)j * k + i] = row[j];
+        }
     } catch (...) {
-        for (auto* t : B) free_tensor(t);
+        for (auto* t : B.q) free_tensor(t);
         throw;
     }
     std::lock_guard<std::mutex> lk(s->mu);
@@ -276,8 +312,8 @@ tt_status tt_server_submit(tt_server* s, tt_request_kind kind, const tt_tensor* 
             throw_status(TT_ERR_ARG, "an orthogonalization step takes TT_CGS, TT_MGS, TT_CGS2 or TT_MGS2");
         std::lock_guard<std::mutex> lk(s->mu);
         if (basis_id < 0 || basis_id >= (int)s->bases.size()) throw_status(TT_ERR_ARG, "unknown basis");
-        if (k < 0 || k > (int)s->bases[basis_id].size()) throw_status(TT_ERR_ARG, "k exceeds the basis size");
-        if (k > 0) check_same_modes(s->bases[basis_id][0], x);
+        if (k < 0 || k > (int)s->bases[basis_id].q.size()) throw_status(TT_ERR_ARG, "k exceeds the basis size");
+        if (k > 0) check_same_modes(s->bases[basis_id].q[0], x);
         q->basis = basis_id;
         q->k = k;
         q->scheme = scheme;
@@ -400,7 +436,7 @@ void tt_server_destroy(tt_server* s) {
         delete q;
     }
     for (auto& B : s->bases)
-        for (auto* t : B) free_tensor(t);
+        for (auto* t : B.q) free_tensor(t);
     for (Ctx* l : s->lanes) {
         cudaStreamSynchronize(l->stream);
         delete static_cast<tt_ctx*>(l);

@@ -242,6 +242,9 @@ struct Ctx {
     // delta = 1e-6 against 1.06e-6 with the CUDA-core FP32 GEMM)
     bool use_tc_gemm = false;
     int tc_gemm_split = 3;    // 3: hi + mid + lo (6 products), 2: hi + lo (3 products)
+    // the absorbs alone (core_{k-1} L, R core_{k+1}: no explicit inverse, no
+    // cancellation) on the split-TF32 tensor-core GEMM
+    bool use_tc_absorb = false;
     int* tc_err = nullptr;  // device flag: a bounded wait of a tensor-core kernel ran out
     long long tc_wait_limit = 0;  // SM cycles of the row Gram's bounded waits (0: ~2 s)
     // lifetime: one reference for the owner plus one per live tensor; the
