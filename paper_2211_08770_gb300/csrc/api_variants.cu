@@ -71,6 +71,17 @@ int trunc_rank_host(const std::vector<double>& s, double eps, int max_rank, doub
     return rr;
 }
 
+// x *= 1 / sqrt(*ss) when *ss > 0 (a device sum of squares): rescales a
+// sketch contraction without a host round trip
+template <class T>
+__global__ void scale_rsqrt_kernel(T* __restrict__ x, long n, const double* __restrict__ ss) {
+    const double v = *ss;
+    if (!(v > 0.0) || !isfinite(v)) return;
+    const double f = 1.0 / sqrt(v);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        x[i] = (T)((double)x[i] * f);
+}
+
 template <class T>
 void read_status(tt_ctx* c, const CholStatus* st, int n) {
     std::vector<CholStatus> h(n);
@@ -226,7 +237,8 @@ tt_tensor* randomized_t(tt_ctx* c, const tt_tensor* x, const tt_tensor* om, doub
     cap = std::max(cap, zmax);
     const size_t ll = (size_t)lmax * lmax;
     const size_t bytes = (d + 3) * al256(cap * sizeof(T)) + (d + 1) * al256(wmax * sizeof(T)) +
-                         3 * al256(ll * sizeof(T)) + al256((3 * d + 3) * sizeof(CholStatus)) + 4096;
+                         3 * al256(ll * sizeof(T)) + al256((3 * d + 3) * sizeof(CholStatus)) +
+                         al256((d + 1) * sizeof(double)) + 4096;
     Work<T> w(c, bytes);
     std::vector<T*> core(d), W(d + 1, nullptr);
     for (int k = 0; k < d; ++k) {
@@ -241,13 +253,26 @@ tt_tensor* randomized_t(tt_ctx* c, const tt_tensor* x, const tt_tensor* om, doub
     T* L = w.template take<T>(ll);
     T* Tinv = w.template take<T>(ll);
     CholStatus* st = w.template take<CholStatus>(3 * d + 3);
+    double* wss = w.template take<double>(d + 1);
     const T* const* oc = (const T* const*)om->cores.data();
+    // each W[k] is scaled to unit Frobenius norm: the column space of the
+    // sketch Z = X^L W does not depend on W's scale, and unscaled products of
+    // d Gaussian sketch cores overflow FP32
+    auto normalize = [&](int k) {
+        const long ne = (long)r[k] * l[k];
+        sumsq<T>(*c, ne, W[k], wss + k);
+        const long want = (ne + 255) / 256;
+        scale_rsqrt_kernel<T><<<(unsigned)std::max(1L, std::min(want, (long)std::max(1, c->sm_count) * 4)), 256, 0,
+                                c->stream>>>(W[k], ne, wss + k);
+        TT_LAUNCHED(*c);
+    };
 
     // W[k] (r_k x l_k) = sum_i X_k(i) W[k+1] Omega_k(i)^T, W[d] = 1
     {
         const int a = r[d - 1], b = l[d - 1];
         const long K = (long)n[d - 1];  // r_d = l_d = 1
         gemm<T>(*c, false, true, a, b, (int)K, T(1), core[d - 1], K, oc[d - 1], K, T(0), W[d - 1], b);
+        normalize(d - 1);
         for (int k = d - 2; k >= 1; --k) {
             // V = X_k^L (r_k n x r_{k+1}) W[k+1] (r_{k+1} x l_{k+1})
             gemm<T>(*c, false, false, r[k] * n[k], l[k + 1], r[k + 1], T(1), core[k], r[k + 1], W[k + 1], l[k + 1],
@@ -255,6 +280,7 @@ tt_tensor* randomized_t(tt_ctx* c, const tt_tensor* x, const tt_tensor* om, doub
             // W[k] = V^R (r_k x n l_{k+1}) Omega_k^R^T (n l_{k+1} x l_k)
             const long NL = (long)n[k] * l[k + 1];
             gemm<T>(*c, false, true, r[k], l[k], (int)NL, T(1), spare, NL, oc[k], NL, T(0), W[k], l[k]);
+            normalize(k);
         }
     }
     int nst = 0;
