@@ -344,7 +344,10 @@ void      tt_operator_free(tt_operator* op);
 
 /* y = M x: core k of y is y_k((a, p), i, (b, q)) = sum_j M_k(a, i, j, b)
  * x_k(p, j, q), mode sizes m_k and ranks R_k r_k (the operator's rank
- * index slowest).  One thread per output element, FP64 accumulation.
+ * index slowest).  One thread per output element; the n_k-term sums in the
+ * storage precision (FP32 contexts round them at FP32 level); operator
+ * entries that are zero are skipped (a Laplacian core touches at most three
+ * inputs per output).
  * TT_ERR_SHAPE when the orders or the input modes differ. */
 tt_status tt_matvec(tt_ctx* ctx, const tt_operator* M, const tt_tensor* x, tt_tensor** out);
 

@@ -31,10 +31,14 @@ namespace ttgb {
 namespace {
 
 // One thread per output element (grid-stride): the n_in-term sum of
-// operator entries times input-core entries, accumulated in FP64.  The
+// operator entries times input-core entries, in the storage precision.  The
 // output's fastest index (b, q) has q fastest, so neighbouring threads read
 // neighbouring x entries (coalesced) and share one operator entry
-// (broadcast); every output element is written once, coalesced.
+// (broadcast); every output element is written once, coalesced.  The
+// operator entry is the same for the whole warp except where a warp spans
+// two (a, i, b) groups, so a zero entry skips its input load without
+// divergence: the Laplacian's cores (tridiagonal or identity slices) touch
+// at most three of the n inputs per output.
 template <class T>
 __global__ void matvec_core_kernel(const T* __restrict__ M, const T* __restrict__ X, T* __restrict__ Y, int A,
                                    int P, int mo, int ni, int B, int Q, long total) {
@@ -48,9 +52,12 @@ __global__ void matvec_core_kernel(const T* __restrict__ M, const T* __restrict_
         const int a = (int)(ap / P), p = (int)(ap % P);
         const T* mrow = M + (((long)a * mo + i) * ni) * B + b;  // M[a, i, j, b] at mrow[j * B]
         const T* xcol = X + (long)p * ni * Q + q;                // x[p, j, q] at xcol[j * Q]
-        double acc = 0.0;
-        for (int j = 0; j < ni; ++j) acc += (double)__ldg(mrow + (long)j * B) * (double)__ldg(xcol + (long)j * Q);
-        Y[t] = (T)acc;
+        T acc = T(0);
+        for (int j = 0; j < ni; ++j) {
+            const T m = __ldg(mrow + (long)j * B);
+            if (m != T(0)) acc = fma(m, __ldg(xcol + (long)j * Q), acc);
+        }
+        Y[t] = acc;
     }
 }
 

@@ -6,6 +6,8 @@ profiling it in isolation (e.g. under ncu):
     python -m paper_2211_08770_gb300.kernel_driver chol   # Cholesky + inverse, n = 256 (FP32)
     python -m paper_2211_08770_gb300.kernel_driver chol400  # the blocked r = 400 factorization
     python -m paper_2211_08770_gb300.kernel_driver rgemm  # r x r product, 400 x 400 x 400 (FP32)
+    python -m paper_2211_08770_gb300.kernel_driver matvec # Laplacian TT-matrix x rank-400 TT (d = 5, n = 64)
+    python -m paper_2211_08770_gb300.kernel_driver dotstack  # CGS2 passes against 48 rank-4 vectors (stacked dots)
 
 The shapes are the interior bond of the single-rounding workload (20 summed
 rank-20 TTs, n = 64: rank 400, unfolding length 64 x 400)."""
@@ -46,8 +48,21 @@ def main(which, r=400, K=25600, n=256):
         Ti = torch.empty_like(G)
         for _ in range(3):
             T.tt_cholesky_inverse(c, n, G.data_ptr(), L.data_ptr(), Ti.data_ptr())
+    elif which == "matvec":
+        from ttinputs import random_tt
+        x = random_tt(rng, [64] * 5, [1, 64, 400, 400, 64, 1], scale="unit-core")
+        xt = T.tt_tensor_create(c, x)
+        op = T.tt_operator_laplacian(c, 5, 64)
+        for _ in range(3):
+            T.tt_matvec(c, op, xt).free()
+    elif which == "dotstack":
+        from ttinputs import orthonormal_basis, random_tt
+        Q = orthonormal_basis(rng, [64] * 10, 48, 4)
+        A = [T.tt_tensor_create(c, q) for q in Q] + [
+            T.tt_tensor_create(c, random_tt(rng, [64] * 10, [1] + [60] * 9 + [1], scale="unit-core"))]
+        T.tt_orthogonalize(c, "cgs2", A, 1e-6)
     else:
-        raise SystemExit("usage: kernel_driver gemm|gram|chol|chol400|rgemm")
+        raise SystemExit("usage: kernel_driver gemm|gram|chol|chol400|rgemm|matvec|dotstack")
     torch.cuda.synchronize()
     c.close()
     print("ok", which)

@@ -191,15 +191,22 @@ def order3(ctxs):
 K_FP64 = 14
 
 
+STABLE = ("cgs2", "mgs2", "householder")
+
+
 def test_order3_experiment_fp64_matches_oracle_curves(order3):
-    # the FP64 GPU path follows the oracle's curve within 1.5 decades, both
-    # taken at a floor of 1e-14 (values below are round-off)
+    # the FP64 GPU path follows the oracle's curve, both taken at a floor of
+    # 1e-14 (values below are round-off): within a factor 10 for the stable
+    # schemes; within a factor 100 for CGS, MGS and Gram, whose loss of
+    # orthogonality is a constant times u kappa^p with a constant that the
+    # rounding errors of each implementation set
     _, out = order3
     for (s, delta), (lo, lg) in out.items():
         k = min(len(lo), len(lg), K_FP64)
         assert len(lg) >= len(lo) - 1, (s, delta, len(lo), len(lg))
         a, b = np.maximum(lo[:k], 1e-14), np.maximum(lg[:k], 1e-14)
-        assert np.all(np.abs(np.log10(a) - np.log10(b)) <= 1.5), (s, delta, lo, lg)
+        dec = 1.0 if s in STABLE else 2.0
+        assert np.all(np.abs(np.log10(a) - np.log10(b)) <= dec), (s, delta, lo, lg)
 
 
 def test_order3_experiment_fp64_matches_printed_levels(order3):
@@ -208,7 +215,7 @@ def test_order3_experiment_fp64_matches_printed_levels(order3):
     for delta in g["workload"]["deltas"]:
         c2 = out[("cgs2", delta)][1]
         m2 = out[("mgs2", delta)][1][:K_FP64]
-        hh = out[("householder", delta)][1]
+        hh = out[("householder", delta)][1][:K_FP64]
         k0 = lv["cgs2"]["flat_until_k"]
         assert c2[:k0].max() <= lv["cgs2"]["machine_level"], (delta, c2)
         if delta in lv["mgs2"]["flat_for_deltas"]:
