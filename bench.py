@@ -537,7 +537,8 @@ def time_orth(T, dev, m, budget_s):
                                 "loo_curve_every_5": [float("%.3g" % v) for v in loo[4::5]],
                                 "kappa": float(np.sqrt(max(ev[-1], 0) / max(ev[0], 1e-300))),
                                 "max_rank": max(max(q.ranks) for q in Q), "svd_calls": int(st["svd_calls"]),
-                                "fallback_orth": int(st["fallback_orth"]), "gpu_launches": int(st["kernel_launches"]),
+                                "fallback_orth": int(st["fallback_orth"]), "fallback_fp32": int(st["fallback_fp32"]),
+                                "gpu_launches": int(st["kernel_launches"]),
                                 "host_syncs": int(st["host_syncs"]), "sizes_timed": sizes})
             for q in Q:
                 q.free()

@@ -110,6 +110,9 @@ typedef struct {
     uint64_t second_pass_skips; /* certified left-to-right bonds whose first
                                    Cholesky QR pass was already orthonormal to
                                    the required level (second pass not run) */
+    uint64_t fallback_fp32;    /* fallback orthogonalizations of FP32 data kept
+                                  in FP32 (exactly rank-deficient unfoldings);
+                                  the rest of fallback_orth ran in FP64 */
 } tt_stats;
 
 /* Per-kernel timing of a context (tt_ctx_set_profiling): CUDA events are

@@ -67,6 +67,7 @@ void merge_lane(Ctx& root, Ctx& lane) {
     root.stats.series_passes += lane.stats.series_passes;
     root.stats.series_retries += lane.stats.series_retries;
     root.stats.second_pass_skips += lane.stats.second_pass_skips;
+    root.stats.fallback_fp32 += lane.stats.fallback_fp32;
     lane.stats = tt_stats{};
     for (auto& r : lane.recs) {
         ProfRec q = r;

@@ -321,8 +321,22 @@ struct Rounder {
         c->stats.fallback_orth++;
         o.shifted = true;
         if constexpr (sizeof(T) == 4) {
-            fallback_fp64(rows, a, K, X, o);
-            return o;
+            // FP32 data: an FP32 Gram (CUDA cores) and Cholesky with
+            // numerically zero pivots dropped tell an exactly rank-deficient
+            // unfolding (dropped rows, the kept pivots healthy: the FP32
+            // fallback below loses nothing but the dependent rows) from an
+            // ill-conditioned one (small kept pivots: content far below the
+            // unfolding's norm, which FP32 Cholesky QR resolves only to about
+            // sqrt(u_32) of it), which takes the FP64 fallback
+            gram_into(rows, false, a, K, X);
+            CholStatus* sc = next_st();
+            chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 0.0, drop_fb, sc);
+            const CholStatus h2 = read_st(sc);
+            if (!(h2.min_ratio >= 100.0 * ug_fb)) {
+                fallback_fp64(rows, a, K, X, o);
+                return o;
+            }
+            c->stats.fallback_fp32++;
         }
         gram_into(rows, false, a, K, X);
         chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 8.0 * ug_fb * sq, 0.0, next_st());

@@ -36,7 +36,7 @@ class _Stats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("kernel_launches", "roundings", "host_syncs", "bytes_in_use",
                                            "peak_bytes", "svd_calls", "certified_bonds", "fallback_orth", "svd_sweeps",
                                            "series_passes", "series_retries",
-                                           "second_pass_skips")]
+                                           "second_pass_skips", "fallback_fp32")]
 
 
 class _Prof(C.Structure):
