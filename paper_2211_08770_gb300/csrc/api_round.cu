@@ -321,19 +321,25 @@ struct Rounder {
         c->stats.fallback_orth++;
         o.shifted = true;
         if constexpr (sizeof(T) == 4) {
-            // FP32 data: an FP32 Gram (CUDA cores) and Cholesky with
-            // numerically zero pivots dropped tell an exactly rank-deficient
-            // unfolding (dropped rows, the kept pivots healthy: the FP32
-            // fallback below loses nothing but the dependent rows) from an
-            // ill-conditioned one (small kept pivots: content far below the
-            // unfolding's norm, which FP32 Cholesky QR resolves only to about
-            // sqrt(u_32) of it), which takes the FP64 fallback
-            gram_into(rows, false, a, K, X);
+            // FP32 data: the FP64 Gram of the widened X and its Cholesky
+            // with FP64-level zero pivots dropped tell an exactly
+            // rank-deficient unfolding (rows dependent in the stored data:
+            // pivots at FP64 round-off, dropped; the kept ones healthy at
+            // FP32 level, so the FP32 fallback below loses only the
+            // dependent rows) from an ill-conditioned one (kept pivots below
+            // FP32 level: content that FP32 Cholesky QR would resolve only to
+            // about sqrt(u_32) of the unfolding's norm), which continues in
+            // FP64 from this Gram.  An FP32 Gram cannot make the distinction:
+            // its own rounding (about u_32 sqrt(K) of the diagonal) hides
+            // both kinds of small pivot alike.
+            ensure_ws64();
+            convert<T, double>(*c, (long)a * K, X, x64);
+            gram<double, double>(*c, rows, a, K, x64, rows ? K : a, G64);
             CholStatus* sc = next_st();
-            chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 0.0, drop_fb, sc);
+            chol_inv<double, double>(*c, a, G64, L64[0], T64[0], 0.0, 8.0 * 1.1102230246251565e-16 * sq, sc);
             const CholStatus h2 = read_st(sc);
             if (!(h2.min_ratio >= 100.0 * ug_fb)) {
-                fallback_fp64(rows, a, K, X, o);
+                fallback_fp64(rows, a, K, X, o, true);
                 return o;
             }
             c->stats.fallback_fp32++;
@@ -385,16 +391,18 @@ struct Rounder {
     // norm, which for the cancelling sums of the Gram-Schmidt schemes is a
     // large part of the result; in FP64 the loss is at the FP32 storage
     // rounding itself (X = L Q to u_32 ||X||).
-    void fallback_fp64(bool rows, int a, long K, T*& X, Orth& o) {
+    // have_gram: x64 already holds X widened and G64 its Gram (the
+    // classification's), so the first pass starts at its Cholesky
+    void fallback_fp64(bool rows, int a, long K, T*& X, Orth& o, bool have_gram = false) {
         ensure_ws64();
         const double u64 = 1.1102230246251565e-16;
         const double sq = sqrt((double)a);
         const long nel = (long)a * K;
-        convert<T, double>(*c, nel, X, x64);
+        if (!have_gram) convert<T, double>(*c, nel, X, x64);
         double* Xd = x64;
         double* Sd = s64;
         for (int p = 0; p < 3; ++p) {
-            gram<double, double>(*c, rows, a, K, Xd, rows ? K : a, G64);
+            if (p > 0 || !have_gram) gram<double, double>(*c, rows, a, K, Xd, rows ? K : a, G64);
             chol_inv<double, double>(*c, a, G64, L64[p], T64[p], p == 0 ? 8.0 * u64 * sq : 0.0,
                                      p == 0 ? 0.0 : 8.0 * u64 * sq, next_st());
             if (rows)
