@@ -177,6 +177,21 @@ struct Rounder {
         gemm<T>(*c, tA, tB, M, N, K, T(1), A, lda, B, ldb, T(0), C, ldc, 1, 0, 0, 0, tri);
     }
 
+    // a Cholesky QR pass's product X <- L_p^{-1} X (or X L_p^{-T}): FP64 data
+    // by substitution with L_p (backward stable whatever kappa(L_p): the
+    // explicit inverse's error grows like kappa(L) u, which an
+    // ill-conditioned unfolding's content does not survive), FP32 data with
+    // the explicit inverse T_p (its kappa stays below 1/sqrt(100 u_32) on the
+    // fast path, and the FP32 fallback keeps only healthy pivots)
+    void apply_factor(bool rows, int a, long K, T*& X, int p) {
+        if constexpr (sizeof(T) == 8) {
+            trsm_lower<T>(*c, rows, a, K, Lf[p], X, spare);
+            std::swap(X, spare);
+        } else {
+            apply(rows, a, K, X, Ti[p]);
+        }
+    }
+
     // X <- Ti X (rows) or X Ti^T (cols); Ti lower-triangular unless !tri
     void apply(bool rows, int a, long K, T*& X, const T* Tinv, bool tri = true) {
         if (rows) mm(false, false, a, (int)K, a, Tinv, a, X, K, spare, K, tri ? TRI_A_LOWER : 0);
@@ -250,7 +265,7 @@ struct Rounder {
             // pivot / own diagonal, which Cholesky QR is invariant to
             // (column or row scaling does not change it)
             chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 0.0, drop_fb, s0);
-            apply(rows, a, K, X, Ti[0]);
+            apply_factor(rows, a, K, X, 0);
             // the second pass's Gram: a TF32 Gram of the nearly
             // orthonormal X measures E to about u_tf32 / sqrt(K), so
             // it leaves Q orthonormal to that (not to FP32 level); the
@@ -309,7 +324,7 @@ struct Rounder {
                     return o;
                 }
                 chol_inv<T, T>(*c, a, G, Lf[1], Ti[1], 0.0, drop_fb, next_st());
-                apply(rows, a, K, X, Ti[1]);
+                apply_factor(rows, a, K, X, 1);
                 mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Lp, a, TRI_A_LOWER | TRI_B_LOWER);
                 o.nchol = 2;
                 return o;
@@ -326,10 +341,9 @@ struct Rounder {
             // rank-deficient unfolding (rows dependent in the stored data:
             // pivots at FP64 round-off, dropped; the kept ones healthy at
             // FP32 level, so the FP32 fallback below loses only the
-            // dependent rows) from an ill-conditioned one (kept pivots below
-            // FP32 level: content that FP32 Cholesky QR would resolve only to
-            // about sqrt(u_32) of the unfolding's norm), which continues in
-            // FP64 from this Gram.  An FP32 Gram cannot make the distinction:
+            // dependent rows) from an ill-conditioned one (kept pivots within
+            // reach of the FP32 Gram's rounding: content that FP32 Cholesky QR
+            // would not resolve), which continues in FP64 from this Gram.  An FP32 Gram cannot make the distinction:
             // its own rounding (about u_32 sqrt(K) of the diagonal) hides
             // both kinds of small pivot alike.
             ensure_ws64();
@@ -338,7 +352,10 @@ struct Rounder {
             CholStatus* sc = next_st();
             chol_inv<double, double>(*c, a, G64, L64[0], T64[0], 0.0, 8.0 * 1.1102230246251565e-16 * sq, sc);
             const CholStatus h2 = read_st(sc);
-            if (!(h2.min_ratio >= 100.0 * ug_fb)) {
+            // healthy at FP32 level: every kept pivot clear of the FP32
+            // Gram's own rounding (about u_32 sqrt(K) of the diagonal) by a
+            // margin, so the FP32 passes resolve every kept direction
+            if (!(h2.min_ratio >= 64.0 * ug_fb * sqrt((double)K))) {
                 fallback_fp64(rows, a, K, X, o, true);
                 return o;
             }
@@ -346,11 +363,11 @@ struct Rounder {
         }
         gram_into(rows, false, a, K, X);
         chol_inv<T, T>(*c, a, G, Lf[0], Ti[0], 8.0 * ug_fb * sq, 0.0, next_st());
-        apply(rows, a, K, X, Ti[0]);
+        apply_factor(rows, a, K, X, 0);
         for (int p = 1; p <= 2; ++p) {
             gram_into(rows, false, a, K, X);
             chol_inv<T, T>(*c, a, G, Lf[p], Ti[p], 0.0, drop_fb, next_st());
-            apply(rows, a, K, X, Ti[p]);
+            apply_factor(rows, a, K, X, p);
         }
         mm(false, false, a, a, a, Lf[0], a, Lf[1], a, Tmp, a, TRI_A_LOWER | TRI_B_LOWER);
         mm(false, false, a, a, a, Tmp, a, Lf[2], a, Lp, a, TRI_A_LOWER | TRI_B_LOWER);
@@ -405,10 +422,9 @@ struct Rounder {
             if (p > 0 || !have_gram) gram<double, double>(*c, rows, a, K, Xd, rows ? K : a, G64);
             chol_inv<double, double>(*c, a, G64, L64[p], T64[p], p == 0 ? 8.0 * u64 * sq : 0.0,
                                      p == 0 ? 0.0 : 8.0 * u64 * sq, next_st());
-            if (rows)
-                gemm<double>(*c, false, false, a, (int)K, a, 1.0, T64[p], a, Xd, K, 0.0, Sd, K, 1, 0, 0, 0, TRI_A_LOWER);
-            else
-                gemm<double>(*c, false, true, (int)K, a, a, 1.0, Xd, a, T64[p], a, 0.0, Sd, a, 1, 0, 0, 0, TRI_B_UPPER);
+            // Q = L^{-1} X by substitution (not the explicit inverse): the
+            // fallback's unfoldings are the ill-conditioned ones
+            trsm_lower<double>(*c, rows, a, K, L64[p], Xd, Sd);
             std::swap(Xd, Sd);
         }
         convert<double, T>(*c, nel, Xd, X);

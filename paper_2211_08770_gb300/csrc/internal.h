@@ -217,6 +217,13 @@ bool gram_cols_tc_tf32(Ctx& c, int n, long m, const float* X, long ldx, float* G
 // launched) when a pointer or leading dimension is not 16-byte aligned.
 bool gemm_tc3_tf32(Ctx& c, bool bT, int M, int N, int K, const float* A, long lda, const float* B, long ldb,
                    float* C, long ldc, int nsplit);
+// Triangular solve with a lower-triangular a x a L (leading dimension a):
+// rows: Q (a x K) = L^{-1} X; !rows: Q (K x a) = X L^{-T}; row-major, Q does
+// not alias X.  Blocked forward substitution (backward stable), FP64
+// arithmetic in the diagonal blocks; a zero pivot gives a zero component.
+template <class T>
+void trsm_lower(Ctx& c, bool rows, int a, long K, const T* L, const T* X, T* Q);
+
 // reads (and clears) the tensor-core timeout flag; throws TT_ERR_TIMEOUT if set
 void check_tc_error(Ctx& c);
 
