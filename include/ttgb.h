@@ -347,10 +347,11 @@ void      tt_operator_free(tt_operator* op);
 
 /* y = M x: core k of y is y_k((a, p), i, (b, q)) = sum_j M_k(a, i, j, b)
  * x_k(p, j, q), mode sizes m_k and ranks R_k r_k (the operator's rank
- * index slowest).  One thread per output element; the n_k-term sums in the
- * storage precision (FP32 contexts round them at FP32 level); operator
- * entries that are zero are skipped (a Laplacian core touches at most three
- * inputs per output).
+ * index slowest).  One CTA per operator entry triple (a, i, b): its
+ * nonzero entries over j are compacted once, then every output is their sum
+ * against x, in the storage precision (FP32 contexts round at FP32 level);
+ * zero entries cost nothing (a Laplacian core touches at most three inputs
+ * per output).  Input mode sizes up to 4096 (TT_ERR_ARG above).
  * TT_ERR_SHAPE when the orders or the input modes differ. */
 tt_status tt_matvec(tt_ctx* ctx, const tt_operator* M, const tt_tensor* x, tt_tensor** out);
 

@@ -30,34 +30,54 @@ namespace ttgb {
 
 namespace {
 
-// One thread per output element (grid-stride): the n_in-term sum of
-// operator entries times input-core entries, in the storage precision.  The
-// output's fastest index (b, q) has q fastest, so neighbouring threads read
-// neighbouring x entries (coalesced) and share one operator entry
-// (broadcast); every output element is written once, coalesced.  The
-// operator entry is the same for the whole warp except where a warp spans
-// two (a, i, b) groups, so a zero entry skips its input load without
-// divergence: the Laplacian's cores (tridiagonal or identity slices) touch
-// at most three of the n inputs per output.
+// One CTA per (a, i, b) triple of the operator core and chunk of p: the
+// nonzero entries M_k(a, i, j, b) over j are compacted into shared memory
+// once, then every output y((a, p), i, (b, q)) of the chunk is their sum
+// against x(p, j, q), in the storage precision.  Threads run over q
+// fastest, so the reads of x and the writes of y are coalesced; the
+// operator is read once per CTA, and a zero entry costs nothing (the
+// Laplacian's cores touch at most three inputs per output).  HBM-bound on
+// the output, which is the product of the ranks.
 template <class T>
-__global__ void matvec_core_kernel(const T* __restrict__ M, const T* __restrict__ X, T* __restrict__ Y, int A,
-                                   int P, int mo, int ni, int B, int Q, long total) {
+__global__ void __launch_bounds__(256) matvec_core_kernel(const T* __restrict__ M, const T* __restrict__ X,
+                                                          T* __restrict__ Y, int A, int P, int mo, int ni, int B,
+                                                          int Q, int pchunk) {
+    extern __shared__ __align__(16) unsigned char mv_smem[];
+    T* ms = reinterpret_cast<T*>(mv_smem);
+    int* js = reinterpret_cast<int*>(ms + ni);
+    __shared__ int nnz_s;
+    const long triples = (long)A * mo * B;
     const long BQ = (long)B * Q;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const long col = t % BQ;
-        const long rowp = t / BQ;
-        const int b = (int)(col / Q), q = (int)(col % Q);
-        const int i = (int)(rowp % mo);
-        const long ap = rowp / mo;
-        const int a = (int)(ap / P), p = (int)(ap % P);
-        const T* mrow = M + (((long)a * mo + i) * ni) * B + b;  // M[a, i, j, b] at mrow[j * B]
-        const T* xcol = X + (long)p * ni * Q + q;                // x[p, j, q] at xcol[j * Q]
-        T acc = T(0);
-        for (int j = 0; j < ni; ++j) {
-            const T m = __ldg(mrow + (long)j * B);
-            if (m != T(0)) acc = fma(m, __ldg(xcol + (long)j * Q), acc);
+    const int p0 = blockIdx.y * pchunk, p1 = min(P, p0 + pchunk);
+    for (long tr = blockIdx.x; tr < triples; tr += gridDim.x) {
+        const int b = (int)(tr % B);
+        const long ai = tr / B;
+        const int i = (int)(ai % mo), a = (int)(ai / mo);
+        __syncthreads();  // the previous triple's entries are no longer read
+        if (threadIdx.x == 0) {
+            int cnt = 0;
+            const T* mrow = M + (((long)a * mo + i) * ni) * B + b;  // M[a, i, j, b] at mrow[j B]
+            for (int j = 0; j < ni; ++j) {
+                const T m = mrow[(long)j * B];
+                if (m != T(0)) {
+                    ms[cnt] = m;
+                    js[cnt] = j;
+                    ++cnt;
+                }
+            }
+            nnz_s = cnt;
         }
-        Y[t] = acc;
+        __syncthreads();
+        const int nnz = nnz_s;
+        const long nout = (long)(p1 - p0) * Q;
+        for (long e = threadIdx.x; e < nout; e += blockDim.x) {
+            const int q = (int)(e % Q);
+            const int p = p0 + (int)(e / Q);
+            const T* xp = X + (long)p * ni * Q + q;  // x[p, j, q] at xp[j Q]
+            T acc = T(0);
+            for (int t = 0; t < nnz; ++t) acc = fma(ms[t], __ldg(xp + (long)js[t] * Q), acc);
+            Y[(((long)a * P + p) * mo + i) * BQ + (long)b * Q + q] = acc;
+        }
     }
 }
 
@@ -65,14 +85,18 @@ template <class T>
 void matvec_core(Ctx& c, const T* M, const T* X, T* Y, int A, int P, int mo, int ni, int B, int Q) {
     const long total = (long)A * P * mo * B * Q;
     if (total == 0) return;
-    const int threads = 256;
-    const long want = (total + threads - 1) / threads;
-    const long cap = (long)std::max(1, c.sm_count) * 8;  // 8 resident CTAs of 256 threads fill an SM
-    const unsigned blocks = (unsigned)std::max(1L, std::min(want, cap));
+    const long triples = (long)A * mo * B;
+    // about eight CTAs per SM in all: split p when the triples are fewer
+    const long target = (long)std::max(1, c.sm_count) * 8;
+    const int ysplit = (int)std::max(1L, std::min((long)P, (target + triples - 1) / triples));
+    const int pchunk = (P + ysplit - 1) / ysplit;
+    const unsigned gx = (unsigned)std::min(triples, std::max(1L, target));
+    const size_t smem = (size_t)ni * (sizeof(T) + sizeof(int)) + 16;
     const double es = sizeof(T);
     ProfScope ps(c, sizeof(T) == 8 ? "matvec_f64" : "matvec_f32", 2.0 * (double)total * ni,
                  es * ((double)P * ni * Q + (double)A * mo * ni * B + (double)total));
-    matvec_core_kernel<T><<<blocks, threads, 0, c.stream>>>(M, X, Y, A, P, mo, ni, B, Q, total);
+    matvec_core_kernel<T><<<dim3(gx, (unsigned)((P + pchunk - 1) / pchunk)), 256, smem, c.stream>>>(
+        M, X, Y, A, P, mo, ni, B, Q, pchunk);
     TT_LAUNCHED(c);
 }
 
@@ -140,8 +164,11 @@ tt_tensor* matvec_internal(tt_ctx* ctx, const tt_operator* op, const tt_tensor* 
     const Ctx* hc = ctx->root ? ctx->root : static_cast<const Ctx*>(ctx);
     if (ho != hc) throw_status(TT_ERR_ARG, "operator belongs to another context");
     if (op->d != x->d) throw_status(TT_ERR_SHAPE, "orders differ");
-    for (int k = 0; k < x->d; ++k)
+    for (int k = 0; k < x->d; ++k) {
         if (op->n[k] != x->n[k]) throw_status(TT_ERR_SHAPE, "operator input modes differ from the tensor's");
+        if (op->n[k] > 4096) throw_status(TT_ERR_ARG, "tt_matvec: input mode size above 4096");
+        if ((long)x->r[k] * op->R[k] > 65535L * 1024) throw_status(TT_ERR_ARG, "tt_matvec: ranks too large");
+    }
     const int d = x->d;
     std::vector<int> r(d + 1);
     for (int k = 0; k <= d; ++k) {
