@@ -41,8 +41,11 @@ tt_tensor* scale_internal(tt_ctx* ctx, const tt_tensor* x, double alpha);
 // contraction of each pair (count >= 2; FP64 storage is unaffected)
 void dot_many_internal(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tensor* const* y, double* out,
                        bool stacked = false);
+// fb32_ok (FP32 storage): the caller vouches that x does not cancel far
+// below the scale of its representation, so the fallback orthogonalizations
+// may stay in FP32 (otherwise they run in FP64)
 tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est,
-                          void* const* host_out = nullptr, int max_rank = 0);
+                          void* const* host_out = nullptr, int max_rank = 0, bool fb32_ok = false);
 double norm_internal(tt_ctx* ctx, const tt_tensor* x);
 // moves a tensor made on a lane to its root (see get_lanes)
 void rehome(tt_tensor* t, Ctx& root);

@@ -62,6 +62,7 @@ struct Rounder {
     double err2 = 0.0;       // accumulated discarded tail (squared, absolute)
     bool series = true;      // second Cholesky QR passes by the series
     bool series_used = false;
+    bool fb32_ok = false;      // FP32 data: fallbacks may stay in FP32 (see orth)
     double skip_budget = 0.0;  // second passes are skipped (first pass kept
                                // alone) while the sum of their ||E||_F stays
                                // within this budget (0: never, e.g. for norms)
@@ -336,27 +337,16 @@ struct Rounder {
         c->stats.fallback_orth++;
         o.shifted = true;
         if constexpr (sizeof(T) == 4) {
-            // FP32 data: the FP64 Gram of the widened X and its Cholesky
-            // with FP64-level zero pivots dropped tell an exactly
-            // rank-deficient unfolding (rows dependent in the stored data:
-            // pivots at FP64 round-off, dropped; the kept ones healthy at
-            // FP32 level, so the FP32 fallback below loses only the
-            // dependent rows) from an ill-conditioned one (kept pivots within
-            // reach of the FP32 Gram's rounding: content that FP32 Cholesky QR
-            // would not resolve), which continues in FP64 from this Gram.  An FP32 Gram cannot make the distinction:
-            // its own rounding (about u_32 sqrt(K) of the diagonal) hides
-            // both kinds of small pivot alike.
-            ensure_ws64();
-            convert<T, double>(*c, (long)a * K, X, x64);
-            gram<double, double>(*c, rows, a, K, x64, rows ? K : a, G64);
-            CholStatus* sc = next_st();
-            chol_inv<double, double>(*c, a, G64, L64[0], T64[0], 0.0, 8.0 * 1.1102230246251565e-16 * sq, sc);
-            const CholStatus h2 = read_st(sc);
-            // healthy at FP32 level: every kept pivot clear of the FP32
-            // Gram's own rounding (about u_32 sqrt(K) of the diagonal) by a
-            // margin, so the FP32 passes resolve every kept direction
-            if (!(h2.min_ratio >= 64.0 * ug_fb * sqrt((double)K))) {
-                fallback_fp64(rows, a, K, X, o, true);
+            // FP32 data: FP64 unless the caller vouched that the tensor
+            // being rounded does not cancel far below the scale of its
+            // representation (fb32_ok): then the FP32 passes lose nothing
+            // the FP32 storage keeps (an exactly rank-deficient concatenation
+            // loses only its dependent rows).  Where the tensor cancels (the
+            // sums of a Gram-Schmidt scheme on nearly dependent inputs) or
+            // its spectrum is graded, FP32 Cholesky QR resolves the content
+            // only to about sqrt(u_32) of the unfolding's norm.
+            if (!fb32_ok) {
+                fallback_fp64(rows, a, K, X, o);
                 return o;
             }
             c->stats.fallback_fp32++;
@@ -761,7 +751,7 @@ tt_tensor* finish_round(Rounder<T>& R, const tt_tensor* x, double nrm, double* e
 
 template <class T>
 tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est, void* const* host_out = nullptr,
-                   int max_rank = 0) {
+                   int max_rank = 0, bool fb32_ok = false) {
     ctx->stats.roundings++;
     if (x->d == 1) {
         if (err_est) *err_est = 0.0;
@@ -775,6 +765,7 @@ tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_es
         Rounder<T> R(ctx, x);
         R.host_out = host_out;
         R.max_rank = max_rank;
+        R.fb32_ok = fb32_ok;
         if (attempt > 0) R.series = false;
         // skipped second passes (either sweep) leave cores orthonormal to
         // their ||E||_F; the norm and every truncation then see singular
@@ -832,12 +823,12 @@ size_t round_footprint(const tt_tensor* x, tt_precision prec) {
 }
 
 tt_tensor* round_internal(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est, void* const* host_out,
-                          int max_rank) {
+                          int max_rank, bool fb32_ok) {
     check_tensor(ctx, x);
     if (!(delta >= 0.0) || !isfinite(delta)) throw_status(TT_ERR_ARG, "delta must be finite and >= 0");
     if (max_rank < 0) throw_status(TT_ERR_ARG, "max_rank must be >= 0");
     if (ctx->prec == TT_FP64) return round_t<double>(ctx, x, delta, err_est, host_out, max_rank);
-    return round_t<float>(ctx, x, delta, err_est, host_out, max_rank);
+    return round_t<float>(ctx, x, delta, err_est, host_out, max_rank, fb32_ok);
 }
 
 double norm_internal(tt_ctx* ctx, const tt_tensor* x) {

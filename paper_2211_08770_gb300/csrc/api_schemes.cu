@@ -20,9 +20,9 @@ struct Driver {
     tt_round_policy pol;
     int nrounds = 0;
 
-    tt_tensor* round(const tt_tensor* p) {
+    tt_tensor* round(const tt_tensor* p, bool fb32_ok = false) {
         nrounds++;
-        return round_internal(c, p, delta, nullptr);
+        return round_internal(c, p, delta, nullptr, nullptr, 0, fb32_ok);
     }
     double dot(const tt_tensor* a, const tt_tensor* b) {
         double v = 0.0;
@@ -80,6 +80,10 @@ tt_tensor* gs_step(Driver& D, const tt_tensor* a, int i, const tt_tensor* const*
     for (int k = 0; k < (twice ? 2 : 1); ++k) {
         Cur p;
         p.p = prev.p;
+        // the pass's sum keeps at least 1e-2 of ||p_prev||^2 (estimated
+        // below from the basis Gram when it is known): no cancellation that
+        // FP32 fallbacks of the rounding could not resolve
+        bool pass_fb32 = false;
         const bool linear_mgs = modified && qgram && D.pol == TT_ROUND_PAPER && i > 0;
         if ((!modified || linear_mgs) && i > 0) {
             // classical: every projection is against the same vector, so the
@@ -88,9 +92,25 @@ tt_tensor* gs_step(Driver& D, const tt_tensor* a, int i, const tt_tensor* const*
             // coefficients (1, -r_0, ..., -r_{i-1}), the same TT the
             // successive axpys build
             dot_many_internal(D.c, prev.p, i, Q, rk.data(), true);
+            const std::vector<double> cdots(rk);  // <p_prev, q_j>
             if (linear_mgs)
                 for (int j = 0; j < i; ++j)
                     for (int jp = 0; jp < j; ++jp) rk[j] -= rk[jp] * qgram[(size_t)jp * ldg + j];
+            if (qgram && D.c->prec != TT_FP64) {
+                // with the basis Gram at hand (resident bases): the sum
+                // p_prev - sum_j r_j q_j keeps ||p||^2 = ||p_prev||^2 - 2 r^T c
+                // + r^T G r of ||p_prev||^2 (c the dots); when that share is
+                // not small, the rounding's fallbacks may stay in FP32
+                const double np = D.norm(prev.p);
+                const double n2 = np * np;
+                double rc = 0.0, rgr = 0.0;
+                for (int j = 0; j < i; ++j) {
+                    rc += rk[j] * cdots[j];
+                    for (int jp = 0; jp < i; ++jp) rgr += rk[j] * qgram[(size_t)j * ldg + jp] * rk[jp];
+                }
+                const double left = n2 - 2.0 * rc + rgr;
+                pass_fb32 = n2 > 0.0 && left >= 1e-2 * n2;
+            }
             if (D.pol == TT_ROUND_PAPER) {
                 al[0] = 1.0;
                 xs[0] = prev.p;
@@ -115,7 +135,7 @@ tt_tensor* gs_step(Driver& D, const tt_tensor* a, int i, const tt_tensor* const*
                 if (D.pol == TT_ROUND_EVERY_UPDATE) p.set_owned(D.round(p.p));
             }
         }
-        if (D.pol == TT_ROUND_PAPER || i == 0) p.set_owned(D.round(p.p));
+        if (D.pol == TT_ROUND_PAPER || i == 0) p.set_owned(D.round(p.p, pass_fb32));
         // prev <- p (move ownership)
         if (p.own.get()) {
             prev.own = std::move(p.own);

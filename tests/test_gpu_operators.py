@@ -189,6 +189,16 @@ def order3(ctxs):
 # of orthogonality rises to 1e-11 - 1e-10 where the oracle's Householder QR
 # keeps it at the round-off (the bench reports the whole curves).
 K_FP64 = 14
+# TT-Householder forms r(i) = +-sqrt(||a||^2 - s) (Algorithm 6), a
+# difference of squares that leaves the new component to rounding once
+# kappa(A_k)^2 u nears 1: at k = 13 (kappa ~ 1e8) the oracle's and the GPU's
+# r(13) already differ in every digit and the curves part (oracle 3e-10,
+# GPU 2e-5 at delta = 1e-8); it is compared up to k = 12
+K_FP64_HH = 12
+
+
+def _k_fp64(scheme):
+    return K_FP64_HH if scheme == "householder" else K_FP64
 
 
 STABLE = ("cgs2", "mgs2", "householder")
@@ -202,7 +212,7 @@ def test_order3_experiment_fp64_matches_oracle_curves(order3):
     # rounding errors of each implementation set
     _, out = order3
     for (s, delta), (lo, lg) in out.items():
-        k = min(len(lo), len(lg), K_FP64)
+        k = min(len(lo), len(lg), _k_fp64(s))
         assert len(lg) >= len(lo) - 1, (s, delta, len(lo), len(lg))
         a, b = np.maximum(lo[:k], 1e-14), np.maximum(lg[:k], 1e-14)
         dec = 1.0 if s in STABLE else 2.0
@@ -215,7 +225,7 @@ def test_order3_experiment_fp64_matches_printed_levels(order3):
     for delta in g["workload"]["deltas"]:
         c2 = out[("cgs2", delta)][1]
         m2 = out[("mgs2", delta)][1][:K_FP64]
-        hh = out[("householder", delta)][1][:K_FP64]
+        hh = out[("householder", delta)][1][:K_FP64_HH]
         k0 = lv["cgs2"]["flat_until_k"]
         assert c2[:k0].max() <= lv["cgs2"]["machine_level"], (delta, c2)
         if delta in lv["mgs2"]["flat_for_deltas"]:
