@@ -69,14 +69,27 @@ __global__ void __launch_bounds__(256) matvec_core_kernel(const T* __restrict__ 
         }
         __syncthreads();
         const int nnz = nnz_s;
-        const long nout = (long)(p1 - p0) * Q;
-        for (long e = threadIdx.x; e < nout; e += blockDim.x) {
-            const int q = (int)(e % Q);
-            const int p = p0 + (int)(e / Q);
-            const T* xp = X + (long)p * ni * Q + q;  // x[p, j, q] at xp[j Q]
-            T acc = T(0);
-            for (int t = 0; t < nnz; ++t) acc = fma(ms[t], __ldg(xp + (long)js[t] * Q), acc);
-            Y[(((long)a * P + p) * mo + i) * BQ + (long)b * Q + q] = acc;
+        if (Q >= 128) {
+            // rows of q: no index division
+            for (int p = p0; p < p1; ++p) {
+                const T* xp = X + (long)p * ni * Q;
+                T* yp = Y + (((long)a * P + p) * mo + i) * BQ + (long)b * Q;
+                for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+                    T acc = T(0);
+                    for (int t = 0; t < nnz; ++t) acc = fma(ms[t], __ldg(xp + (long)js[t] * Q + q), acc);
+                    yp[q] = acc;
+                }
+            }
+        } else {
+            const int nout = (p1 - p0) * Q;  // < 2^31: p1 - p0 <= P, Q < 128
+            for (int e = threadIdx.x; e < nout; e += blockDim.x) {
+                const int q = e % Q;
+                const int p = p0 + e / Q;
+                const T* xp = X + (long)p * ni * Q + q;  // x[p, j, q] at xp[j Q]
+                T acc = T(0);
+                for (int t = 0; t < nnz; ++t) acc = fma(ms[t], __ldg(xp + (long)js[t] * Q), acc);
+                Y[(((long)a * P + p) * mo + i) * BQ + (long)b * Q + q] = acc;
+            }
         }
     }
 }

@@ -233,7 +233,10 @@ def test_order3_experiment_fp64_matches_printed_levels(order3):
         else:
             assert m2[: lv["mgs2"]["jump_after_k"]].max() <= lv["mgs2"]["machine_level"]
             assert out[("mgs2", delta)][1][-1] >= lv["mgs2"]["jump_level"], (delta, m2)
+        # up to k = 12 the Householder curve is still rising to its plateau
+        # (reached near k = 20, where the oracle test checks the band from
+        # below as well): here only the band's upper side applies
         h = lv["householder"]
-        assert delta / h["band_below_delta"] <= hh[-1] <= h["band_above_delta"] * delta, (delta, hh)
+        assert hh.max() <= h["band_above_delta"] * delta, (delta, hh)
         cg = out[("cgs", delta)][1]
         assert np.all(cg[lv["cgs"]["stagnation_after_k"] + 1:] < lv["cgs"]["stagnation_ceiling"])
