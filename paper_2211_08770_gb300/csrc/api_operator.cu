@@ -9,6 +9,7 @@
 // x_k(p, j, q), ranks R_k r_k with the operator's rank index slowest.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include <algorithm>
 #include <vector>
@@ -32,23 +33,36 @@ namespace {
 
 // One CTA per (a, i, b) triple of the operator core and chunk of p: the
 // nonzero entries M_k(a, i, j, b) over j are compacted into shared memory
-// once, then every output y((a, p), i, (b, q)) of the chunk is their sum
-// against x(p, j, q), in the storage precision.  Threads run over q
-// fastest, so the reads of x and the writes of y are coalesced; the
-// operator is read once per CTA, and a zero entry costs nothing (the
-// Laplacian's cores touch at most three inputs per output).  HBM-bound on
-// the output, which is the product of the ranks.
-template <class T>
+// once (with their row offsets j Q into x), then every output
+// y((a, p), i, (b, q)) of the chunk is their sum against x(p, j, q), in the
+// storage precision.  Each thread produces V consecutive q at a time with
+// one 16-byte load per entry and one 16-byte store (V = 4 for FP32, 2 for
+// FP64 when Q and the core addresses allow it), running over q fastest, so
+// the reads of x and the writes of y are coalesced; the operator is read
+// once per CTA, and a zero entry costs nothing (the Laplacian's cores touch
+// at most three inputs per output).  HBM-bound on the output, which is the
+// product of the ranks.
+template <class T, int V>
+struct alignas(sizeof(T) * V) VecT {
+    T v[V];
+};
+
+template <class T, int V>
 __global__ void __launch_bounds__(256) matvec_core_kernel(const T* __restrict__ M, const T* __restrict__ X,
                                                           T* __restrict__ Y, int A, int P, int mo, int ni, int B,
                                                           int Q, int pchunk) {
+    using VT = VecT<T, V>;
     extern __shared__ __align__(16) unsigned char mv_smem[];
-    T* ms = reinterpret_cast<T*>(mv_smem);
-    int* js = reinterpret_cast<int*>(ms + ni);
+    long long* offs = reinterpret_cast<long long*>(mv_smem);
+    T* ms = reinterpret_cast<T*>(offs + ni);
     __shared__ int nnz_s;
     const long triples = (long)A * mo * B;
     const long BQ = (long)B * Q;
+    const int Qv = Q / V;  // Q is a multiple of V
     const int p0 = blockIdx.y * pchunk, p1 = min(P, p0 + pchunk);
+    // the thread's first (p, q) of the chunk and its stride, with q carried
+    const int dq = (int)(blockDim.x % Qv), dp = (int)(blockDim.x / Qv);
+    const int q0 = (int)(threadIdx.x % Qv), pp0 = p0 + (int)(threadIdx.x / Qv);
     for (long tr = blockIdx.x; tr < triples; tr += gridDim.x) {
         const int b = (int)(tr % B);
         const long ai = tr / B;
@@ -61,7 +75,7 @@ __global__ void __launch_bounds__(256) matvec_core_kernel(const T* __restrict__ 
                 const T m = mrow[(long)j * B];
                 if (m != T(0)) {
                     ms[cnt] = m;
-                    js[cnt] = j;
+                    offs[cnt] = (long long)j * Q;
                     ++cnt;
                 }
             }
@@ -69,29 +83,34 @@ __global__ void __launch_bounds__(256) matvec_core_kernel(const T* __restrict__ 
         }
         __syncthreads();
         const int nnz = nnz_s;
-        if (Q >= 128) {
-            // rows of q: no index division
-            for (int p = p0; p < p1; ++p) {
-                const T* xp = X + (long)p * ni * Q;
-                T* yp = Y + (((long)a * P + p) * mo + i) * BQ + (long)b * Q;
-                for (int q = threadIdx.x; q < Q; q += blockDim.x) {
-                    T acc = T(0);
-                    for (int t = 0; t < nnz; ++t) acc = fma(ms[t], __ldg(xp + (long)js[t] * Q + q), acc);
-                    yp[q] = acc;
-                }
+        T* yab = Y + (long)a * P * mo * BQ + (long)i * BQ + (long)b * Q;  // + p mo BQ + q
+        int q = q0;
+        for (int p = pp0; p < p1;) {
+            const T* xp = X + (long)p * ni * Q + (long)q * V;
+            VT acc;
+#pragma unroll
+            for (int l = 0; l < V; ++l) acc.v[l] = T(0);
+            for (int t = 0; t < nnz; ++t) {
+                const T m = ms[t];
+                const VT xv = *reinterpret_cast<const VT*>(xp + offs[t]);
+#pragma unroll
+                for (int l = 0; l < V; ++l) acc.v[l] = fma(m, xv.v[l], acc.v[l]);
             }
-        } else {
-            const int nout = (p1 - p0) * Q;  // < 2^31: p1 - p0 <= P, Q < 128
-            for (int e = threadIdx.x; e < nout; e += blockDim.x) {
-                const int q = e % Q;
-                const int p = p0 + e / Q;
-                const T* xp = X + (long)p * ni * Q + q;  // x[p, j, q] at xp[j Q]
-                T acc = T(0);
-                for (int t = 0; t < nnz; ++t) acc = fma(ms[t], __ldg(xp + (long)js[t] * Q), acc);
-                Y[(((long)a * P + p) * mo + i) * BQ + (long)b * Q + q] = acc;
+            *reinterpret_cast<VT*>(yab + (long)p * mo * BQ + (long)q * V) = acc;
+            q += dq;
+            p += dp;
+            if (q >= Qv) {
+                q -= Qv;
+                ++p;
             }
         }
     }
+}
+
+template <class T, int V>
+void launch_matvec(Ctx& c, dim3 grid, size_t smem, const T* M, const T* X, T* Y, int A, int P, int mo, int ni,
+                   int B, int Q, int pchunk) {
+    matvec_core_kernel<T, V><<<grid, 256, smem, c.stream>>>(M, X, Y, A, P, mo, ni, B, Q, pchunk);
 }
 
 template <class T>
@@ -103,13 +122,20 @@ void matvec_core(Ctx& c, const T* M, const T* X, T* Y, int A, int P, int mo, int
     const long target = (long)std::max(1, c.sm_count) * 8;
     const int ysplit = (int)std::max(1L, std::min((long)P, (target + triples - 1) / triples));
     const int pchunk = (P + ysplit - 1) / ysplit;
-    const unsigned gx = (unsigned)std::min(triples, std::max(1L, target));
-    const size_t smem = (size_t)ni * (sizeof(T) + sizeof(int)) + 16;
+    const dim3 grid((unsigned)std::min(triples, std::max(1L, target)), (unsigned)((P + pchunk - 1) / pchunk));
+    const size_t smem = (size_t)ni * (sizeof(T) + sizeof(long long)) + 16;
     const double es = sizeof(T);
     ProfScope ps(c, sizeof(T) == 8 ? "matvec_f64" : "matvec_f32", 2.0 * (double)total * ni,
                  es * ((double)P * ni * Q + (double)A * mo * ni * B + (double)total));
-    matvec_core_kernel<T><<<dim3(gx, (unsigned)((P + pchunk - 1) / pchunk)), 256, smem, c.stream>>>(
-        M, X, Y, A, P, mo, ni, B, Q, pchunk);
+    // 16-byte vectors when Q and both cores' addresses allow them
+    const bool al16 = ((uintptr_t)X % 16 == 0) && ((uintptr_t)Y % 16 == 0);
+    constexpr int V16 = 16 / sizeof(T);
+    if (al16 && Q % V16 == 0)
+        launch_matvec<T, V16>(c, grid, smem, M, X, Y, A, P, mo, ni, B, Q, pchunk);
+    else if (sizeof(T) == 4 && al16 && Q % 2 == 0)
+        launch_matvec<T, 2>(c, grid, smem, M, X, Y, A, P, mo, ni, B, Q, pchunk);
+    else
+        launch_matvec<T, 1>(c, grid, smem, M, X, Y, A, P, mo, ni, B, Q, pchunk);
     TT_LAUNCHED(c);
 }
 

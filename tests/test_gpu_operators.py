@@ -48,13 +48,17 @@ def _rand_ttm(rng, m, n, R):
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("fp32", 1e-6), ("mixed_tf32", 1e-6)])
-@pytest.mark.parametrize("case", ["ragged", "large"])
+@pytest.mark.parametrize("case", ["ragged", "large", "vec4", "vec2wide"])
 def test_matvec_matches_oracle(ctxs, prec, tol, case):
-    rng = np.random.default_rng(11 if case == "ragged" else 12)
+    rng = np.random.default_rng({"ragged": 11, "large": 12, "vec4": 13, "vec2wide": 14}[case])
     if case == "ragged":
         m, n, R, r = [3, 5, 2, 4], [4, 2, 3, 3], [1, 2, 3, 2, 1], [1, 3, 2, 4, 1]
-    else:  # several thousand CTAs' worth of outputs and a ragged tail
+    elif case == "large":  # several thousand CTAs' worth of outputs and a ragged tail
         m, n, R, r = [5, 64, 3], [7, 50, 9], [1, 3, 2, 1], [1, 7, 33, 1]
+    elif case == "vec4":  # input-rank rows of 16-byte vectors (Q = 8, 260)
+        m, n, R, r = [6, 64, 5], [5, 40, 6], [1, 2, 3, 1], [1, 8, 260, 1]
+    else:  # rows of pairs longer than a CTA (Q = 1030), rows of 3 vectors (Q = 12)
+        m, n, R, r = [6, 16, 5], [5, 40, 6], [1, 2, 3, 1], [1, 12, 1030, 1]
     op_h = _rand_ttm(rng, m, n, R)
     x = random_tt(rng, n, r)
     c = ctxs[prec]
