@@ -24,6 +24,14 @@ struct tt_operator {
     std::vector<void*> cores;
     void* block = nullptr;
     size_t bytes = 0;
+    // the nonzero entries of each core, listed per (a, i, b) triple (built
+    // on the host at upload): entries ptr[t] .. ptr[t + 1] - 1 of triple
+    // t = (a m_k + i) R_k + b have input index js[e] and value vals[e]
+    std::vector<const int*> nz_ptr, nz_j;
+    std::vector<const void*> nz_val;
+    std::vector<long> nz_count;  // entries per core
+    void* nz_block = nullptr;
+    size_t nz_bytes = 0;
     size_t core_elems(int k) const { return (size_t)R[k] * m[k] * n[k] * R[k + 1]; }
 };
 
@@ -31,74 +39,76 @@ namespace ttgb {
 
 namespace {
 
-// One CTA per (a, i, b) triple of the operator core and chunk of p: the
-// nonzero entries M_k(a, i, j, b) over j are compacted into shared memory
-// once (with their row offsets j Q into x), then every output
-// y((a, p), i, (b, q)) of the chunk is their sum against x(p, j, q), in the
-// storage precision.  Each thread produces V consecutive q at a time with
-// one 16-byte load per entry and one 16-byte store (V = 4 for FP32, 2 for
-// FP64 when Q and the core addresses allow it), running over q fastest, so
-// the reads of x and the writes of y are coalesced; the operator is read
-// once per CTA, and a zero entry costs nothing (the Laplacian's cores touch
-// at most three inputs per output).  HBM-bound on the output, which is the
-// product of the ranks.
+// y((a, p), i, (b, q)) = sum_j M_k(a, i, j, b) x(p, j, q) over the nonzero
+// M_k(a, i, j, b) only (the lists built at upload; the Laplacian's cores
+// have at most three per triple), in the storage precision.  A work item is
+// one triple and a chunk of rows p; a grid of resident CTAs takes the items
+// in turn.  Each thread produces V consecutive q at a time with one 16-byte
+// load per entry and one 16-byte store (V = 4 for FP32, 2 for FP64 when Q
+// and the core addresses allow it), two such vectors per iteration, running
+// over q fastest, so the reads of x and the writes of y are coalesced and
+// every thread has two independent loads in flight; the entry lists are
+// uniform across the CTA (broadcast loads).  HBM-bound on the output, which
+// is the product of the ranks.
 template <class T, int V>
 struct alignas(sizeof(T) * V) VecT {
     T v[V];
 };
 
+constexpr int kMvThreads = 256;
+
 template <class T, int V>
-__global__ void __launch_bounds__(256) matvec_core_kernel(const T* __restrict__ M, const T* __restrict__ X,
-                                                          T* __restrict__ Y, int A, int P, int mo, int ni, int B,
-                                                          int Q, int pchunk) {
+__global__ void __launch_bounds__(kMvThreads) matvec_core_kernel(const int* __restrict__ nzp,
+                                                                 const int* __restrict__ nzj,
+                                                                 const T* __restrict__ nzv, const T* __restrict__ X,
+                                                                 T* __restrict__ Y, int P, int mo, int ni, int B,
+                                                                 int Q, int pchunk, int nch, long items) {
     using VT = VecT<T, V>;
-    extern __shared__ __align__(16) unsigned char mv_smem[];
-    long long* offs = reinterpret_cast<long long*>(mv_smem);
-    T* ms = reinterpret_cast<T*>(offs + ni);
-    __shared__ int nnz_s;
-    const long triples = (long)A * mo * B;
     const long BQ = (long)B * Q;
     const int Qv = Q / V;  // Q is a multiple of V
-    const int p0 = blockIdx.y * pchunk, p1 = min(P, p0 + pchunk);
-    // the thread's first (p, q) of the chunk and its stride, with q carried
-    const int dq = (int)(blockDim.x % Qv), dp = (int)(blockDim.x / Qv);
-    const int q0 = (int)(threadIdx.x % Qv), pp0 = p0 + (int)(threadIdx.x / Qv);
-    for (long tr = blockIdx.x; tr < triples; tr += gridDim.x) {
+    // the thread's first (p, q) of a chunk and its stride, with q carried
+    const int dq = kMvThreads % Qv, dp = kMvThreads / Qv;
+    const int q0 = (int)threadIdx.x % Qv, pr0 = (int)threadIdx.x / Qv;
+    for (long it = blockIdx.x; it < items; it += gridDim.x) {
+        const long tr = it / nch;
+        const int ch = (int)(it - tr * nch);
         const int b = (int)(tr % B);
         const long ai = tr / B;
         const int i = (int)(ai % mo), a = (int)(ai / mo);
-        __syncthreads();  // the previous triple's entries are no longer read
-        if (threadIdx.x == 0) {
-            int cnt = 0;
-            const T* mrow = M + (((long)a * mo + i) * ni) * B + b;  // M[a, i, j, b] at mrow[j B]
-            for (int j = 0; j < ni; ++j) {
-                const T m = mrow[(long)j * B];
-                if (m != T(0)) {
-                    ms[cnt] = m;
-                    offs[cnt] = (long long)j * Q;
-                    ++cnt;
+        const int e0 = nzp[tr], nnz = nzp[tr + 1] - e0;
+        const int p1 = min(P, (ch + 1) * pchunk);
+        const long P_mo_BQ = (long)P * mo * BQ;
+        T* yab = Y + a * P_mo_BQ + (long)i * BQ + (long)b * Q;  // + p mo BQ + q
+        int q = q0, p = ch * pchunk + pr0;
+        while (p < p1) {
+            int q2 = q + dq, p2 = p + dp;
+            if (q2 >= Qv) {
+                q2 -= Qv;
+                ++p2;
+            }
+            const bool two = p2 < p1;
+            const T* x1 = X + (long)p * ni * Q + (long)q * V;
+            const T* x2 = X + (long)p2 * ni * Q + (long)q2 * V;
+            VT acc1, acc2;
+#pragma unroll
+            for (int l = 0; l < V; ++l) acc1.v[l] = acc2.v[l] = T(0);
+            for (int t = 0; t < nnz; ++t) {
+                const T m = nzv[e0 + t];
+                const long off = (long)nzj[e0 + t] * Q;
+                const VT u = *reinterpret_cast<const VT*>(x1 + off);
+                VT w;
+                if (two) w = *reinterpret_cast<const VT*>(x2 + off);
+#pragma unroll
+                for (int l = 0; l < V; ++l) acc1.v[l] = fma(m, u.v[l], acc1.v[l]);
+                if (two) {
+#pragma unroll
+                    for (int l = 0; l < V; ++l) acc2.v[l] = fma(m, w.v[l], acc2.v[l]);
                 }
             }
-            nnz_s = cnt;
-        }
-        __syncthreads();
-        const int nnz = nnz_s;
-        T* yab = Y + (long)a * P * mo * BQ + (long)i * BQ + (long)b * Q;  // + p mo BQ + q
-        int q = q0;
-        for (int p = pp0; p < p1;) {
-            const T* xp = X + (long)p * ni * Q + (long)q * V;
-            VT acc;
-#pragma unroll
-            for (int l = 0; l < V; ++l) acc.v[l] = T(0);
-            for (int t = 0; t < nnz; ++t) {
-                const T m = ms[t];
-                const VT xv = *reinterpret_cast<const VT*>(xp + offs[t]);
-#pragma unroll
-                for (int l = 0; l < V; ++l) acc.v[l] = fma(m, xv.v[l], acc.v[l]);
-            }
-            *reinterpret_cast<VT*>(yab + (long)p * mo * BQ + (long)q * V) = acc;
-            q += dq;
-            p += dp;
+            *reinterpret_cast<VT*>(yab + (long)p * mo * BQ + (long)q * V) = acc1;
+            if (two) *reinterpret_cast<VT*>(yab + (long)p2 * mo * BQ + (long)q2 * V) = acc2;
+            q = q2 + dq;
+            p = p2 + dp;
             if (q >= Qv) {
                 q -= Qv;
                 ++p;
@@ -108,34 +118,47 @@ __global__ void __launch_bounds__(256) matvec_core_kernel(const T* __restrict__ 
 }
 
 template <class T, int V>
-void launch_matvec(Ctx& c, dim3 grid, size_t smem, const T* M, const T* X, T* Y, int A, int P, int mo, int ni,
-                   int B, int Q, int pchunk) {
-    matvec_core_kernel<T, V><<<grid, 256, smem, c.stream>>>(M, X, Y, A, P, mo, ni, B, Q, pchunk);
+void launch_matvec(Ctx& c, const int* nzp, const int* nzj, const T* nzv, const T* X, T* Y, int P, int mo, int ni,
+                   int B, int Q, long triples) {
+    // resident CTAs of this kernel on the whole GPU
+    static const int per_sm = [] {
+        int nb = 0;
+        TT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, matvec_core_kernel<T, V>, kMvThreads, 0));
+        return std::max(1, nb);
+    }();
+    const long slots = (long)std::max(1, c.sm_count) * per_sm;
+    // items of about four 256-vector steps each, at least eight per
+    // resident CTA where the rows allow it (the last round of items is then
+    // a small part of the launch)
+    const long vecs = (long)P * (Q / V);
+    int nch = (int)std::max(1L, std::min((long)P, (vecs + 4L * kMvThreads - 1) / (4L * kMvThreads)));
+    if (triples * nch < 8 * slots) nch = (int)std::min((long)P, (8 * slots + triples - 1) / triples);
+    const int pchunk = (P + nch - 1) / nch;
+    nch = (P + pchunk - 1) / pchunk;
+    const long items = triples * nch;
+    const unsigned grid = (unsigned)std::min(items, slots);
+    matvec_core_kernel<T, V><<<grid, kMvThreads, 0, c.stream>>>(nzp, nzj, nzv, X, Y, P, mo, ni, B, Q, pchunk, nch,
+                                                               items);
 }
 
 template <class T>
-void matvec_core(Ctx& c, const T* M, const T* X, T* Y, int A, int P, int mo, int ni, int B, int Q) {
+void matvec_core(Ctx& c, const int* nzp, const int* nzj, const T* nzv, long nnz, const T* X, T* Y, int A, int P,
+                 int mo, int ni, int B, int Q) {
     const long total = (long)A * P * mo * B * Q;
     if (total == 0) return;
     const long triples = (long)A * mo * B;
-    // about eight CTAs per SM in all: split p when the triples are fewer
-    const long target = (long)std::max(1, c.sm_count) * 8;
-    const int ysplit = (int)std::max(1L, std::min((long)P, (target + triples - 1) / triples));
-    const int pchunk = (P + ysplit - 1) / ysplit;
-    const dim3 grid((unsigned)std::min(triples, std::max(1L, target)), (unsigned)((P + pchunk - 1) / pchunk));
-    const size_t smem = (size_t)ni * (sizeof(T) + sizeof(long long)) + 16;
     const double es = sizeof(T);
-    ProfScope ps(c, sizeof(T) == 8 ? "matvec_f64" : "matvec_f32", 2.0 * (double)total * ni,
-                 es * ((double)P * ni * Q + (double)A * mo * ni * B + (double)total));
+    ProfScope ps(c, sizeof(T) == 8 ? "matvec_f64" : "matvec_f32", 2.0 * (double)nnz * P * Q,
+                 es * ((double)P * ni * Q + (double)total) + (es + 4.0) * nnz + 4.0 * (triples + 1));
     // 16-byte vectors when Q and both cores' addresses allow them
     const bool al16 = ((uintptr_t)X % 16 == 0) && ((uintptr_t)Y % 16 == 0);
     constexpr int V16 = 16 / sizeof(T);
     if (al16 && Q % V16 == 0)
-        launch_matvec<T, V16>(c, grid, smem, M, X, Y, A, P, mo, ni, B, Q, pchunk);
+        launch_matvec<T, V16>(c, nzp, nzj, nzv, X, Y, P, mo, ni, B, Q, triples);
     else if (sizeof(T) == 4 && al16 && Q % 2 == 0)
-        launch_matvec<T, 2>(c, grid, smem, M, X, Y, A, P, mo, ni, B, Q, pchunk);
+        launch_matvec<T, 2>(c, nzp, nzj, nzv, X, Y, P, mo, ni, B, Q, triples);
     else
-        launch_matvec<T, 1>(c, grid, smem, M, X, Y, A, P, mo, ni, B, Q, pchunk);
+        launch_matvec<T, 1>(c, nzp, nzj, nzv, X, Y, P, mo, ni, B, Q, triples);
     TT_LAUNCHED(c);
 }
 
@@ -175,25 +198,76 @@ void free_operator(tt_operator* op) {
     if (!op) return;
     tt_ctx* c = op->ctx;
     c->release(op->block, op->bytes);
+    if (op->nz_block) c->release(op->nz_block, op->nz_bytes);
     delete op;
     drop_ctx_ref(c);
 }
 
 // uploads FP64 host cores, narrowed to the storage type on the host (the
-// operators are small: a few ranks times n^2 per core)
-void upload_cores(tt_operator* op, const double* const* host) {
+// operators are small: a few ranks times n^2 per core), and the lists of
+// each core's nonzero entries (of the narrowed values) per (a, i, b) triple
+template <class T>
+void upload_t(tt_operator* op, const double* const* host) {
     tt_ctx* c = op->ctx;
-    for (int k = 0; k < op->d; ++k) {
+    const int d = op->d;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    std::vector<std::vector<T>> vals(d), narrowed(d);
+    std::vector<std::vector<int>> ptr(d), js(d);
+    size_t nzb = 0;
+    for (int k = 0; k < d; ++k) {
+        const int A = op->R[k], mo = op->m[k], ni = op->n[k], B = op->R[k + 1];
         const size_t ne = op->core_elems(k);
-        if (op->dtype == TT_DTYPE_F64) {
-            TT_CUDA(cudaMemcpyAsync(op->cores[k], host[k], ne * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        } else {
-            std::vector<float> f(host[k], host[k] + ne);
-            TT_CUDA(cudaMemcpyAsync(op->cores[k], f.data(), ne * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-            c->sync();  // f is released at the end of this iteration
-        }
+        narrowed[k].assign(host[k], host[k] + ne);
+        const std::vector<T>& h = narrowed[k];
+        const long triples = (long)A * mo * B;
+        ptr[k].assign(triples + 1, 0);
+        for (int a = 0; a < A; ++a)
+            for (int i = 0; i < mo; ++i)
+                for (int b = 0; b < B; ++b) {
+                    const long t = ((long)a * mo + i) * B + b;
+                    for (int j = 0; j < ni; ++j) {
+                        const T v = h[(((size_t)a * mo + i) * ni + j) * B + b];
+                        if (v != T(0)) {
+                            vals[k].push_back(v);
+                            js[k].push_back(j);
+                        }
+                    }
+                    if (vals[k].size() > (size_t)INT32_MAX) throw_status(TT_ERR_ARG, "operator core too large");
+                    ptr[k][t + 1] = (int)vals[k].size();
+                }
+        nzb += al(ptr[k].size() * sizeof(int)) + al(std::max<size_t>(1, js[k].size()) * sizeof(int)) +
+               al(std::max<size_t>(1, vals[k].size()) * sizeof(T));
     }
-    c->sync();
+    op->nz_block = c->alloc(nzb);
+    op->nz_bytes = nzb;
+    op->nz_ptr.resize(d);
+    op->nz_j.resize(d);
+    op->nz_val.resize(d);
+    op->nz_count.resize(d);
+    char* p = (char*)op->nz_block;
+    for (int k = 0; k < d; ++k) {
+        TT_CUDA(cudaMemcpyAsync(op->cores[k], narrowed[k].data(), narrowed[k].size() * sizeof(T),
+                                cudaMemcpyHostToDevice, c->stream));
+        op->nz_count[k] = (long)vals[k].size();
+        op->nz_ptr[k] = (const int*)p;
+        TT_CUDA(cudaMemcpyAsync(p, ptr[k].data(), ptr[k].size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        p += al(ptr[k].size() * sizeof(int));
+        op->nz_j[k] = (const int*)p;
+        if (!js[k].empty())
+            TT_CUDA(cudaMemcpyAsync(p, js[k].data(), js[k].size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        p += al(std::max<size_t>(1, js[k].size()) * sizeof(int));
+        op->nz_val[k] = p;
+        if (!vals[k].empty())
+            TT_CUDA(cudaMemcpyAsync(p, vals[k].data(), vals[k].size() * sizeof(T), cudaMemcpyHostToDevice,
+                                    c->stream));
+        p += al(std::max<size_t>(1, vals[k].size()) * sizeof(T));
+    }
+    c->sync();  // the host vectors are released on return
+}
+
+void upload_cores(tt_operator* op, const double* const* host) {
+    if (op->dtype == TT_DTYPE_F64) upload_t<double>(op, host);
+    else upload_t<float>(op, host);
 }
 
 tt_tensor* matvec_internal(tt_ctx* ctx, const tt_operator* op, const tt_tensor* x) {
@@ -217,12 +291,15 @@ tt_tensor* matvec_internal(tt_ctx* ctx, const tt_operator* op, const tt_tensor* 
     }
     tt_tensor* y = new_tensor(ctx, d, op->m.data(), r.data());
     for (int k = 0; k < d; ++k) {
+        const long nnz = op->nz_count[k];
         if (ctx->prec == TT_FP64)
-            matvec_core<double>(*ctx, (const double*)op->cores[k], (const double*)x->cores[k], (double*)y->cores[k],
-                                op->R[k], x->r[k], op->m[k], op->n[k], op->R[k + 1], x->r[k + 1]);
+            matvec_core<double>(*ctx, op->nz_ptr[k], op->nz_j[k], (const double*)op->nz_val[k], nnz,
+                                (const double*)x->cores[k], (double*)y->cores[k], op->R[k], x->r[k], op->m[k],
+                                op->n[k], op->R[k + 1], x->r[k + 1]);
         else
-            matvec_core<float>(*ctx, (const float*)op->cores[k], (const float*)x->cores[k], (float*)y->cores[k],
-                               op->R[k], x->r[k], op->m[k], op->n[k], op->R[k + 1], x->r[k + 1]);
+            matvec_core<float>(*ctx, op->nz_ptr[k], op->nz_j[k], (const float*)op->nz_val[k], nnz,
+                               (const float*)x->cores[k], (float*)y->cores[k], op->R[k], x->r[k], op->m[k],
+                               op->n[k], op->R[k + 1], x->r[k + 1]);
     }
     return y;
 }
