@@ -331,8 +331,10 @@ tt_status tt_round_randomized(tt_ctx* ctx, const tt_tensor* x, const tt_tensor* 
 typedef struct tt_operator tt_operator;
 
 /* Copies host FP64 cores (host_cores[k]: R[k]*m[k]*n[k]*R[k+1] doubles) to
- * the device (narrowed to FP32 for FP32 contexts).  TT_ERR_ARG for d < 1,
- * R_0 != 1, R_d != 1, or a size or rank < 1. */
+ * the device (narrowed to FP32 for FP32 contexts), with the lists of each
+ * core's nonzero entries per (a, i, b) triple that tt_matvec reads (built
+ * on the host from the narrowed values).  TT_ERR_ARG for d < 1, R_0 != 1,
+ * R_d != 1, or a size or rank < 1. */
 tt_status tt_operator_create(tt_ctx* ctx, int d, const int* m, const int* n, const int* R,
                              const double* const* host_cores, tt_operator** out);
 /* The d-dimensional Dirichlet Laplacian on n points per mode,
@@ -347,12 +349,12 @@ void      tt_operator_free(tt_operator* op);
 
 /* y = M x: core k of y is y_k((a, p), i, (b, q)) = sum_j M_k(a, i, j, b)
  * x_k(p, j, q), mode sizes m_k and ranks R_k r_k (the operator's rank
- * index slowest).  One CTA per operator entry triple (a, i, b): its
- * nonzero entries over j are compacted once, then every output is their sum
- * against x, in the storage precision (FP32 contexts round at FP32 level);
- * zero entries cost nothing (a Laplacian core touches at most three inputs
- * per output).  Input mode sizes up to 4096 (TT_ERR_ARG above).
- * TT_ERR_SHAPE when the orders or the input modes differ. */
+ * index slowest).  Each output is the sum over the nonzero entries of its
+ * triple (a, i, b) only, in the storage precision (FP32 contexts round at
+ * FP32 level); zero entries cost nothing (a Laplacian core touches at most
+ * three inputs per output).  TT_ERR_SHAPE when the orders or the input
+ * modes differ; TT_ERR_ARG when a product rank R_k r_k exceeds 2^30 or an
+ * operator core has more than 2^31 - 1 triples. */
 tt_status tt_matvec(tt_ctx* ctx, const tt_operator* M, const tt_tensor* x, tt_tensor** out);
 
 /* The input family of the paper's experiments (Section 4): from x_1,

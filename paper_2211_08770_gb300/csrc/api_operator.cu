@@ -43,7 +43,7 @@ namespace {
 // M_k(a, i, j, b) only (the lists built at upload; the Laplacian's cores
 // have at most three per triple), in the storage precision.  A work item is
 // one triple and a chunk of rows p; a grid of resident CTAs takes the items
-// in turn.  Each thread produces V consecutive q at a time with one 16-byte
+// in turn, all triples of a chunk before the next chunk.  Each thread produces V consecutive q at a time with one 16-byte
 // load per entry and one 16-byte store (V = 4 for FP32, 2 for FP64 when Q
 // and the core addresses allow it), two such vectors per iteration, running
 // over q fastest, so the reads of x and the writes of y are coalesced and
@@ -62,19 +62,21 @@ __global__ void __launch_bounds__(kMvThreads) matvec_core_kernel(const int* __re
                                                                  const int* __restrict__ nzj,
                                                                  const T* __restrict__ nzv, const T* __restrict__ X,
                                                                  T* __restrict__ Y, int P, int mo, int ni, int B,
-                                                                 int Q, int pchunk, int nch, long items) {
+                                                                 int Q, int pchunk, int triples, int items) {
     using VT = VecT<T, V>;
     const long BQ = (long)B * Q;
     const int Qv = Q / V;  // Q is a multiple of V
     // the thread's first (p, q) of a chunk and its stride, with q carried
     const int dq = kMvThreads % Qv, dp = kMvThreads / Qv;
     const int q0 = (int)threadIdx.x % Qv, pr0 = (int)threadIdx.x / Qv;
-    for (long it = blockIdx.x; it < items; it += gridDim.x) {
-        const long tr = it / nch;
-        const int ch = (int)(it - tr * nch);
-        const int b = (int)(tr % B);
-        const long ai = tr / B;
-        const int i = (int)(ai % mo), a = (int)(ai / mo);
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        // chunk-major: the CTAs resident at a time share a few chunks of
+        // rows of x, which stay in L2 while every triple reads them
+        const int ch = it / triples;
+        const int tr = it - ch * triples;
+        const int b = tr % B;
+        const int ai = tr / B;
+        const int i = ai % mo, a = ai / mo;
         const int e0 = nzp[tr], nnz = nzp[tr + 1] - e0;
         const int p1 = min(P, (ch + 1) * pchunk);
         const long P_mo_BQ = (long)P * mo * BQ;
@@ -133,12 +135,13 @@ void launch_matvec(Ctx& c, const int* nzp, const int* nzj, const T* nzv, const T
     const long vecs = (long)P * (Q / V);
     int nch = (int)std::max(1L, std::min((long)P, (vecs + 4L * kMvThreads - 1) / (4L * kMvThreads)));
     if (triples * nch < 8 * slots) nch = (int)std::min((long)P, (8 * slots + triples - 1) / triples);
+    nch = (int)std::max(1L, std::min((long)nch, (long)INT32_MAX / triples));
     const int pchunk = (P + nch - 1) / nch;
     nch = (P + pchunk - 1) / pchunk;
-    const long items = triples * nch;
+    const long items = triples * nch;  // <= INT_MAX (checked by the caller)
     const unsigned grid = (unsigned)std::min(items, slots);
-    matvec_core_kernel<T, V><<<grid, kMvThreads, 0, c.stream>>>(nzp, nzj, nzv, X, Y, P, mo, ni, B, Q, pchunk, nch,
-                                                               items);
+    matvec_core_kernel<T, V><<<grid, kMvThreads, 0, c.stream>>>(nzp, nzj, nzv, X, Y, P, mo, ni, B, Q, pchunk,
+                                                               (int)triples, (int)items);
 }
 
 template <class T>
@@ -279,8 +282,8 @@ tt_tensor* matvec_internal(tt_ctx* ctx, const tt_operator* op, const tt_tensor* 
     if (op->d != x->d) throw_status(TT_ERR_SHAPE, "orders differ");
     for (int k = 0; k < x->d; ++k) {
         if (op->n[k] != x->n[k]) throw_status(TT_ERR_SHAPE, "operator input modes differ from the tensor's");
-        if (op->n[k] > 4096) throw_status(TT_ERR_ARG, "tt_matvec: input mode size above 4096");
-        if ((long)x->r[k] * op->R[k] > 65535L * 1024) throw_status(TT_ERR_ARG, "tt_matvec: ranks too large");
+        if ((long)op->R[k] * op->m[k] * op->R[k + 1] > INT32_MAX)
+            throw_status(TT_ERR_ARG, "tt_matvec: operator core with more than 2^31 - 1 (a, i, b) triples");
     }
     const int d = x->d;
     std::vector<int> r(d + 1);
