@@ -154,6 +154,24 @@ tt_precision tt_ctx_precision(const tt_ctx* ctx);
  * the setting.  TT_ERR_ARG for a negative limit. */
 tt_status tt_ctx_set_tc_wait_limit(tt_ctx* ctx, long long cycles);
 
+/* Pipelined sweeps of TT-round (on != 0, the default; TTGB_PIPELINE=0 in
+ * the environment turns them off for new contexts).  On a context that is
+ * not a lane, with the series second pass on, a rounding runs each bond on
+ * the assumption that its first Cholesky QR pass is healthy and its second
+ * pass will be skipped: the factor is absorbed into the next core on a
+ * high-priority stream as soon as the factorization ends, while the
+ * product Q = L^{-1} X and the checks of the second pass run on a second
+ * stream, and the host reads the checks after the next bond is queued.  A
+ * bond that fails them is undone (both streams drain, the cores return to
+ * their buffers) and redone sequentially, so the results are those of the
+ * sequential sweeps.  The pipeline holds four more core-sized buffers; when
+ * the context's HBM budget does not allow them the rounding runs
+ * sequentially.  Profiling (tt_ctx_set_profiling) runs sequentially too, so
+ * that each launch is timed alone.  The rounding stays ordered on the
+ * context's stream: its internal streams wait for it and it waits for
+ * them. */
+tt_status tt_ctx_set_pipeline(tt_ctx* ctx, int on);
+
 /* Enables (on != 0) or disables event timing of the library's launches. */
 tt_status tt_ctx_set_profiling(tt_ctx* ctx, int on);
 /* Restricts event timing to one kernel family (its name as reported by

@@ -84,11 +84,36 @@ cudaStream_t Ctx::copies() {
     return copy_stream;
 }
 
+cudaStream_t Ctx::crit() {
+    if (!crit_stream) {
+        int least = 0, greatest = 0;
+        TT_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        TT_CUDA(cudaStreamCreateWithPriority(&crit_stream, cudaStreamNonBlocking, greatest));
+    }
+    return crit_stream;
+}
+
+cudaStream_t Ctx::side() {
+    if (!side_stream) TT_CUDA(cudaStreamCreateWithFlags(&side_stream, cudaStreamNonBlocking));
+    return side_stream;
+}
+
+void* Ctx::pinned_words() {
+    if (!host_words) TT_CUDA(cudaHostAlloc(&host_words, kHostWords, cudaHostAllocDefault));
+    return host_words;
+}
+
 Ctx::~Ctx() {
     if (copy_stream) {
         cudaStreamSynchronize(copy_stream);
         cudaStreamDestroy(copy_stream);
     }
+    for (cudaStream_t* s : {&crit_stream, &side_stream})
+        if (*s) {
+            cudaStreamSynchronize(*s);
+            cudaStreamDestroy(*s);
+        }
+    if (host_words) cudaFreeHost(host_words);
     for (Ctx* l : lanes) {
         cudaStreamSynchronize(l->stream);
         delete static_cast<tt_ctx*>(l);  // lanes are allocated as tt_ctx
@@ -587,6 +612,10 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     if (sp && sp[0] == 'r') c->series_force_retry = true;
     // =noskip: every second pass runs (no first pass is kept alone)
     if (sp && sp[0] == 'n') c->series_no_skip = true;
+    // TTGB_PIPELINE=0 runs the sweeps of TT-round on the context's stream
+    // alone (no speculative overlap)
+    const char* pl = getenv("TTGB_PIPELINE");
+    if (pl && pl[0] == '0') c->pipeline = false;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
@@ -625,6 +654,12 @@ tt_precision tt_ctx_precision(const tt_ctx* ctx) { return ctx ? ctx->prec : TT_F
 tt_status tt_ctx_set_profiling(tt_ctx* ctx, int on) {
     if (!ctx) return TT_ERR_ARG;
     ctx->prof = on != 0;
+    return TT_OK;
+}
+
+tt_status tt_ctx_set_pipeline(tt_ctx* ctx, int on) {
+    if (!ctx) return TT_ERR_ARG;
+    ctx->pipeline = on != 0;
     return TT_OK;
 }
 

@@ -25,6 +25,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "api_common.h"
@@ -69,7 +70,8 @@ struct Rounder {
     int max_rank = 0;          // rank cap of the left-to-right truncation (0: none)
     bool capped(int b) const { return max_rank > 0 && b > max_rank; }
 
-    Rounder(tt_ctx* ctx, const tt_tensor* x) : c(ctx), d(x->d), n(x->n), r(x->r) {
+    Rounder(tt_ctx* ctx, const tt_tensor* x, bool pipelined = false)
+        : c(ctx), d(x->d), n(x->n), r(x->r), pipe(pipelined) {
         const bool is64 = sizeof(T) == 8;
         tc = (ctx->prec == TT_MIXED_TF32) && ctx->use_tc;
         ug_fb = is64 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
@@ -81,7 +83,7 @@ struct Rounder {
         auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
         const size_t core_b = al(cap * sizeof(T));
         const size_t small_b = al(rr * sizeof(T));
-        ws_bytes = workspace_bytes(d, rmax, cap, sizeof(T));
+        ws_bytes = workspace_bytes(d, rmax, cap, sizeof(T), pipe);
         ws = (char*)ctx->alloc(ws_bytes);
         char* p = ws;
         core.resize(d);
@@ -103,12 +105,36 @@ struct Rounder {
         series = ctx->use_series;
         TT_CUDA(cudaMemsetAsync(dsc, 0, 16 * sizeof(double), c->stream));
         st = (CholStatus*)p;
+        p += al((size_t)st_cap * sizeof(CholStatus));
+        if (pipe) {
+            for (int i = 0; i < kPool; ++i) { freeb.push_back((T*)p); p += core_b; }
+            for (int i = 0; i < 2; ++i) {
+                Lq[i] = (T*)p; p += small_b;
+                Tq[i] = (T*)p; p += small_b;
+                Gq[i] = (T*)p; p += small_b;
+                Eq[i] = (T*)p; p += small_b;
+                Rq[i] = (T*)p; p += small_b;
+            }
+            dq = (double*)p;
+            hw = static_cast<HostSlot*>(c->pinned_words());
+        }
         for (int k = 0; k < d; ++k)
             TT_CUDA(cudaMemcpyAsync(core[k], x->cores[k], sizeof(T) * x->core_elems(k), cudaMemcpyDeviceToDevice,
                                     c->stream));
     }
     ~Rounder() {
-        // host copies still reading the workspace's cores finish first
+        // the second stream's work and the host copies still reading the
+        // workspace's cores finish first
+        if (side_used) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+                cudaEventRecord(e, c->side_stream);
+                cudaStreamWaitEvent(c->stream, e, 0);
+                cudaEventDestroy(e);
+            } else {
+                cudaStreamSynchronize(c->side_stream);
+            }
+        }
         if (copied) cudaStreamSynchronize(c->copy_stream);
         for (cudaEvent_t e : copy_events) c->ev_pool.push_back(e);
         if (ws) c->release(ws, ws_bytes);
@@ -121,13 +147,17 @@ struct Rounder {
     void* const* host_out = nullptr;
     bool copied = false;
     std::vector<cudaEvent_t> copy_events;
-    void stream_core(int k) {
+    // ready: core k is already complete on the device (the host has waited
+    // for the event that follows its last write)
+    void stream_core(int k, bool ready = false) {
         if (!host_out) return;
         cudaStream_t cs = c->copies();
-        cudaEvent_t ev = c->event();
-        copy_events.push_back(ev);
-        TT_CUDA(cudaEventRecord(ev, c->stream));
-        TT_CUDA(cudaStreamWaitEvent(cs, ev, 0));
+        if (!ready) {
+            cudaEvent_t ev = c->event();
+            copy_events.push_back(ev);
+            TT_CUDA(cudaEventRecord(ev, c->stream));
+            TT_CUDA(cudaStreamWaitEvent(cs, ev, 0));
+        }
         const size_t bytes = sizeof(T) * (size_t)r[k] * n[k] * r[k + 1];
         TT_CUDA(cudaMemcpyAsync(host_out[k], core[k], bytes, cudaMemcpyDeviceToHost, cs));
         copied = true;
@@ -135,11 +165,15 @@ struct Rounder {
 
     // bytes of the workspace carved in the constructor (d + 1 core buffers,
     // 12 + d r x r matrices, Jacobi work, singular values, scalars, statuses)
-    static size_t workspace_bytes(int d, int rmax, size_t cap, size_t es) {
+    // (+ with pipelined sweeps: kPool core buffers, 10 r x r matrices and
+    // 16 device words)
+    static size_t workspace_bytes(int d, int rmax, size_t cap, size_t es, bool pipelined = false) {
         auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
         const size_t rr = (size_t)rmax * rmax;
-        return (d + 1) * al(cap * es) + (12 + d) * al(rr * es) + al(2 * rr * sizeof(double)) + al(rmax * sizeof(double)) +
-               al(16 * sizeof(double)) + al((16 * d + 16) * sizeof(CholStatus));
+        const size_t base = (d + 1) * al(cap * es) + (12 + d) * al(rr * es) + al(2 * rr * sizeof(double)) +
+                            al(rmax * sizeof(double)) + al(16 * sizeof(double)) +
+                            al((16 * d + 16) * sizeof(CholStatus));
+        return base + (pipelined ? kPool * al(cap * es) + 10 * al(rr * es) + al(16 * sizeof(double)) : 0);
     }
 
     CholStatus* next_st() {
@@ -155,14 +189,15 @@ struct Rounder {
         return h;
     }
 
-    void gram_into(bool rows, bool fast, int a, long K, const T* X) {
+    void gram_into(bool rows, bool fast, int a, long K, const T* X, T* dst = nullptr) {
+        T* Gd = dst ? dst : G;
         if constexpr (sizeof(T) == 4) {
             if (fast && tc) {
-                if (rows && gram_rows_tc_tf32(*c, a, K, (const float*)X, K, (float*)G)) return;
-                if (!rows && gram_cols_tc_tf32(*c, a, K, (const float*)X, a, (float*)G)) return;
+                if (rows && gram_rows_tc_tf32(*c, a, K, (const float*)X, K, (float*)Gd)) return;
+                if (!rows && gram_cols_tc_tf32(*c, a, K, (const float*)X, a, (float*)Gd)) return;
             }
         }
-        gram<T, T>(*c, rows, a, K, X, rows ? K : a, G);
+        gram<T, T>(*c, rows, a, K, X, rows ? K : a, Gd);
     }
 
     // C = op(A) op(B): tensor-core split TF32 when the context allows it and
@@ -473,7 +508,8 @@ struct Rounder {
 
     // core_{k+1} <- M core_{k+1} (M: rows x r_{k+1}, ld ldm), with core
     // k+1's deferred transform folded in first (M Pend[k+1], r x r)
-    void absorb_next(int k, int rows, const T* M, long ldm, int tri) {
+    // (out: the product's buffer, which becomes core k+1; else spare)
+    void absorb_next(int k, int rows, const T* M, long ldm, int tri, T* out = nullptr) {
         const int b = r[k + 1];
         const long NR = (long)n[k + 1] * r[k + 2];
         if (pend[k + 1]) {
@@ -482,6 +518,11 @@ struct Rounder {
             ldm = b;
             tri = 0;
             pend[k + 1] = 0;
+        }
+        if (out) {
+            mm(false, false, rows, (int)NR, b, M, ldm, core[k + 1], NR, out, NR, tri, true);
+            core[k + 1] = out;
+            return;
         }
         mm(false, false, rows, (int)NR, b, M, ldm, core[k + 1], NR, spare, NR, tri, true);
         std::swap(core[k + 1], spare);
@@ -574,24 +615,32 @@ struct Rounder {
         return rr;
     }
 
-    void rl_sweep() {
-        for (int k = d - 1; k >= 1; --k) {
-            const int a = r[k];
-            const long K = (long)n[k] * r[k + 1];
-            const int M = r[k - 1] * n[k - 1];
-            if (K <= a) {
-                // rank cap: X = I_K X, absorb X itself
-                mm(false, false, M, (int)K, a, core[k - 1], a, core[k], K, spare, K);
-                std::swap(core[k - 1], spare);
-                fill_identity<T>(*c, (int)K, core[k], K);
-                r[k] = (int)K;
-            } else {
-                const Orth o = orth(true, a, K, core[k], Pend + (size_t)k * rmax * rmax, &skip_budget);
-                pend[k] = o.deferred;
-                mm(false, false, M, a, a, core[k - 1], a, Lp, a, spare, a, o.lower ? TRI_B_LOWER : 0, true);
-                std::swap(core[k - 1], spare);
-            }
+    // bond k of the right-to-left sweep: core k orthonormalized, its factor
+    // absorbed into core k-1
+    void rl_bond(int k) {
+        const int a = r[k];
+        const long K = (long)n[k] * r[k + 1];
+        const int M = r[k - 1] * n[k - 1];
+        if (K <= a) {
+            // rank cap: X = I_K X, absorb X itself
+            mm(false, false, M, (int)K, a, core[k - 1], a, core[k], K, spare, K);
+            std::swap(core[k - 1], spare);
+            fill_identity<T>(*c, (int)K, core[k], K);
+            r[k] = (int)K;
+        } else {
+            const Orth o = orth(true, a, K, core[k], Pend + (size_t)k * rmax * rmax, &skip_budget);
+            pend[k] = o.deferred;
+            mm(false, false, M, a, a, core[k - 1], a, Lp, a, spare, a, o.lower ? TRI_B_LOWER : 0, true);
+            std::swap(core[k - 1], spare);
         }
+    }
+
+    void rl_sweep() {
+        if (pipe && series && skip_budget > 0.0) {
+            rl_sweep_pipelined();
+            return;
+        }
+        for (int k = d - 1; k >= 1; --k) rl_bond(k);
     }
 
     double core_norm(int k) {
@@ -603,97 +652,380 @@ struct Rounder {
         return sqrt(h);
     }
 
+    // bond k of the left-to-right sweep: core k orthonormalized (and
+    // truncated unless certified), its factor absorbed into core k+1
+    void lr_bond(int k, double eps) {
+        const int m = r[k] * n[k];
+        const int b = r[k + 1];
+        const long NR = (long)n[k + 1] * r[k + 2];
+        if (m >= b) {
+            Orth o = orth(false, b, m, core[k], nullptr, nullptr, true);
+            // a capped bond is truncated whatever its spectrum: no certificate
+            const bool cap = capped(b);
+            const double lb = cap ? 0.0 : (o.lb >= 0.0 ? o.lb : sigma_lb(b, o));
+            if (o.series_pending) {
+                if (!cap && lb > 2.0 * eps && lb > 0.0 && o.e <= skip_budget) {
+                    // certified, and Q1 is orthonormal to ||E||_F: the
+                    // bond keeps its rank with core_k = Q1 and
+                    // core_{k+1} <- L1^T core_{k+1} (X = Q1 L1^T exactly);
+                    // the second pass would only sharpen the cores'
+                    // orthonormality.  The left factor of a later bond
+                    // then has singular values within 1 +- (sum of the
+                    // skipped ||E||_F) / 2, which scales that bond's
+                    // truncation error by at most the same factor
+                    skip_budget -= o.e;
+                    c->stats.certified_bonds++;
+                    c->stats.second_pass_skips++;
+                    transpose<T>(*c, b, b, Lf[0], Tmp);
+                    absorb_next(k, b, Tmp, b, TRI_A_UPPER);
+                    return;
+                }
+                finish_series(false, b, m, core[k], nullptr, o);
+            }
+            if (lb > 2.0 * eps && lb > 0.0) {
+                c->stats.certified_bonds++;
+                // core_{k+1} <- R core_{k+1}, R = Lp^T
+                transpose<T>(*c, b, b, Lp, Tmp);
+                absorb_next(k, b, Tmp, b, o.lower ? TRI_A_UPPER : 0);
+                return;
+            }
+            // R = Lp^T (b x b), SVD, truncate
+            transpose<T>(*c, b, b, Lp, Tmp);
+            c->stats.svd_calls++;
+            // FP32 data: columns of R = rows of Lp, FP32 column Jacobi
+            if (trunc_f32(m, b, b, Lp, b, Tmp, eps, k, NR, true)) return;
+            jacobi_svd<T>(*c, b, b, Tmp, Ub, SVt, sig, (T*)jwork, svd_tol(b), svd_floor(b));
+            std::vector<double> hs(b);
+            TT_CUDA(cudaMemcpyAsync(hs.data(), sig, b * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            c->sync();
+            const int rp = trunc_rank(hs, eps);
+            mm(false, false, m, rp, b, core[k], b, Ub, b, spare, rp);
+            std::swap(core[k], spare);
+            absorb_next(k, rp, SVt, b, 0);
+            r[k + 1] = rp;
+        } else {
+            // m < b: Q = I_m, R = X (m x b); certificate from the Gram of
+            // the rows of X (SIMT arithmetic, its error is subtracted)
+            const T* X = core[k];
+            gram<T, T>(*c, true, m, b, X, b, G);
+            CholStatus* s = next_st();
+            chol_inv<T, T>(*c, m, G, Lf[0], Ti[0], 0.0, 8.0 * ug_fb * sqrt((double)m), s);
+            Orth o1{1, 0, false};
+            o1.nchol = 1;
+            const bool cap = capped(m);
+            double lb = cap ? 0.0 : sigma_lb(m, o1);
+            CholStatus hs0 = read_st(s);
+            const double noise = 16.0 * ug_fb * sqrt((double)m) * hs0.trace;
+            const double lb2 = lb * lb - noise;
+            if (!cap && lb > 0.0 && lb2 > 4.0 * eps * eps) {
+                c->stats.certified_bonds++;
+                absorb_next(k, m, X, b, 0);
+                fill_identity<T>(*c, m, core[k], m);
+                r[k + 1] = m;
+                return;
+            }
+            c->stats.svd_calls++;
+            // FP32 data: columns of X = rows of X^T (b x m, in Tmp)
+            if constexpr (sizeof(T) == 4) {
+                transpose<T>(*c, b, m, X, Tmp);
+                if (trunc_f32(m, m, b, Tmp, m, X, eps, k, NR, false)) return;
+            }
+            jacobi_svd<T>(*c, m, b, X, Ub, SVt, sig, (T*)jwork, svd_tol(b), svd_floor(b));
+            std::vector<double> hsg(m);
+            TT_CUDA(cudaMemcpyAsync(hsg.data(), sig, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            c->sync();
+            const int rp = trunc_rank(hsg, eps);
+            // core_k <- U[:, :rp] (m x rp)
+            TT_CUDA(cudaMemcpy2DAsync(core[k], rp * sizeof(T), Ub, m * sizeof(T), rp * sizeof(T), m,
+                                      cudaMemcpyDeviceToDevice, c->stream));
+            absorb_next(k, rp, SVt, b, 0);
+            r[k + 1] = rp;
+        }
+    }
+
     void lr_sweep(double eps) {
+        if (pipe && series && skip_budget > 0.0) {
+            lr_sweep_pipelined(eps);
+            return;
+        }
         for (int k = 0; k + 1 < d; ++k) {
             if (k > 0) stream_core(k - 1);  // final since the last iteration
-            const int m = r[k] * n[k];
-            const int b = r[k + 1];
-            const long NR = (long)n[k + 1] * r[k + 2];
-            if (m >= b) {
-                Orth o = orth(false, b, m, core[k], nullptr, nullptr, true);
-                // a capped bond is truncated whatever its spectrum: no certificate
-                const bool cap = capped(b);
-                const double lb = cap ? 0.0 : (o.lb >= 0.0 ? o.lb : sigma_lb(b, o));
-                if (o.series_pending) {
-                    if (!cap && lb > 2.0 * eps && lb > 0.0 && o.e <= skip_budget) {
-                        // certified, and Q1 is orthonormal to ||E||_F: the
-                        // bond keeps its rank with core_k = Q1 and
-                        // core_{k+1} <- L1^T core_{k+1} (X = Q1 L1^T exactly);
-                        // the second pass would only sharpen the cores'
-                        // orthonormality.  The left factor of a later bond
-                        // then has singular values within 1 +- (sum of the
-                        // skipped ||E||_F) / 2, which scales that bond's
-                        // truncation error by at most the same factor
-                        skip_budget -= o.e;
-                        c->stats.certified_bonds++;
-                        c->stats.second_pass_skips++;
-                        transpose<T>(*c, b, b, Lf[0], Tmp);
-                        absorb_next(k, b, Tmp, b, TRI_A_UPPER);
-                        continue;
-                    }
-                    finish_series(false, b, m, core[k], nullptr, o);
-                }
-                if (lb > 2.0 * eps && lb > 0.0) {
-                    c->stats.certified_bonds++;
-                    // core_{k+1} <- R core_{k+1}, R = Lp^T
-                    transpose<T>(*c, b, b, Lp, Tmp);
-                    absorb_next(k, b, Tmp, b, o.lower ? TRI_A_UPPER : 0);
-                    continue;
-                }
-                // R = Lp^T (b x b), SVD, truncate
-                transpose<T>(*c, b, b, Lp, Tmp);
-                c->stats.svd_calls++;
-                // FP32 data: columns of R = rows of Lp, FP32 column Jacobi
-                if (trunc_f32(m, b, b, Lp, b, Tmp, eps, k, NR, true)) continue;
-                jacobi_svd<T>(*c, b, b, Tmp, Ub, SVt, sig, (T*)jwork, svd_tol(b), svd_floor(b));
-                std::vector<double> hs(b);
-                TT_CUDA(cudaMemcpyAsync(hs.data(), sig, b * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-                c->sync();
-                const int rp = trunc_rank(hs, eps);
-                mm(false, false, m, rp, b, core[k], b, Ub, b, spare, rp);
-                std::swap(core[k], spare);
-                absorb_next(k, rp, SVt, b, 0);
-                r[k + 1] = rp;
-            } else {
-                // m < b: Q = I_m, R = X (m x b); certificate from the Gram of
-                // the rows of X (SIMT arithmetic, its error is subtracted)
-                const T* X = core[k];
-                gram<T, T>(*c, true, m, b, X, b, G);
-                CholStatus* s = next_st();
-                chol_inv<T, T>(*c, m, G, Lf[0], Ti[0], 0.0, 8.0 * ug_fb * sqrt((double)m), s);
-                Orth o1{1, 0, false};
-                o1.nchol = 1;
-                const bool cap = capped(m);
-                double lb = cap ? 0.0 : sigma_lb(m, o1);
-                CholStatus hs0 = read_st(s);
-                const double noise = 16.0 * ug_fb * sqrt((double)m) * hs0.trace;
-                const double lb2 = lb * lb - noise;
-                if (!cap && lb > 0.0 && lb2 > 4.0 * eps * eps) {
-                    c->stats.certified_bonds++;
-                    absorb_next(k, m, X, b, 0);
-                    fill_identity<T>(*c, m, core[k], m);
-                    r[k + 1] = m;
-                    continue;
-                }
-                c->stats.svd_calls++;
-                // FP32 data: columns of X = rows of X^T (b x m, in Tmp)
-                if constexpr (sizeof(T) == 4) {
-                    transpose<T>(*c, b, m, X, Tmp);
-                    if (trunc_f32(m, m, b, Tmp, m, X, eps, k, NR, false)) continue;
-                }
-                jacobi_svd<T>(*c, m, b, X, Ub, SVt, sig, (T*)jwork, svd_tol(b), svd_floor(b));
-                std::vector<double> hsg(m);
-                TT_CUDA(cudaMemcpyAsync(hsg.data(), sig, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-                c->sync();
-                const int rp = trunc_rank(hsg, eps);
-                // core_k <- U[:, :rp] (m x rp)
-                TT_CUDA(cudaMemcpy2DAsync(core[k], rp * sizeof(T), Ub, m * sizeof(T), rp * sizeof(T), m,
-                                          cudaMemcpyDeviceToDevice, c->stream));
-                absorb_next(k, rp, SVt, b, 0);
-                r[k + 1] = rp;
-            }
+            lr_bond(k, eps);
         }
         if (d >= 2) stream_core(d - 2);
+        stream_core(d - 1);
+    }
+
+    // ---- pipelined sweeps ------------------------------------------------
+    // With second passes skippable (series on, positive budget), a bond is
+    // run on the assumption that its first Cholesky QR pass is healthy and
+    // its second pass will be skipped (every bond of a well-conditioned
+    // rounding): the factor L1 is absorbed into the neighbouring core as
+    // soon as the Cholesky ends, on the critical stream, while the apply
+    // Q1 = L1^{-1} X, the second Gram, E (and, left to right, the
+    // certificate's norms) run on the second stream.  The host reads a
+    // bond's decision data after the next bond is queued, so neither the
+    // applies nor the host round trip sit on the chain Gram -> Cholesky ->
+    // absorb -> next Gram.  A bond that does not pass (unhealthy, E too
+    // large for the budget, not certified) is undone with the next one:
+    // both streams drain, the cores return to the buffers they started from
+    // (the speculative products went to fresh buffers) and the bond runs
+    // the sequential path.  The arithmetic of a passed bond is that of the
+    // sequential path's skip.
+    bool pipe = false;
+    bool side_used = false;
+    static constexpr int kPool = 4;  // two bonds in flight, two fresh cores each
+    std::vector<T*> freeb;           // free core buffers of the pipeline
+    T *Lq[2] = {}, *Tq[2] = {}, *Gq[2] = {}, *Eq[2] = {}, *Rq[2] = {};  // per bond parity
+    double* dq = nullptr;            // device words, 8 per parity
+    struct HostSlot {
+        CholStatus st;
+        double w[4];
+    };
+    HostSlot* hw = nullptr;  // page-locked mirror of each parity's decision data
+    struct Spec {
+        int k = -1, slot = 0;
+        T *x_orig = nullptr, *q = nullptr;         // core k before; Q1
+        T *nb_orig = nullptr, *nb_new = nullptr;  // neighbour before; with L1 absorbed
+        CholStatus* s0 = nullptr;
+        cudaEvent_t ev_main = nullptr, ev_dec = nullptr;
+    };
+    T* take() {
+        if (freeb.empty()) throw_status(TT_ERR_ARG, "internal: pipeline buffers exhausted");
+        T* b = freeb.back();
+        freeb.pop_back();
+        return b;
+    }
+    void give(T* b) { freeb.push_back(b); }
+    void drop_events(Spec& s) {
+        if (s.ev_main) c->ev_pool.push_back(s.ev_main);
+        if (s.ev_dec) c->ev_pool.push_back(s.ev_dec);
+        s.ev_main = s.ev_dec = nullptr;
+    }
+    // launches go to the second stream while alive
+    struct OnSide {
+        Ctx* c;
+        cudaStream_t saved;
+        explicit OnSide(Ctx* cc) : c(cc), saved(cc->stream) { c->stream = c->side(); }
+        ~OnSide() { c->stream = saved; }
+    };
+    // the critical stream waits for everything queued on the second one
+    void join_side() {
+        if (!side_used) return;
+        cudaEvent_t e = c->event();
+        TT_CUDA(cudaEventRecord(e, c->side()));
+        TT_CUDA(cudaStreamWaitEvent(c->stream, e, 0));
+        c->ev_pool.push_back(e);
+    }
+    // Q = L1^{-1} X (rows) or X L1^{-T} (cols), as apply_factor does it
+    void side_apply(bool rows, int a, long K, const T* X, T* Q, int slot) {
+        if constexpr (sizeof(T) == 8) {
+            trsm_lower<T>(*c, rows, a, K, Lq[slot], X, Q);
+        } else {
+            if (rows) mm(false, false, a, (int)K, a, Tq[slot], a, X, K, Q, K, TRI_A_LOWER);
+            else mm(false, true, (int)K, a, a, X, a, Tq[slot], a, Q, a, TRI_B_UPPER);
+        }
+    }
+    // (second stream) the bond's status and words to the host, then its event
+    void post(Spec& s) {
+        TT_CUDA(cudaMemcpyAsync(&hw[s.slot].st, s.s0, sizeof(CholStatus), cudaMemcpyDeviceToHost, c->stream));
+        TT_CUDA(cudaMemcpyAsync(hw[s.slot].w, dq + 8 * s.slot, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+        s.ev_dec = c->event();
+        TT_CUDA(cudaEventRecord(s.ev_dec, c->stream));
+    }
+    // the first pass's health and ||E||_F of a bond whose data has arrived
+    bool first_pass_ok(const Spec& s, double& e) {
+        TT_CUDA(cudaEventSynchronize(s.ev_dec));
+        c->stats.host_syncs++;
+        const CholStatus h = hw[s.slot].st;
+        if (h.nonfinite) throw_status(TT_ERR_NONFINITE, "NaN or Inf in a Gram matrix");
+        e = sqrt(hw[s.slot].w[2]);
+        const double ratio_fast = tc ? 10.0 * ug_fast : 100.0 * ug_fast;
+        return h.ndrop == 0 && h.min_ratio >= ratio_fast && series_valid(e) && e <= skip_budget;
+    }
+    // both streams drain and bond s (and cur, queued after it) is undone
+    void rollback(Spec& s, Spec* cur, bool rl) {
+        join_side();
+        c->sync();
+        if (cur) {
+            core[rl ? cur->k - 1 : cur->k + 1] = cur->nb_orig;
+            core[cur->k] = cur->x_orig;  // s.nb_new
+            give(cur->q);
+            give(cur->nb_new);
+            drop_events(*cur);
+        }
+        core[s.k] = s.x_orig;
+        core[rl ? s.k - 1 : s.k + 1] = s.nb_orig;
+        give(s.q);
+        give(s.nb_new);
+        drop_events(s);
+    }
+
+    Spec enqueue_rl(int k) {
+        Spec s;
+        s.k = k;
+        s.slot = k & 1;
+        const int a = r[k];
+        const long K = (long)n[k] * r[k + 1];
+        const int M = r[k - 1] * n[k - 1];
+        s.x_orig = core[k];
+        s.nb_orig = core[k - 1];
+        s.q = take();
+        s.nb_new = take();
+        gram_into(true, true, a, K, core[k]);
+        s.s0 = next_st();
+        chol_inv<T, T>(*c, a, G, Lq[s.slot], Tq[s.slot], 0.0, 8.0 * ug_fb * sqrt((double)a), s.s0);
+        mm(false, false, M, a, a, core[k - 1], a, Lq[s.slot], a, s.nb_new, a, TRI_B_LOWER, true);
+        s.ev_main = c->event();
+        TT_CUDA(cudaEventRecord(s.ev_main, c->stream));
+        {
+            OnSide os(c);
+            side_used = true;
+            TT_CUDA(cudaStreamWaitEvent(c->stream, s.ev_main, 0));
+            side_apply(true, a, K, core[k], s.q, s.slot);
+            gram_into(true, K >= kTc2MinK, a, K, s.q, Gq[s.slot]);
+            near_identity<T>(*c, a, Gq[s.slot], Eq[s.slot], dq + 8 * s.slot + 2);
+            post(s);
+        }
+        core[k - 1] = s.nb_new;
+        return s;
+    }
+
+    bool resolve_rl(Spec& s) {
+        double e = 0.0;
+        const bool ok = first_pass_ok(s, e);
+        if (!ok) return false;
+        skip_budget -= e;
+        c->stats.second_pass_skips++;
+        core[s.k] = s.q;
+        give(s.x_orig);
+        give(s.nb_orig);
+        drop_events(s);
+        return true;
+    }
+
+    void settle_rl(Spec& s) {
+        if (resolve_rl(s)) return;
+        rollback(s, nullptr, true);
+        rl_bond(s.k);
+    }
+
+    void rl_sweep_pipelined() {
+        Spec prev;
+        bool have = false;
+        int k = d - 1;
+        while (k >= 1) {
+            if ((long)n[k] * r[k + 1] <= r[k]) {
+                if (have) settle_rl(prev);
+                have = false;
+                rl_bond(k);
+                --k;
+                continue;
+            }
+            Spec cur = enqueue_rl(k);
+            if (have && !resolve_rl(prev)) {
+                rollback(prev, &cur, true);
+                rl_bond(prev.k);
+                have = false;
+                continue;  // bond k again, from the corrected core
+            }
+            prev = cur;
+            have = true;
+            --k;
+        }
+        if (have) settle_rl(prev);
+        join_side();
+    }
+
+    Spec enqueue_lr(int k) {
+        Spec s;
+        s.k = k;
+        s.slot = k & 1;
+        const int m = r[k] * n[k];
+        const int b = r[k + 1];
+        s.x_orig = core[k];
+        s.nb_orig = core[k + 1];
+        s.q = take();
+        s.nb_new = take();
+        gram_into(false, true, b, m, core[k]);
+        s.s0 = next_st();
+        chol_inv<T, T>(*c, b, G, Lq[s.slot], Tq[s.slot], 0.0, 8.0 * ug_fb * sqrt((double)b), s.s0);
+        transpose<T>(*c, b, b, Lq[s.slot], Rq[s.slot]);
+        absorb_next(k, b, Rq[s.slot], b, TRI_A_UPPER, s.nb_new);  // core k+1 <- L1^T core k+1
+        s.ev_main = c->event();
+        TT_CUDA(cudaEventRecord(s.ev_main, c->stream));
+        {
+            OnSide os(c);
+            side_used = true;
+            TT_CUDA(cudaStreamWaitEvent(c->stream, s.ev_main, 0));
+            side_apply(false, b, m, core[k], s.q, s.slot);
+            gram_into(false, m >= kTc2MinK, b, m, s.q, Gq[s.slot]);
+            near_identity<T>(*c, b, Gq[s.slot], Eq[s.slot], dq + 8 * s.slot + 2);
+            TT_CUDA(cudaMemsetAsync(dq + 8 * s.slot, 0, 2 * sizeof(double), c->stream));
+            inv_and_identity_defect<T>(*c, b, Lq[s.slot], Tq[s.slot], dq + 8 * s.slot);
+            post(s);
+        }
+        return s;
+    }
+
+    // the certified skip of the sequential path (lr_bond with a series
+    // pass pending): sigma_min(Q1 L1^T) bounded from L1, its inverse and E
+    bool resolve_lr(Spec& s, double eps) {
+        double e = 0.0;
+        if (!first_pass_ok(s, e)) return false;
+        const int b = r[s.k + 1];
+        const double sq = sqrt((double)b);
+        const double w0 = hw[s.slot].w[0], w1 = hw[s.slot].w[1];
+        const double lb1 = std::max(w0 > 0.0 ? 1.0 / sqrt(w0) : 0.0, 1.0 - sqrt(w1));
+        const double lb = lb1 * std::max(0.0, sqrt(1.0 - e) - (2.0 + sq) * ug_fb);
+        if (!(lb > 2.0 * eps && lb > 0.0)) return false;
+        skip_budget -= e;
+        c->stats.certified_bonds++;
+        c->stats.second_pass_skips++;
+        core[s.k] = s.q;
+        give(s.x_orig);
+        give(s.nb_orig);
+        drop_events(s);
+        stream_core(s.k, true);
+        return true;
+    }
+
+    void settle_lr(Spec& s, double eps) {
+        if (resolve_lr(s, eps)) return;
+        rollback(s, nullptr, false);
+        lr_bond(s.k, eps);
+        stream_core(s.k);
+    }
+
+    void lr_sweep_pipelined(double eps) {
+        Spec prev;
+        bool have = false;
+        int k = 0;
+        while (k + 1 < d) {
+            const bool spec = r[k] * n[k] >= r[k + 1] && !capped(r[k + 1]) && !pend[k + 1];
+            if (!spec) {
+                if (have) settle_lr(prev, eps);
+                have = false;
+                lr_bond(k, eps);
+                stream_core(k);
+                ++k;
+                continue;
+            }
+            Spec cur = enqueue_lr(k);
+            if (have && !resolve_lr(prev, eps)) {
+                rollback(prev, &cur, false);
+                lr_bond(prev.k, eps);
+                stream_core(prev.k);
+                have = false;
+                continue;  // bond k again, from the corrected core
+            }
+            prev = cur;
+            have = true;
+            ++k;
+        }
+        if (have) settle_lr(prev, eps);
+        join_side();
         stream_core(d - 1);
     }
 
@@ -749,6 +1081,38 @@ tt_tensor* finish_round(Rounder<T>& R, const tt_tensor* x, double nrm, double* e
     return y;
 }
 
+// While alive (and on), the context's launches go to its high-priority
+// critical stream, which first waits for the caller's stream; on exit the
+// caller's stream waits for it.
+struct OnCritStream {
+    Ctx* c;
+    cudaStream_t saved = nullptr;
+    bool on = false;
+    OnCritStream(Ctx* ctx, bool use) : c(ctx) {
+        if (!use) return;
+        cudaStream_t crit = c->crit();
+        cudaEvent_t e = c->event();
+        TT_CUDA(cudaEventRecord(e, c->stream));
+        TT_CUDA(cudaStreamWaitEvent(crit, e, 0));
+        c->ev_pool.push_back(e);
+        saved = c->stream;
+        c->stream = crit;
+        on = true;
+    }
+    ~OnCritStream() {
+        if (!on) return;
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(e, c->stream);
+            cudaStreamWaitEvent(saved, e, 0);
+            cudaEventDestroy(e);
+        } else {
+            cudaStreamSynchronize(c->stream);
+        }
+        c->stream = saved;
+    }
+};
+
 template <class T>
 tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_est, void* const* host_out = nullptr,
                    int max_rank = 0, bool fb32_ok = false) {
@@ -762,7 +1126,23 @@ tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_es
         return y;
     }
     for (int attempt = 0;; ++attempt) {
-        Rounder<T> R(ctx, x);
+        // pipelined sweeps on a root context (lanes already overlap whole
+        // roundings), not while profiling (each launch is timed alone), and
+        // only where second passes may be skipped; the sweeps then run on the
+        // context's critical stream, ordered after and before the caller's
+        const bool pipe = attempt == 0 && ctx->pipeline && !ctx->root && !ctx->prof && ctx->use_series &&
+                          !ctx->series_no_skip && !ctx->series_force_retry;
+        OnCritStream cs(ctx, pipe);
+        std::unique_ptr<Rounder<T>> Rp;
+        try {
+            Rp.reset(new Rounder<T>(ctx, x, pipe));
+        } catch (const Error& e) {
+            // a budget that holds the sequential workspace but not the
+            // pipeline's buffers: the sequential sweeps
+            if (!pipe || e.status != TT_ERR_OOM) throw;
+            Rp.reset(new Rounder<T>(ctx, x, false));
+        }
+        Rounder<T>& R = *Rp;
         R.host_out = host_out;
         R.max_rank = max_rank;
         R.fb32_ok = fb32_ok;

@@ -273,6 +273,15 @@ struct Ctx {
 
     cudaStream_t copy_stream = nullptr;  // device-to-host copies overlapping the
                                          // left-to-right sweep (created on first use)
+    // Pipelined sweeps of TT-round (root contexts; off while profiling):
+    // the critical path (Gram, Cholesky, absorb) runs on a high-priority
+    // stream, the applies and second-pass checks on a second stream, and
+    // the host reads each bond's decision from page-locked words
+    bool pipeline = true;
+    cudaStream_t crit_stream = nullptr;
+    cudaStream_t side_stream = nullptr;
+    void* host_words = nullptr;  // kHostWords bytes, page-locked
+    static constexpr size_t kHostWords = 4096;
 
     // event profiling of launches (off by default)
     bool prof = false;
@@ -283,6 +292,9 @@ struct Ctx {
     std::vector<cudaEvent_t> ev_pool;
 
     cudaStream_t copies();  // copy_stream, created on first use
+    cudaStream_t crit();    // crit_stream, created on first use
+    cudaStream_t side();    // side_stream, created on first use
+    void* pinned_words();   // host_words, allocated on first use
     void* alloc(size_t bytes);
     void release(void* p, size_t bytes);
     void sync();

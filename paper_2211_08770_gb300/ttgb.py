@@ -61,6 +61,7 @@ _SIGS = {
     "tt_ctx_set_profiling": (_I, [_P, _I]),
     "tt_ctx_set_profiling_family": (_I, [_P, C.c_char_p]),
     "tt_ctx_set_tc_wait_limit": (_I, [_P, C.c_longlong]),
+    "tt_ctx_set_pipeline": (_I, [_P, _I]),
     "tt_ctx_get_profile": (_I, [_P, C.POINTER(_Prof), _I, _PI]),
     "tt_ctx_reset_profile": (None, [_P]),
     "tt_tensor_create": (_I, [_P, _I, _PI, _PI, C.POINTER(_PD), C.POINTER(_P)]),
@@ -194,6 +195,11 @@ class Ctx:
         """SM-cycle limit of the tensor-core row Gram's bounded waits (0: the
         default, about 2 s)."""
         _check(lib().tt_ctx_set_tc_wait_limit(self._h, int(cycles)), "tt_ctx_set_tc_wait_limit")
+
+    def set_pipeline(self, on=True):
+        """Pipelined (speculative two-stream) sweeps of TT-round on this
+        context (on by default); off: every sweep on the context's stream."""
+        _check(lib().tt_ctx_set_pipeline(self._h, 1 if on else 0), "tt_ctx_set_pipeline")
 
     def set_sign_rule(self, rule):
         _check(lib().tt_set_sign_rule(self._h, SIGN[rule]), "tt_set_sign_rule")
