@@ -166,8 +166,10 @@ tt_status tt_ctx_set_tc_wait_limit(tt_ctx* ctx, long long cycles);
  * their buffers) and redone sequentially, so the results are those of the
  * sequential sweeps.  The pipeline holds four more core-sized buffers; when
  * the context's HBM budget does not allow them the rounding runs
- * sequentially.  Profiling (tt_ctx_set_profiling) runs sequentially too, so
- * that each launch is timed alone.  The rounding stays ordered on the
+ * sequentially.  Profiling of every kernel family (tt_ctx_set_profiling
+ * with no family set) runs sequentially too, so that each launch is timed
+ * alone; timing one family keeps the pipeline, and its launches' events
+ * are recorded on the stream each runs on.  The rounding stays ordered on the
  * context's stream: its internal streams wait for it and it waits for
  * them. */
 tt_status tt_ctx_set_pipeline(tt_ctx* ctx, int on);

@@ -1127,11 +1127,13 @@ tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_es
     }
     for (int attempt = 0;; ++attempt) {
         // pipelined sweeps on a root context (lanes already overlap whole
-        // roundings), not while profiling (each launch is timed alone), and
-        // only where second passes may be skipped; the sweeps then run on the
-        // context's critical stream, ordered after and before the caller's
-        const bool pipe = attempt == 0 && ctx->pipeline && !ctx->root && !ctx->prof && ctx->use_series &&
-                          !ctx->series_no_skip && !ctx->series_force_retry;
+        // roundings), not while every kernel family is being timed (each
+        // launch is then timed alone; timing one family times its launches
+        // where they run), and only where second passes may be skipped; the
+        // sweeps then run on the context's critical stream, ordered after
+        // and before the caller's
+        const bool pipe = attempt == 0 && ctx->pipeline && !ctx->root && !(ctx->prof && ctx->prof_only.empty()) &&
+                          ctx->use_series && !ctx->series_no_skip && !ctx->series_force_retry;
         OnCritStream cs(ctx, pipe);
         std::unique_ptr<Rounder<T>> Rp;
         try {
