@@ -788,7 +788,9 @@ struct Rounder {
         T *x_orig = nullptr, *q = nullptr;         // core k before; Q1
         T *nb_orig = nullptr, *nb_new = nullptr;  // neighbour before; with L1 absorbed
         CholStatus* s0 = nullptr;
-        cudaEvent_t ev_main = nullptr, ev_dec = nullptr;
+        cudaEvent_t ev_mark = nullptr;  // before the bond's first tile kernel
+        cudaEvent_t ev_main = nullptr;  // after the absorb
+        cudaEvent_t ev_dec = nullptr;   // after the checks' copies to the host
     };
     T* take() {
         if (freeb.empty()) throw_status(TT_ERR_ARG, "internal: pipeline buffers exhausted");
@@ -798,9 +800,23 @@ struct Rounder {
     }
     void give(T* b) { freeb.push_back(b); }
     void drop_events(Spec& s) {
-        if (s.ev_main) c->ev_pool.push_back(s.ev_main);
-        if (s.ev_dec) c->ev_pool.push_back(s.ev_dec);
-        s.ev_main = s.ev_dec = nullptr;
+        for (cudaEvent_t* e : {&s.ev_mark, &s.ev_main, &s.ev_dec})
+            if (*e) {
+                c->ev_pool.push_back(*e);
+                *e = nullptr;
+            }
+    }
+    // the bond's factorization, marking the point before its first tile
+    // kernel
+    void chol_marked(Spec& s, int a, const T* Gm) {
+        s.s0 = next_st();
+        s.ev_mark = c->event();
+        struct Unmark {
+            Ctx* c;
+            ~Unmark() { c->chol_mark = nullptr; }
+        } um{c};
+        c->chol_mark = s.ev_mark;
+        chol_inv<T, T>(*c, a, Gm, Lq[s.slot], Tq[s.slot], 0.0, 8.0 * ug_fb * sqrt((double)a), s.s0);
     }
     // launches go to the second stream while alive
     struct OnSide {
@@ -862,7 +878,9 @@ struct Rounder {
         drop_events(s);
     }
 
-    Spec enqueue_rl(int k) {
+    // The critical stream's part of bond k: Gram, Cholesky, absorb into
+    // core k-1 (a fresh buffer)
+    Spec main_rl(int k) {
         Spec s;
         s.k = k;
         s.slot = k & 1;
@@ -874,22 +892,27 @@ struct Rounder {
         s.q = take();
         s.nb_new = take();
         gram_into(true, true, a, K, core[k]);
-        s.s0 = next_st();
-        chol_inv<T, T>(*c, a, G, Lq[s.slot], Tq[s.slot], 0.0, 8.0 * ug_fb * sqrt((double)a), s.s0);
+        chol_marked(s, a, G);
         mm(false, false, M, a, a, core[k - 1], a, Lq[s.slot], a, s.nb_new, a, TRI_B_LOWER, true);
         s.ev_main = c->event();
         TT_CUDA(cudaEventRecord(s.ev_main, c->stream));
-        {
-            OnSide os(c);
-            side_used = true;
-            TT_CUDA(cudaStreamWaitEvent(c->stream, s.ev_main, 0));
-            side_apply(true, a, K, core[k], s.q, s.slot);
-            gram_into(true, K >= kTc2MinK, a, K, s.q, Gq[s.slot]);
-            near_identity<T>(*c, a, Gq[s.slot], Eq[s.slot], dq + 8 * s.slot + 2);
-            post(s);
-        }
         core[k - 1] = s.nb_new;
         return s;
+    }
+
+    // The second stream's part of bond s.k, released by `after` (the next
+    // bond's mark, so that its tile kernel is resident first, or s's own
+    // absorb when no bond follows): Q1, its Gram, E, the host copies
+    void side_rl(Spec& s, cudaEvent_t after) {
+        const int k = s.k, a = r[k];
+        const long K = (long)n[k] * r[k + 1];
+        OnSide os(c);
+        side_used = true;
+        TT_CUDA(cudaStreamWaitEvent(c->stream, after, 0));
+        side_apply(true, a, K, s.x_orig, s.q, s.slot);
+        gram_into(true, K >= kTc2MinK, a, K, s.q, Gq[s.slot]);
+        near_identity<T>(*c, a, Gq[s.slot], Eq[s.slot], dq + 8 * s.slot + 2);
+        post(s);
     }
 
     bool resolve_rl(Spec& s) {
@@ -911,34 +934,45 @@ struct Rounder {
         rl_bond(s.k);
     }
 
+    // Bond k+1's checks are queued after bond k's critical part and read
+    // back while bond k's Cholesky runs
     void rl_sweep_pipelined() {
         Spec prev;
         bool have = false;
         int k = d - 1;
         while (k >= 1) {
             if ((long)n[k] * r[k + 1] <= r[k]) {
-                if (have) settle_rl(prev);
+                if (have) {
+                    side_rl(prev, prev.ev_main);
+                    settle_rl(prev);
+                }
                 have = false;
                 rl_bond(k);
                 --k;
                 continue;
             }
-            Spec cur = enqueue_rl(k);
-            if (have && !resolve_rl(prev)) {
-                rollback(prev, &cur, true);
-                rl_bond(prev.k);
-                have = false;
-                continue;  // bond k again, from the corrected core
+            Spec cur = main_rl(k);
+            if (have) {
+                side_rl(prev, cur.ev_mark);
+                if (!resolve_rl(prev)) {
+                    rollback(prev, &cur, true);
+                    rl_bond(prev.k);
+                    have = false;
+                    continue;  // bond k again, from the corrected core
+                }
             }
             prev = cur;
             have = true;
             --k;
         }
-        if (have) settle_rl(prev);
+        if (have) {
+            side_rl(prev, prev.ev_main);
+            settle_rl(prev);
+        }
         join_side();
     }
 
-    Spec enqueue_lr(int k) {
+    Spec main_lr(int k) {
         Spec s;
         s.k = k;
         s.slot = k & 1;
@@ -949,24 +983,25 @@ struct Rounder {
         s.q = take();
         s.nb_new = take();
         gram_into(false, true, b, m, core[k]);
-        s.s0 = next_st();
-        chol_inv<T, T>(*c, b, G, Lq[s.slot], Tq[s.slot], 0.0, 8.0 * ug_fb * sqrt((double)b), s.s0);
+        chol_marked(s, b, G);
         transpose<T>(*c, b, b, Lq[s.slot], Rq[s.slot]);
         absorb_next(k, b, Rq[s.slot], b, TRI_A_UPPER, s.nb_new);  // core k+1 <- L1^T core k+1
         s.ev_main = c->event();
         TT_CUDA(cudaEventRecord(s.ev_main, c->stream));
-        {
-            OnSide os(c);
-            side_used = true;
-            TT_CUDA(cudaStreamWaitEvent(c->stream, s.ev_main, 0));
-            side_apply(false, b, m, core[k], s.q, s.slot);
-            gram_into(false, m >= kTc2MinK, b, m, s.q, Gq[s.slot]);
-            near_identity<T>(*c, b, Gq[s.slot], Eq[s.slot], dq + 8 * s.slot + 2);
-            TT_CUDA(cudaMemsetAsync(dq + 8 * s.slot, 0, 2 * sizeof(double), c->stream));
-            inv_and_identity_defect<T>(*c, b, Lq[s.slot], Tq[s.slot], dq + 8 * s.slot);
-            post(s);
-        }
         return s;
+    }
+
+    void side_lr(Spec& s, cudaEvent_t after) {
+        const int k = s.k, m = r[k] * n[k], b = r[k + 1];
+        OnSide os(c);
+        side_used = true;
+        TT_CUDA(cudaStreamWaitEvent(c->stream, after, 0));
+        side_apply(false, b, m, s.x_orig, s.q, s.slot);
+        gram_into(false, m >= kTc2MinK, b, m, s.q, Gq[s.slot]);
+        near_identity<T>(*c, b, Gq[s.slot], Eq[s.slot], dq + 8 * s.slot + 2);
+        TT_CUDA(cudaMemsetAsync(dq + 8 * s.slot, 0, 2 * sizeof(double), c->stream));
+        inv_and_identity_defect<T>(*c, b, Lq[s.slot], Tq[s.slot], dq + 8 * s.slot);
+        post(s);
     }
 
     // the certified skip of the sequential path (lr_bond with a series
@@ -1005,26 +1040,35 @@ struct Rounder {
         while (k + 1 < d) {
             const bool spec = r[k] * n[k] >= r[k + 1] && !capped(r[k + 1]) && !pend[k + 1];
             if (!spec) {
-                if (have) settle_lr(prev, eps);
+                if (have) {
+                    side_lr(prev, prev.ev_main);
+                    settle_lr(prev, eps);
+                }
                 have = false;
                 lr_bond(k, eps);
                 stream_core(k);
                 ++k;
                 continue;
             }
-            Spec cur = enqueue_lr(k);
-            if (have && !resolve_lr(prev, eps)) {
-                rollback(prev, &cur, false);
-                lr_bond(prev.k, eps);
-                stream_core(prev.k);
-                have = false;
-                continue;  // bond k again, from the corrected core
+            Spec cur = main_lr(k);
+            if (have) {
+                side_lr(prev, cur.ev_mark);
+                if (!resolve_lr(prev, eps)) {
+                    rollback(prev, &cur, false);
+                    lr_bond(prev.k, eps);
+                    stream_core(prev.k);
+                    have = false;
+                    continue;  // bond k again, from the corrected core
+                }
             }
             prev = cur;
             have = true;
             ++k;
         }
-        if (have) settle_lr(prev, eps);
+        if (have) {
+            side_lr(prev, prev.ev_main);
+            settle_lr(prev, eps);
+        }
         join_side();
         stream_core(d - 1);
     }

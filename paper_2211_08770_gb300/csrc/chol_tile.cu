@@ -715,6 +715,13 @@ void launch_tile(Ctx& c, const TileArgs<S>& a) {
     TT_LAUNCHED(c);
 }
 
+void mark_chol(Ctx& c) {
+    if (!c.chol_mark) return;
+    cudaEvent_t e = c.chol_mark;
+    c.chol_mark = nullptr;
+    TT_CUDA(cudaEventRecord(e, c.stream));
+}
+
 template <class S, class C>
 void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, double drop_rel, CholStatus* st) {
     const int m = (n + nb - 1) / nb;
@@ -731,6 +738,7 @@ void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, do
     const int cb = std::min(2 * c.sm_count, (int)(((long)n * n + 255) / 256));
     chol_prep_kernel<S><<<std::max(cb, 1), 256, 0, c.stream>>>(n, G, shift_rel, drop_rel, ext, st, L, T);
     TT_LAUNCHED(c);
+    mark_chol(c);
     const long ld = n;
     for (int j = 0; j < m; ++j) {
         const int j0 = j * nb, b = std::min(nb, n - j0), j1 = j0 + b, M = n - j1;
@@ -789,6 +797,7 @@ void chol_inv_nb(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel
     const int nmax = chol_tile_max<S, C>();
     if (nb >= n && n <= nmax) {
         TileArgs<S> a{n, G, n, L, n, T, n, G, (long)n + 1, shift_rel, drop_rel, nullptr, st};
+        mark_chol(c);
         launch_tile<S, C>(c, a);
     } else {
         blocked<S, C>(c, n, std::max(32, std::min(nb, nmax)), G, L, T, shift_rel, drop_rel, st);

@@ -278,6 +278,11 @@ struct Ctx {
     // stream, the applies and second-pass checks on a second stream, and
     // the host reads each bond's decision from page-locked words
     bool pipeline = true;
+    // when set, the next chol_inv records it on the stream just before its
+    // first single-CTA tile kernel (after the factor's preparation), then
+    // clears it: the pipelined sweeps release the previous bond's checks
+    // there, so the tile kernel holds its SM before they fill the GPU
+    cudaEvent_t chol_mark = nullptr;
     cudaStream_t crit_stream = nullptr;
     cudaStream_t side_stream = nullptr;
     void* host_words = nullptr;  // kHostWords bytes, page-locked
