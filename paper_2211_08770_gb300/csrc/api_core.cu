@@ -98,6 +98,11 @@ cudaStream_t Ctx::side() {
     return side_stream;
 }
 
+cudaStream_t Ctx::tail() {
+    if (!tail_stream) TT_CUDA(cudaStreamCreateWithFlags(&tail_stream, cudaStreamNonBlocking));
+    return tail_stream;
+}
+
 void* Ctx::pinned_words() {
     if (!host_words) TT_CUDA(cudaHostAlloc(&host_words, kHostWords, cudaHostAllocDefault));
     return host_words;
@@ -108,7 +113,7 @@ Ctx::~Ctx() {
         cudaStreamSynchronize(copy_stream);
         cudaStreamDestroy(copy_stream);
     }
-    for (cudaStream_t* s : {&crit_stream, &side_stream})
+    for (cudaStream_t* s : {&crit_stream, &side_stream, &tail_stream})
         if (*s) {
             cudaStreamSynchronize(*s);
             cudaStreamDestroy(*s);

@@ -125,14 +125,16 @@ struct Rounder {
     ~Rounder() {
         // the second stream's work and the host copies still reading the
         // workspace's cores finish first
-        if (side_used) {
+        for (int i = 0; i < 2; ++i) {
+            if (!(i == 0 ? side_used : tail_used)) continue;
+            cudaStream_t sj = i == 0 ? c->side_stream : c->tail_stream;
             cudaEvent_t e = nullptr;
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
-                cudaEventRecord(e, c->side_stream);
+                cudaEventRecord(e, sj);
                 cudaStreamWaitEvent(c->stream, e, 0);
                 cudaEventDestroy(e);
             } else {
-                cudaStreamSynchronize(c->side_stream);
+                cudaStreamSynchronize(sj);
             }
         }
         if (copied) cudaStreamSynchronize(c->copy_stream);
@@ -774,6 +776,7 @@ struct Rounder {
     // sequential path's skip.
     bool pipe = false;
     bool side_used = false;
+    bool tail_used = false;
     static constexpr int kPool = 4;  // two bonds in flight, two fresh cores each
     std::vector<T*> freeb;           // free core buffers of the pipeline
     T *Lq[2] = {}, *Tq[2] = {}, *Gq[2] = {}, *Eq[2] = {}, *Rq[2] = {};  // per bond parity
@@ -789,6 +792,7 @@ struct Rounder {
         T *nb_orig = nullptr, *nb_new = nullptr;  // neighbour before; with L1 absorbed
         CholStatus* s0 = nullptr;
         cudaEvent_t ev_mark = nullptr;  // before the bond's first tile kernel
+        cudaEvent_t ev_tail = nullptr;  // after its inverse's tail (tail stream)
         cudaEvent_t ev_main = nullptr;  // after the absorb
         cudaEvent_t ev_dec = nullptr;   // after the checks' copies to the host
     };
@@ -800,23 +804,31 @@ struct Rounder {
     }
     void give(T* b) { freeb.push_back(b); }
     void drop_events(Spec& s) {
-        for (cudaEvent_t* e : {&s.ev_mark, &s.ev_main, &s.ev_dec})
+        for (cudaEvent_t* e : {&s.ev_mark, &s.ev_tail, &s.ev_main, &s.ev_dec})
             if (*e) {
                 c->ev_pool.push_back(*e);
                 *e = nullptr;
             }
     }
     // the bond's factorization, marking the point before its first tile
-    // kernel
+    // kernel; a blocked factorization leaves its inverse's off-diagonal
+    // blocks to the tail stream (only the second stream's work reads them)
     void chol_marked(Spec& s, int a, const T* Gm) {
         s.s0 = next_st();
         s.ev_mark = c->event();
         struct Unmark {
             Ctx* c;
-            ~Unmark() { c->chol_mark = nullptr; }
+            ~Unmark() {
+                c->chol_mark = nullptr;
+                c->chol_tail = nullptr;
+            }
         } um{c};
         c->chol_mark = s.ev_mark;
+        c->chol_tail = c->tail();
+        tail_used = true;
         chol_inv<T, T>(*c, a, Gm, Lq[s.slot], Tq[s.slot], 0.0, 8.0 * ug_fb * sqrt((double)a), s.s0);
+        s.ev_tail = c->event();
+        TT_CUDA(cudaEventRecord(s.ev_tail, c->tail()));
     }
     // launches go to the second stream while alive
     struct OnSide {
@@ -825,13 +837,16 @@ struct Rounder {
         explicit OnSide(Ctx* cc) : c(cc), saved(cc->stream) { c->stream = c->side(); }
         ~OnSide() { c->stream = saved; }
     };
-    // the critical stream waits for everything queued on the second one
+    // the critical stream waits for everything queued on the second and
+    // tail streams
     void join_side() {
-        if (!side_used) return;
-        cudaEvent_t e = c->event();
-        TT_CUDA(cudaEventRecord(e, c->side()));
-        TT_CUDA(cudaStreamWaitEvent(c->stream, e, 0));
-        c->ev_pool.push_back(e);
+        for (int i = 0; i < 2; ++i) {
+            if (!(i == 0 ? side_used : tail_used)) continue;
+            cudaEvent_t e = c->event();
+            TT_CUDA(cudaEventRecord(e, i == 0 ? c->side() : c->tail()));
+            TT_CUDA(cudaStreamWaitEvent(c->stream, e, 0));
+            c->ev_pool.push_back(e);
+        }
     }
     // Q = L1^{-1} X (rows) or X L1^{-T} (cols), as apply_factor does it
     void side_apply(bool rows, int a, long K, const T* X, T* Q, int slot) {
@@ -909,6 +924,7 @@ struct Rounder {
         OnSide os(c);
         side_used = true;
         TT_CUDA(cudaStreamWaitEvent(c->stream, after, 0));
+        TT_CUDA(cudaStreamWaitEvent(c->stream, s.ev_tail, 0));
         side_apply(true, a, K, s.x_orig, s.q, s.slot);
         gram_into(true, K >= kTc2MinK, a, K, s.q, Gq[s.slot]);
         near_identity<T>(*c, a, Gq[s.slot], Eq[s.slot], dq + 8 * s.slot + 2);
@@ -996,6 +1012,7 @@ struct Rounder {
         OnSide os(c);
         side_used = true;
         TT_CUDA(cudaStreamWaitEvent(c->stream, after, 0));
+        TT_CUDA(cudaStreamWaitEvent(c->stream, s.ev_tail, 0));
         side_apply(false, b, m, s.x_orig, s.q, s.slot);
         gram_into(false, m >= kTc2MinK, b, m, s.q, Gq[s.slot]);
         near_identity<T>(*c, b, Gq[s.slot], Eq[s.slot], dq + 8 * s.slot + 2);

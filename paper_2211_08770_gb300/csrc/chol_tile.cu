@@ -727,12 +727,19 @@ void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, do
     const int m = (n + nb - 1) / nb;
     const size_t wbytes = sizeof(S) * (size_t)n * nb + 2 * sizeof(double) + 256;
     char* ws = (char*)c.alloc(wbytes);
+    // released on the stream of the last products that read it
     struct Rel {
         Ctx& c;
         void* p;
         size_t b;
-        ~Rel() { c.release(p, b); }
-    } rel{c, ws, wbytes};
+        cudaStream_t on;
+        ~Rel() {
+            const cudaStream_t s0 = c.stream;
+            c.stream = on;
+            c.release(p, b);
+            c.stream = s0;
+        }
+    } rel{c, ws, wbytes, c.stream};
     double* ext = (double*)ws;
     S* W = (S*)(ws + 256);
     const int cb = std::min(2 * c.sm_count, (int)(((long)n * n + 255) / 256));
@@ -755,7 +762,22 @@ void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, do
         gemm<S>(c, false, true, M, M, b, S(-1), W, b, W, b, S(1), L + j1 * (ld + 1), ld, 1, 0, 0, 0, TRI_C_LOWER);
     }
     // off-diagonal inverse blocks, last block column first:
-    // T_{>j,j} = -T_{>j,>j} (L_{>j,j} T_jj)
+    // T_{>j,j} = -T_{>j,>j} (L_{>j,j} T_jj); on the context's tail stream
+    // when one is set (L is final here: only T's readers wait for them)
+    cudaStream_t saved = c.stream;
+    if (c.chol_tail && m >= 2) {
+        cudaEvent_t e = c.event();
+        TT_CUDA(cudaEventRecord(e, c.stream));
+        TT_CUDA(cudaStreamWaitEvent(c.chol_tail, e, 0));
+        c.ev_pool.push_back(e);
+        c.stream = c.chol_tail;
+        rel.on = c.chol_tail;
+    }
+    struct Restore {
+        Ctx& c;
+        cudaStream_t s;
+        ~Restore() { c.stream = s; }
+    } restore{c, saved};
     for (int j = m - 2; j >= 0; --j) {
         const int j0 = j * nb, b = std::min(nb, n - j0), j1 = j0 + b, M = n - j1;
         gemm<S>(c, false, false, M, b, b, S(1), L + j1 * ld + j0, ld, T + j0 * (ld + 1), ld, S(0), W, b, 1, 0, 0, 0,

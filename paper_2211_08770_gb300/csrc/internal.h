@@ -283,8 +283,12 @@ struct Ctx {
     // clears it: the pipelined sweeps release the previous bond's checks
     // there, so the tile kernel holds its SM before they fill the GPU
     cudaEvent_t chol_mark = nullptr;
+    // when set, a blocked chol_inv computes the off-diagonal blocks of the
+    // inverse on this stream (after L is final) instead of the context's
+    cudaStream_t chol_tail = nullptr;
     cudaStream_t crit_stream = nullptr;
     cudaStream_t side_stream = nullptr;
+    cudaStream_t tail_stream = nullptr;  // the factorizations' inverse tails
     void* host_words = nullptr;  // kHostWords bytes, page-locked
     static constexpr size_t kHostWords = 4096;
 
@@ -299,6 +303,7 @@ struct Ctx {
     cudaStream_t copies();  // copy_stream, created on first use
     cudaStream_t crit();    // crit_stream, created on first use
     cudaStream_t side();    // side_stream, created on first use
+    cudaStream_t tail();    // tail_stream, created on first use
     void* pinned_words();   // host_words, allocated on first use
     void* alloc(size_t bytes);
     void release(void* p, size_t bytes);
