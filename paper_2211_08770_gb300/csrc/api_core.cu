@@ -93,6 +93,15 @@ cudaStream_t Ctx::crit() {
     return crit_stream;
 }
 
+cudaStream_t Ctx::crit2() {
+    if (!crit2_stream) {
+        int least = 0, greatest = 0;
+        TT_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        TT_CUDA(cudaStreamCreateWithPriority(&crit2_stream, cudaStreamNonBlocking, greatest));
+    }
+    return crit2_stream;
+}
+
 cudaStream_t Ctx::side() {
     if (!side_stream) TT_CUDA(cudaStreamCreateWithFlags(&side_stream, cudaStreamNonBlocking));
     return side_stream;
@@ -113,7 +122,7 @@ Ctx::~Ctx() {
         cudaStreamSynchronize(copy_stream);
         cudaStreamDestroy(copy_stream);
     }
-    for (cudaStream_t* s : {&crit_stream, &side_stream, &tail_stream})
+    for (cudaStream_t* s : {&crit_stream, &crit2_stream, &side_stream, &tail_stream})
         if (*s) {
             cudaStreamSynchronize(*s);
             cudaStreamDestroy(*s);

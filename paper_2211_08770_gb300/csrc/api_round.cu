@@ -125,9 +125,9 @@ struct Rounder {
     ~Rounder() {
         // the second stream's work and the host copies still reading the
         // workspace's cores finish first
-        for (int i = 0; i < 2; ++i) {
-            if (!(i == 0 ? side_used : tail_used)) continue;
-            cudaStream_t sj = i == 0 ? c->side_stream : c->tail_stream;
+        for (int i = 0; i < 3; ++i) {
+            if (!(i == 0 ? side_used : i == 1 ? tail_used : crit2_used)) continue;
+            cudaStream_t sj = i == 0 ? c->side_stream : i == 1 ? c->tail_stream : c->crit2_stream;
             cudaEvent_t e = nullptr;
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
                 cudaEventRecord(e, sj);
@@ -777,6 +777,7 @@ struct Rounder {
     bool pipe = false;
     bool side_used = false;
     bool tail_used = false;
+    bool crit2_used = false;
     static constexpr int kPool = 4;  // two bonds in flight, two fresh cores each
     std::vector<T*> freeb;           // free core buffers of the pipeline
     T *Lq[2] = {}, *Tq[2] = {}, *Gq[2] = {}, *Eq[2] = {}, *Rq[2] = {};  // per bond parity
@@ -793,6 +794,9 @@ struct Rounder {
         CholStatus* s0 = nullptr;
         cudaEvent_t ev_mark = nullptr;  // before the bond's first tile kernel
         cudaEvent_t ev_tail = nullptr;  // after its inverse's tail (tail stream)
+        cudaEvent_t ev_col = nullptr;   // L's first block column final (critical stream)
+        cudaEvent_t ev_p0 = nullptr;    // after the absorb's first part (crit2 stream)
+        int split = 0;                  // columns of that block (0: no split)
         cudaEvent_t ev_main = nullptr;  // after the absorb
         cudaEvent_t ev_dec = nullptr;   // after the checks' copies to the host
     };
@@ -804,7 +808,7 @@ struct Rounder {
     }
     void give(T* b) { freeb.push_back(b); }
     void drop_events(Spec& s) {
-        for (cudaEvent_t* e : {&s.ev_mark, &s.ev_tail, &s.ev_main, &s.ev_dec})
+        for (cudaEvent_t* e : {&s.ev_mark, &s.ev_tail, &s.ev_col, &s.ev_p0, &s.ev_main, &s.ev_dec})
             if (*e) {
                 c->ev_pool.push_back(*e);
                 *e = nullptr;
@@ -821,14 +825,51 @@ struct Rounder {
             ~Unmark() {
                 c->chol_mark = nullptr;
                 c->chol_tail = nullptr;
+                c->chol_mark2 = nullptr;
             }
         } um{c};
         c->chol_mark = s.ev_mark;
         c->chol_tail = c->tail();
+        s.ev_col = c->event();
+        c->chol_mark2 = s.ev_col;
+        c->chol_split = 0;
         tail_used = true;
         chol_inv<T, T>(*c, a, Gm, Lq[s.slot], Tq[s.slot], 0.0, 8.0 * ug_fb * sqrt((double)a), s.s0);
+        s.split = c->chol_split;
         s.ev_tail = c->event();
         TT_CUDA(cudaEventRecord(s.ev_tail, c->tail()));
+    }
+
+    // launches go to the crit2 stream while alive
+    struct OnCrit2 {
+        Ctx* c;
+        cudaStream_t saved;
+        explicit OnCrit2(Ctx* cc) : c(cc), saved(cc->stream) { c->stream = c->crit2(); }
+        ~OnCrit2() { c->stream = saved; }
+    };
+    // The absorb of a blocked factorization in two parts: the columns (RL)
+    // or rows (LR) of its first block, which need only L's first block
+    // column, on the crit2 stream from the moment that column is final
+    // (beside the remaining tile kernels), then the rest on the critical
+    // stream, which then waits for the first part.  rl: Y = X L with X
+    // (M x a); !rl: Z = L^T C with C (a x NR).
+    void split_absorb(Spec& s, bool rl, int M, int a, long NR, const T* X, T* Y) {
+        const int p = s.split;
+        const T* L = Lq[s.slot];
+        {
+            OnCrit2 o(c);
+            crit2_used = true;
+            TT_CUDA(cudaStreamWaitEvent(c->stream, s.ev_col, 0));
+            if (rl) mm(false, false, M, p, a, X, a, L, a, Y, a, TRI_B_LOWER, true);
+            else mm(true, false, p, (int)NR, a, L, a, X, NR, Y, NR, TRI_A_UPPER, true);
+            s.ev_p0 = c->event();
+            TT_CUDA(cudaEventRecord(s.ev_p0, c->stream));
+        }
+        const int q = a - p;
+        if (rl) mm(false, false, M, q, q, X + p, a, L + (long)p * a + p, a, Y + p, a, TRI_B_LOWER, true);
+        else mm(true, false, q, (int)NR, q, L + (long)p * a + p, a, X + (long)p * NR, NR, Y + (long)p * NR, NR,
+                TRI_A_UPPER, true);
+        TT_CUDA(cudaStreamWaitEvent(c->stream, s.ev_p0, 0));
     }
     // launches go to the second stream while alive
     struct OnSide {
@@ -837,13 +878,13 @@ struct Rounder {
         explicit OnSide(Ctx* cc) : c(cc), saved(cc->stream) { c->stream = c->side(); }
         ~OnSide() { c->stream = saved; }
     };
-    // the critical stream waits for everything queued on the second and
-    // tail streams
+    // the critical stream waits for everything queued on the second, tail
+    // and crit2 streams
     void join_side() {
-        for (int i = 0; i < 2; ++i) {
-            if (!(i == 0 ? side_used : tail_used)) continue;
+        for (int i = 0; i < 3; ++i) {
+            if (!(i == 0 ? side_used : i == 1 ? tail_used : crit2_used)) continue;
             cudaEvent_t e = c->event();
-            TT_CUDA(cudaEventRecord(e, i == 0 ? c->side() : c->tail()));
+            TT_CUDA(cudaEventRecord(e, i == 0 ? c->side() : i == 1 ? c->tail() : c->crit2()));
             TT_CUDA(cudaStreamWaitEvent(c->stream, e, 0));
             c->ev_pool.push_back(e);
         }
@@ -908,7 +949,8 @@ struct Rounder {
         s.nb_new = take();
         gram_into(true, true, a, K, core[k]);
         chol_marked(s, a, G);
-        mm(false, false, M, a, a, core[k - 1], a, Lq[s.slot], a, s.nb_new, a, TRI_B_LOWER, true);
+        if (s.split > 0 && s.split < a) split_absorb(s, true, M, a, 0, core[k - 1], s.nb_new);
+        else mm(false, false, M, a, a, core[k - 1], a, Lq[s.slot], a, s.nb_new, a, TRI_B_LOWER, true);
         s.ev_main = c->event();
         TT_CUDA(cudaEventRecord(s.ev_main, c->stream));
         core[k - 1] = s.nb_new;
@@ -1000,8 +1042,14 @@ struct Rounder {
         s.nb_new = take();
         gram_into(false, true, b, m, core[k]);
         chol_marked(s, b, G);
-        transpose<T>(*c, b, b, Lq[s.slot], Rq[s.slot]);
-        absorb_next(k, b, Rq[s.slot], b, TRI_A_UPPER, s.nb_new);  // core k+1 <- L1^T core k+1
+        // core k+1 <- L1^T core k+1
+        if (s.split > 0 && s.split < b) {
+            split_absorb(s, false, 0, b, (long)n[k + 1] * r[k + 2], core[k + 1], s.nb_new);
+            core[k + 1] = s.nb_new;
+        } else {
+            transpose<T>(*c, b, b, Lq[s.slot], Rq[s.slot]);
+            absorb_next(k, b, Rq[s.slot], b, TRI_A_UPPER, s.nb_new);
+        }
         s.ev_main = c->event();
         TT_CUDA(cudaEventRecord(s.ev_main, c->stream));
         return s;

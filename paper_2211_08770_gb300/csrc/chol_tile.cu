@@ -758,6 +758,13 @@ void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, do
                 TRI_B_UPPER);
         TT_CUDA(cudaMemcpy2DAsync(L + j1 * ld + j0, ld * sizeof(S), W, b * sizeof(S), b * sizeof(S), M,
                                   cudaMemcpyDeviceToDevice, c.stream));
+        if (j == 0 && c.chol_mark2) {
+            // L's first block column is final (later steps write columns >= b)
+            cudaEvent_t e = c.chol_mark2;
+            c.chol_mark2 = nullptr;
+            TT_CUDA(cudaEventRecord(e, c.stream));
+            c.chol_split = b;
+        }
         // lower triangle only (the strictly upper part of L is zeroed at the end)
         gemm<S>(c, false, true, M, M, b, S(-1), W, b, W, b, S(1), L + j1 * (ld + 1), ld, 1, 0, 0, 0, TRI_C_LOWER);
     }

@@ -286,9 +286,16 @@ struct Ctx {
     // when set, a blocked chol_inv computes the off-diagonal blocks of the
     // inverse on this stream (after L is final) instead of the context's
     cudaStream_t chol_tail = nullptr;
+    // when set, a blocked chol_inv records it as soon as the first block
+    // column of L (its first chol_split columns) is final, sets chol_split
+    // and clears it; the pipelined sweeps start the absorb's product with
+    // those columns there, beside the remaining tile kernels
+    cudaEvent_t chol_mark2 = nullptr;
+    int chol_split = 0;
     cudaStream_t crit_stream = nullptr;
     cudaStream_t side_stream = nullptr;
     cudaStream_t tail_stream = nullptr;  // the factorizations' inverse tails
+    cudaStream_t crit2_stream = nullptr; // high priority, beside the critical stream
     void* host_words = nullptr;  // kHostWords bytes, page-locked
     static constexpr size_t kHostWords = 4096;
 
@@ -304,6 +311,7 @@ struct Ctx {
     cudaStream_t crit();    // crit_stream, created on first use
     cudaStream_t side();    // side_stream, created on first use
     cudaStream_t tail();    // tail_stream, created on first use
+    cudaStream_t crit2();   // crit2_stream, created on first use
     void* pinned_words();   // host_words, allocated on first use
     void* alloc(size_t bytes);
     void release(void* p, size_t bytes);
