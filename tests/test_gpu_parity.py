@@ -293,7 +293,17 @@ def test_schemes_fp64_match_oracle(ctxs, scheme):
     A = _small_inputs(m=6, seed=3)
     Qo, Ro, no = O.orthogonalize(scheme, A, 1e-8)
     Qg, Rg, ng = T.tt_orthogonalize(c, scheme, [up(c, a) for a in A], 1e-8)
-    _compare_schemes(Qg, Rg, ng, Qo, Ro, no, 1e-11)
+    # Householder's reflector products round nearly dependent sums (54
+    # shifted fallback passes here): the order of the split-K Gram's FP64
+    # atomic sums moves q_4 by 1e-13 to 3.5e-10 from run to run on a GB300
+    # (the other vectors and R by <= 1e-13), so its vectors get 1e-9
+    tol_q = 1e-9 if scheme == "householder" else 1e-11
+    assert ng == no
+    assert np.allclose(Rg, Ro, atol=1e-11 * np.max(np.abs(Ro)))
+    for qg, qo in zip(Qg, Qo):
+        cq = qg.cores()
+        assert O.tt_ranks(cq) == O.tt_ranks(qo)
+        assert O.tt_diff_norm(cq, qo) <= tol_q
 
 
 @pytest.mark.parametrize("scheme", ["mgs2", "cgs2", "householder", "gram"])
