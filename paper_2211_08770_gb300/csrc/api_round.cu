@@ -794,9 +794,9 @@ struct Rounder {
         CholStatus* s0 = nullptr;
         cudaEvent_t ev_mark = nullptr;  // before the bond's first tile kernel
         cudaEvent_t ev_tail = nullptr;  // after its inverse's tail (tail stream)
-        cudaEvent_t ev_col = nullptr;   // L's first block column final (critical stream)
+        cudaEvent_t ev_col = nullptr;   // before the last tile kernel of a blocked factorization
         cudaEvent_t ev_p0 = nullptr;    // after the absorb's first part (crit2 stream)
-        int split = 0;                  // columns of that block (0: no split)
+        int split = 0;                  // L's columns final at ev_col (0: not blocked)
         cudaEvent_t ev_main = nullptr;  // after the absorb
         cudaEvent_t ev_dec = nullptr;   // after the checks' copies to the host
     };
@@ -847,11 +847,15 @@ struct Rounder {
         explicit OnCrit2(Ctx* cc) : c(cc), saved(cc->stream) { c->stream = c->crit2(); }
         ~OnCrit2() { c->stream = saved; }
     };
+    // the point before the bond's last tile kernel (its only one when the
+    // factorization is a single tile)
+    static cudaEvent_t last_mark(const Spec& s) { return s.split > 0 ? s.ev_col : s.ev_mark; }
+
     // The absorb of a blocked factorization in two parts: the columns (RL)
-    // or rows (LR) of its first block, which need only L's first block
-    // column, on the crit2 stream from the moment that column is final
-    // (beside the remaining tile kernels), then the rest on the critical
-    // stream, which then waits for the first part.  rl: Y = X L with X
+    // or rows (LR) left of its last block, which need only L's columns
+    // there, on the crit2 stream from the moment they are final (beside the
+    // last tile kernel), then the rest on the critical stream, which then
+    // waits for the first part.  rl: Y = X L with X
     // (M x a); !rl: Z = L^T C with C (a x NR).
     void split_absorb(Spec& s, bool rl, int M, int a, long NR, const T* X, T* Y) {
         const int p = s.split;
@@ -957,17 +961,19 @@ struct Rounder {
         return s;
     }
 
-    // The second stream's part of bond s.k, released by `after` (the next
-    // bond's mark, so that its tile kernel is resident first, or s's own
-    // absorb when no bond follows): Q1, its Gram, E, the host copies
-    void side_rl(Spec& s, cudaEvent_t after) {
+    // The second stream's part of bond s.k: Q1 released by `after1`, its
+    // Gram, E and the host copies by `after2` (the next bond's first and
+    // last tile kernels, so that each of those holds its SM before this
+    // work fills the GPU; s's own absorb when no bond follows)
+    void side_rl(Spec& s, cudaEvent_t after1, cudaEvent_t after2) {
         const int k = s.k, a = r[k];
         const long K = (long)n[k] * r[k + 1];
         OnSide os(c);
         side_used = true;
-        TT_CUDA(cudaStreamWaitEvent(c->stream, after, 0));
+        TT_CUDA(cudaStreamWaitEvent(c->stream, after1, 0));
         TT_CUDA(cudaStreamWaitEvent(c->stream, s.ev_tail, 0));
         side_apply(true, a, K, s.x_orig, s.q, s.slot);
+        TT_CUDA(cudaStreamWaitEvent(c->stream, after2, 0));
         gram_into(true, K >= kTc2MinK, a, K, s.q, Gq[s.slot]);
         near_identity<T>(*c, a, Gq[s.slot], Eq[s.slot], dq + 8 * s.slot + 2);
         post(s);
@@ -1001,7 +1007,7 @@ struct Rounder {
         while (k >= 1) {
             if ((long)n[k] * r[k + 1] <= r[k]) {
                 if (have) {
-                    side_rl(prev, prev.ev_main);
+                    side_rl(prev, prev.ev_main, prev.ev_main);
                     settle_rl(prev);
                 }
                 have = false;
@@ -1011,7 +1017,7 @@ struct Rounder {
             }
             Spec cur = main_rl(k);
             if (have) {
-                side_rl(prev, cur.ev_mark);
+                side_rl(prev, cur.ev_mark, last_mark(cur));
                 if (!resolve_rl(prev)) {
                     rollback(prev, &cur, true);
                     rl_bond(prev.k);
@@ -1024,7 +1030,7 @@ struct Rounder {
             --k;
         }
         if (have) {
-            side_rl(prev, prev.ev_main);
+            side_rl(prev, prev.ev_main, prev.ev_main);
             settle_rl(prev);
         }
         join_side();
@@ -1055,13 +1061,14 @@ struct Rounder {
         return s;
     }
 
-    void side_lr(Spec& s, cudaEvent_t after) {
+    void side_lr(Spec& s, cudaEvent_t after1, cudaEvent_t after2) {
         const int k = s.k, m = r[k] * n[k], b = r[k + 1];
         OnSide os(c);
         side_used = true;
-        TT_CUDA(cudaStreamWaitEvent(c->stream, after, 0));
+        TT_CUDA(cudaStreamWaitEvent(c->stream, after1, 0));
         TT_CUDA(cudaStreamWaitEvent(c->stream, s.ev_tail, 0));
         side_apply(false, b, m, s.x_orig, s.q, s.slot);
+        TT_CUDA(cudaStreamWaitEvent(c->stream, after2, 0));
         gram_into(false, m >= kTc2MinK, b, m, s.q, Gq[s.slot]);
         near_identity<T>(*c, b, Gq[s.slot], Eq[s.slot], dq + 8 * s.slot + 2);
         TT_CUDA(cudaMemsetAsync(dq + 8 * s.slot, 0, 2 * sizeof(double), c->stream));
@@ -1106,7 +1113,7 @@ struct Rounder {
             const bool spec = r[k] * n[k] >= r[k + 1] && !capped(r[k + 1]) && !pend[k + 1];
             if (!spec) {
                 if (have) {
-                    side_lr(prev, prev.ev_main);
+                    side_lr(prev, prev.ev_main, prev.ev_main);
                     settle_lr(prev, eps);
                 }
                 have = false;
@@ -1117,7 +1124,7 @@ struct Rounder {
             }
             Spec cur = main_lr(k);
             if (have) {
-                side_lr(prev, cur.ev_mark);
+                side_lr(prev, cur.ev_mark, last_mark(cur));
                 if (!resolve_lr(prev, eps)) {
                     rollback(prev, &cur, false);
                     lr_bond(prev.k, eps);
@@ -1131,7 +1138,7 @@ struct Rounder {
             ++k;
         }
         if (have) {
-            side_lr(prev, prev.ev_main);
+            side_lr(prev, prev.ev_main, prev.ev_main);
             settle_lr(prev, eps);
         }
         join_side();

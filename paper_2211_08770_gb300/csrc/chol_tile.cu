@@ -751,6 +751,14 @@ void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, do
         const int j0 = j * nb, b = std::min(nb, n - j0), j1 = j0 + b, M = n - j1;
         TileArgs<S> a{b, L + j0 * (ld + 1), ld, L + j0 * (ld + 1), ld, T + j0 * (ld + 1), ld,
                       G + j0 * (ld + 1), ld + 1, 0.0, 0.0, ext, st};
+        if (M == 0 && j > 0 && c.chol_mark2) {
+            // before the last tile kernel: L's columns left of this block are
+            // final (the last block writes only its own columns)
+            cudaEvent_t e = c.chol_mark2;
+            c.chol_mark2 = nullptr;
+            TT_CUDA(cudaEventRecord(e, c.stream));
+            c.chol_split = j0;
+        }
         launch_tile<S, C>(c, a);
         if (M == 0) break;
         // panel L_{>j,j} = A_{>j,j} T_jj^T (via W), then the trailing update
@@ -758,13 +766,6 @@ void blocked(Ctx& c, int n, int nb, const S* G, S* L, S* T, double shift_rel, do
                 TRI_B_UPPER);
         TT_CUDA(cudaMemcpy2DAsync(L + j1 * ld + j0, ld * sizeof(S), W, b * sizeof(S), b * sizeof(S), M,
                                   cudaMemcpyDeviceToDevice, c.stream));
-        if (j == 0 && c.chol_mark2) {
-            // L's first block column is final (later steps write columns >= b)
-            cudaEvent_t e = c.chol_mark2;
-            c.chol_mark2 = nullptr;
-            TT_CUDA(cudaEventRecord(e, c.stream));
-            c.chol_split = b;
-        }
         // lower triangle only (the strictly upper part of L is zeroed at the end)
         gemm<S>(c, false, true, M, M, b, S(-1), W, b, W, b, S(1), L + j1 * (ld + 1), ld, 1, 0, 0, 0, TRI_C_LOWER);
     }

@@ -286,10 +286,11 @@ struct Ctx {
     // when set, a blocked chol_inv computes the off-diagonal blocks of the
     // inverse on this stream (after L is final) instead of the context's
     cudaStream_t chol_tail = nullptr;
-    // when set, a blocked chol_inv records it as soon as the first block
-    // column of L (its first chol_split columns) is final, sets chol_split
-    // and clears it; the pipelined sweeps start the absorb's product with
-    // those columns there, beside the remaining tile kernels
+    // when set, a blocked chol_inv records it just before its last tile
+    // kernel, when L's columns left of the last block (the first chol_split
+    // columns) are final, sets chol_split and clears it; the pipelined
+    // sweeps start the absorb's product with those columns there, beside
+    // the last tile kernel
     cudaEvent_t chol_mark2 = nullptr;
     int chol_split = 0;
     cudaStream_t crit_stream = nullptr;

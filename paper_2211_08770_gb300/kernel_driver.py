@@ -8,6 +8,8 @@ profiling it in isolation (e.g. under ncu):
     python -m paper_2211_08770_gb300.kernel_driver rgemm  # r x r product, 400 x 400 x 400 (FP32)
     python -m paper_2211_08770_gb300.kernel_driver matvec # Laplacian TT-matrix x rank-400 TT (d = 5, n = 64)
     python -m paper_2211_08770_gb300.kernel_driver dotstack  # CGS2 passes against 48 rank-4 vectors (stacked dots)
+    python -m paper_2211_08770_gb300.kernel_driver pipeline  # single-rounding step, sweeps pipelined vs sequential:
+                                                             # ms per step and in-step device time per kernel family
 
 The shapes are the interior bond of the single-rounding workload (20 summed
 rank-20 TTs, n = 64: rank 400, unfolding length 64 x 400)."""
@@ -61,11 +63,59 @@ def main(which, r=400, K=25600, n=256):
         A = [T.tt_tensor_create(c, q) for q in Q] + [
             T.tt_tensor_create(c, random_tt(rng, [64] * 10, [1] + [60] * 9 + [1], scale="unit-core"))]
         T.tt_orthogonalize(c, "cgs2", A, 1e-6)
+    elif which == "pipeline":
+        pipeline_families()
     else:
-        raise SystemExit("usage: kernel_driver gemm|gram|chol|chol400|rgemm|matvec|dotstack")
+        raise SystemExit("usage: kernel_driver gemm|gram|chol|chol400|rgemm|matvec|dotstack|pipeline")
     torch.cuda.synchronize()
     c.close()
     print("ok", which)
+
+
+def pipeline_families(steps=10):
+    """ms per step of the single-rounding workload (tt_add + tt_round(1e-6),
+    mixed) with the sweeps pipelined and sequential, and for each timed
+    kernel family (timed alone, in its own pass) its device time per step."""
+    import json
+    from ttinputs import cfg_round_sum
+    al, xs = cfg_round_sum(0)
+    stream = torch.cuda.Stream()
+    out = {}
+    for pipe in (True, False):
+        for fam in (None, "chol_inv", "sgemm_f32", "gram_tf32_tc"):
+            c = T.Ctx(0, "mixed_tf32", stream=stream.cuda_stream)
+            c.set_pipeline(pipe)
+            X = [T.tt_tensor_create(c, x) for x in xs]
+
+            def step():
+                s = T.tt_add(c, al, X)
+                y, _ = T.tt_round(c, s, 1e-6)
+                s.free()
+                y.free()
+
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    step()
+            torch.cuda.synchronize()
+            c.reset_profile()
+            if fam:
+                c.set_profiling(True, family=fam)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(steps):
+                    step()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            prof = c.profile() if fam else {}
+            c.set_profiling(False)
+            out["%s/%s" % ("pipelined" if pipe else "sequential", fam or "step")] = dict(
+                ms_per_step=e0.elapsed_time(e1) / steps,
+                family_ms_per_step={k: v["total_ms"] / steps for k, v in prof.items()})
+            for x in X:
+                x.free()
+            c.close()
+    print(json.dumps(out, indent=1))
 
 
 if __name__ == "__main__":
