@@ -161,10 +161,11 @@ tt_status tt_ctx_set_tc_wait_limit(tt_ctx* ctx, long long cycles);
  * pass will be skipped: the factor is absorbed into the next core on a
  * high-priority stream as soon as the factorization ends, while the
  * product Q = L^{-1} X and the checks of the second pass run on a second
- * stream, and the host reads the checks after the next bond is queued.  A
- * bond that fails them is undone (both streams drain, the cores return to
- * their buffers) and redone sequentially, so the results are those of the
- * sequential sweeps.  The pipeline holds four more core-sized buffers; when
+ * stream, and the host reads the checks once the next two bonds are
+ * queued.  A bond that fails them is undone with the bonds queued after it
+ * (the streams drain, the cores return to their buffers) and redone
+ * sequentially, so the results are those of the sequential sweeps.  The
+ * pipeline holds six more core-sized buffers; when
  * the context's HBM budget does not allow them the rounding runs
  * sequentially.  Profiling of every kernel family (tt_ctx_set_profiling
  * with no family set) runs sequentially too, so that each launch is timed

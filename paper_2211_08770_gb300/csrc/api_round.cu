@@ -25,6 +25,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <deque>
 #include <memory>
 #include <vector>
 
@@ -108,7 +109,7 @@ struct Rounder {
         p += al((size_t)st_cap * sizeof(CholStatus));
         if (pipe) {
             for (int i = 0; i < kPool; ++i) { freeb.push_back((T*)p); p += core_b; }
-            for (int i = 0; i < 2; ++i) {
+            for (int i = 0; i < kDepth; ++i) {
                 Lq[i] = (T*)p; p += small_b;
                 Tq[i] = (T*)p; p += small_b;
                 Gq[i] = (T*)p; p += small_b;
@@ -167,15 +168,16 @@ struct Rounder {
 
     // bytes of the workspace carved in the constructor (d + 1 core buffers,
     // 12 + d r x r matrices, Jacobi work, singular values, scalars, statuses)
-    // (+ with pipelined sweeps: kPool core buffers, 10 r x r matrices and
-    // 16 device words)
+    // (+ with pipelined sweeps: kPool core buffers, 5 kDepth r x r matrices
+    // and 8 kDepth device words)
     static size_t workspace_bytes(int d, int rmax, size_t cap, size_t es, bool pipelined = false) {
         auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
         const size_t rr = (size_t)rmax * rmax;
         const size_t base = (d + 1) * al(cap * es) + (12 + d) * al(rr * es) + al(2 * rr * sizeof(double)) +
                             al(rmax * sizeof(double)) + al(16 * sizeof(double)) +
                             al((16 * d + 16) * sizeof(CholStatus));
-        return base + (pipelined ? kPool * al(cap * es) + 10 * al(rr * es) + al(16 * sizeof(double)) : 0);
+        return base + (pipelined ? kPool * al(cap * es) + 5 * kDepth * al(rr * es) + al(8 * kDepth * sizeof(double))
+                                 : 0);
     }
 
     CholStatus* next_st() {
@@ -778,15 +780,17 @@ struct Rounder {
     bool side_used = false;
     bool tail_used = false;
     bool crit2_used = false;
-    static constexpr int kPool = 4;  // two bonds in flight, two fresh cores each
-    std::vector<T*> freeb;           // free core buffers of the pipeline
-    T *Lq[2] = {}, *Tq[2] = {}, *Gq[2] = {}, *Eq[2] = {}, *Rq[2] = {};  // per bond parity
-    double* dq = nullptr;            // device words, 8 per parity
+    static constexpr int kDepth = 3;          // bonds in flight (queued, undecided)
+    static constexpr int kPool = 2 * kDepth;  // two fresh core buffers per bond in flight
+    std::vector<T*> freeb;                    // free core buffers of the pipeline
+    // per slot (bond index mod kDepth): factor, inverse, second Gram, E, L^T
+    T *Lq[kDepth] = {}, *Tq[kDepth] = {}, *Gq[kDepth] = {}, *Eq[kDepth] = {}, *Rq[kDepth] = {};
+    double* dq = nullptr;                     // device words, 8 per slot
     struct HostSlot {
         CholStatus st;
         double w[4];
     };
-    HostSlot* hw = nullptr;  // page-locked mirror of each parity's decision data
+    HostSlot* hw = nullptr;  // page-locked mirror of each slot's decision data
     struct Spec {
         int k = -1, slot = 0;
         T *x_orig = nullptr, *q = nullptr;         // core k before; Q1
@@ -799,6 +803,7 @@ struct Rounder {
         int split = 0;                  // L's columns final at ev_col (0: not blocked)
         cudaEvent_t ev_main = nullptr;  // after the absorb
         cudaEvent_t ev_dec = nullptr;   // after the checks' copies to the host
+        bool side_queued = false;
     };
     T* take() {
         if (freeb.empty()) throw_status(TT_ERR_ARG, "internal: pipeline buffers exhausted");
@@ -909,6 +914,7 @@ struct Rounder {
                                 c->stream));
         s.ev_dec = c->event();
         TT_CUDA(cudaEventRecord(s.ev_dec, c->stream));
+        s.side_queued = true;
     }
     // the first pass's health and ||E||_F of a bond whose data has arrived
     bool first_pass_ok(const Spec& s, double& e) {
@@ -920,22 +926,20 @@ struct Rounder {
         const double ratio_fast = tc ? 10.0 * ug_fast : 100.0 * ug_fast;
         return h.ndrop == 0 && h.min_ratio >= ratio_fast && series_valid(e) && e <= skip_budget;
     }
-    // both streams drain and bond s (and cur, queued after it) is undone
-    void rollback(Spec& s, Spec* cur, bool rl) {
+    // every stream drains and the pending bonds are undone, newest first:
+    // the cores return to the buffers the oldest one started from
+    void rollback_all(std::deque<Spec>& fl, bool rl) {
         join_side();
         c->sync();
-        if (cur) {
-            core[rl ? cur->k - 1 : cur->k + 1] = cur->nb_orig;
-            core[cur->k] = cur->x_orig;  // s.nb_new
-            give(cur->q);
-            give(cur->nb_new);
-            drop_events(*cur);
+        for (auto it = fl.rbegin(); it != fl.rend(); ++it) {
+            Spec& s = *it;
+            core[rl ? s.k - 1 : s.k + 1] = s.nb_orig;
+            core[s.k] = s.x_orig;  // the previous pending bond's nb_new
+            give(s.q);
+            give(s.nb_new);
+            drop_events(s);
         }
-        core[s.k] = s.x_orig;
-        core[rl ? s.k - 1 : s.k + 1] = s.nb_orig;
-        give(s.q);
-        give(s.nb_new);
-        drop_events(s);
+        fl.clear();
     }
 
     // The critical stream's part of bond k: Gram, Cholesky, absorb into
@@ -943,7 +947,7 @@ struct Rounder {
     Spec main_rl(int k) {
         Spec s;
         s.k = k;
-        s.slot = k & 1;
+        s.slot = k % kDepth;
         const int a = r[k];
         const long K = (long)n[k] * r[k + 1];
         const int M = r[k - 1] * n[k - 1];
@@ -992,46 +996,39 @@ struct Rounder {
         return true;
     }
 
-    void settle_rl(Spec& s) {
-        if (resolve_rl(s)) return;
-        rollback(s, nullptr, true);
-        rl_bond(s.k);
-    }
 
-    // Bond k+1's checks are queued after bond k's critical part and read
-    // back while bond k's Cholesky runs
+    // Bond k's checks are queued after bond k-1's critical part; the host
+    // reads them once bond k-2's critical part is queued too, so it waits
+    // for data that arrived a bond earlier while the GPU has two bonds of
+    // critical work ahead of it
     void rl_sweep_pipelined() {
-        Spec prev;
-        bool have = false;
+        std::deque<Spec> fl;  // bonds queued, not yet decided (oldest first)
         int k = d - 1;
-        while (k >= 1) {
-            if ((long)n[k] * r[k + 1] <= r[k]) {
-                if (have) {
-                    side_rl(prev, prev.ev_main, prev.ev_main);
-                    settle_rl(prev);
-                }
-                have = false;
-                rl_bond(k);
+        for (;;) {
+            const bool spec = k >= 1 && (long)n[k] * r[k + 1] > r[k];
+            if (spec) {
+                Spec cur = main_rl(k);
+                if (!fl.empty()) side_rl(fl.back(), cur.ev_mark, last_mark(cur));
+                fl.push_back(cur);
+                --k;
+                if ((int)fl.size() < kDepth) continue;
+            } else if (!fl.empty() && !fl.back().side_queued) {
+                side_rl(fl.back(), fl.back().ev_main, fl.back().ev_main);
+            }
+            if (fl.empty()) {
+                if (k < 1) break;
+                rl_bond(k);  // a rank-cap bond, nothing pending
                 --k;
                 continue;
             }
-            Spec cur = main_rl(k);
-            if (have) {
-                side_rl(prev, cur.ev_mark, last_mark(cur));
-                if (!resolve_rl(prev)) {
-                    rollback(prev, &cur, true);
-                    rl_bond(prev.k);
-                    have = false;
-                    continue;  // bond k again, from the corrected core
-                }
+            const Spec old = fl.front();
+            if (resolve_rl(fl.front())) {
+                fl.pop_front();
+                continue;
             }
-            prev = cur;
-            have = true;
-            --k;
-        }
-        if (have) {
-            side_rl(prev, prev.ev_main, prev.ev_main);
-            settle_rl(prev);
+            rollback_all(fl, true);
+            rl_bond(old.k);
+            k = old.k - 1;  // the bonds after it again, from the corrected cores
         }
         join_side();
     }
@@ -1039,7 +1036,7 @@ struct Rounder {
     Spec main_lr(int k) {
         Spec s;
         s.k = k;
-        s.slot = k & 1;
+        s.slot = k % kDepth;
         const int m = r[k] * n[k];
         const int b = r[k + 1];
         s.x_orig = core[k];
@@ -1098,48 +1095,37 @@ struct Rounder {
         return true;
     }
 
-    void settle_lr(Spec& s, double eps) {
-        if (resolve_lr(s, eps)) return;
-        rollback(s, nullptr, false);
-        lr_bond(s.k, eps);
-        stream_core(s.k);
-    }
 
     void lr_sweep_pipelined(double eps) {
-        Spec prev;
-        bool have = false;
+        std::deque<Spec> fl;  // bonds queued, not yet decided (oldest first)
         int k = 0;
-        while (k + 1 < d) {
-            const bool spec = r[k] * n[k] >= r[k + 1] && !capped(r[k + 1]) && !pend[k + 1];
-            if (!spec) {
-                if (have) {
-                    side_lr(prev, prev.ev_main, prev.ev_main);
-                    settle_lr(prev, eps);
-                }
-                have = false;
-                lr_bond(k, eps);
+        for (;;) {
+            const bool spec = k + 1 < d && r[k] * n[k] >= r[k + 1] && !capped(r[k + 1]) && !pend[k + 1];
+            if (spec) {
+                Spec cur = main_lr(k);
+                if (!fl.empty()) side_lr(fl.back(), cur.ev_mark, last_mark(cur));
+                fl.push_back(cur);
+                ++k;
+                if ((int)fl.size() < kDepth) continue;
+            } else if (!fl.empty() && !fl.back().side_queued) {
+                side_lr(fl.back(), fl.back().ev_main, fl.back().ev_main);
+            }
+            if (fl.empty()) {
+                if (k + 1 >= d) break;
+                lr_bond(k, eps);  // nothing pending: the sequential path
                 stream_core(k);
                 ++k;
                 continue;
             }
-            Spec cur = main_lr(k);
-            if (have) {
-                side_lr(prev, cur.ev_mark, last_mark(cur));
-                if (!resolve_lr(prev, eps)) {
-                    rollback(prev, &cur, false);
-                    lr_bond(prev.k, eps);
-                    stream_core(prev.k);
-                    have = false;
-                    continue;  // bond k again, from the corrected core
-                }
+            const Spec old = fl.front();
+            if (resolve_lr(fl.front(), eps)) {
+                fl.pop_front();
+                continue;
             }
-            prev = cur;
-            have = true;
-            ++k;
-        }
-        if (have) {
-            side_lr(prev, prev.ev_main, prev.ev_main);
-            settle_lr(prev, eps);
+            rollback_all(fl, false);
+            lr_bond(old.k, eps);
+            stream_core(old.k);
+            k = old.k + 1;
         }
         join_side();
         stream_core(d - 1);
