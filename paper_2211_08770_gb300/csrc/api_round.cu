@@ -139,6 +139,7 @@ struct Rounder {
             }
         }
         if (copied) cudaStreamSynchronize(c->copy_stream);
+        if (ev_norm) c->ev_pool.push_back(ev_norm);
         for (cudaEvent_t e : copy_events) c->ev_pool.push_back(e);
         if (ws) c->release(ws, ws_bytes);
         if (ws64) c->release(ws64, ws64_bytes);
@@ -647,6 +648,27 @@ struct Rounder {
         for (int k = d - 1; k >= 1; --k) rl_bond(k);
     }
 
+    // ||core_k||_F^2 into device words and a page-locked word, with an event
+    cudaEvent_t ev_norm = nullptr;
+    void norm_async(int k) {
+        sumsq<T>(*c, (long)r[k] * n[k] * r[k + 1], core[k], dsc + 15);
+        TT_CUDA(cudaMemcpyAsync(&hw[kDepth].w[0], dsc + 15, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        ev_norm = c->event();
+        TT_CUDA(cudaEventRecord(ev_norm, c->stream));
+    }
+    double nrm_ = -1.0;
+    double norm_value() {
+        if (nrm_ >= 0.0) return nrm_;
+        TT_CUDA(cudaEventSynchronize(ev_norm));
+        c->stats.host_syncs++;
+        c->ev_pool.push_back(ev_norm);
+        ev_norm = nullptr;
+        const double h = hw[kDepth].w[0];
+        if (!isfinite(h)) throw_status(TT_ERR_NONFINITE, "NaN or Inf in the tensor");
+        nrm_ = sqrt(h);
+        return nrm_;
+    }
+
     double core_norm(int k) {
         sumsq<T>(*c, (long)r[k] * n[k] * r[k + 1], core[k], dsc + 15);
         double h;
@@ -748,10 +770,6 @@ struct Rounder {
     }
 
     void lr_sweep(double eps) {
-        if (pipe && series && skip_budget > 0.0) {
-            lr_sweep_pipelined(eps);
-            return;
-        }
         for (int k = 0; k + 1 < d; ++k) {
             if (k > 0) stream_core(k - 1);  // final since the last iteration
             lr_bond(k, eps);
@@ -1096,7 +1114,10 @@ struct Rounder {
     }
 
 
-    void lr_sweep_pipelined(double eps) {
+    // eps_per_norm: the threshold over ||x|| (delta / sqrt(d - 1)); ||x|| is
+    // read at the first decision that needs it (norm_async before)
+    void lr_sweep_pipelined(double eps_per_norm) {
+        auto eps = [&]() { return eps_per_norm * norm_value(); };
         std::deque<Spec> fl;  // bonds queued, not yet decided (oldest first)
         int k = 0;
         for (;;) {
@@ -1112,18 +1133,18 @@ struct Rounder {
             }
             if (fl.empty()) {
                 if (k + 1 >= d) break;
-                lr_bond(k, eps);  // nothing pending: the sequential path
+                lr_bond(k, eps());  // nothing pending: the sequential path
                 stream_core(k);
                 ++k;
                 continue;
             }
             const Spec old = fl.front();
-            if (resolve_lr(fl.front(), eps)) {
+            if (resolve_lr(fl.front(), eps())) {
                 fl.pop_front();
                 continue;
             }
             rollback_all(fl, false);
-            lr_bond(old.k, eps);
+            lr_bond(old.k, eps());
             stream_core(old.k);
             k = old.k + 1;
         }
@@ -1259,8 +1280,18 @@ tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_es
         R.skip_budget = (ctx->series_no_skip || ctx->series_force_retry) ? 0.0
                                             : std::min(0.05, (sizeof(T) == 8 ? 1e-14 : 1e-7) / std::max(delta, 1e-300));
         R.rl_sweep();
-        const double nrm = R.core_norm(0);
-        R.lr_sweep(delta * nrm / sqrt((double)(x->d - 1)));
+        double nrm;
+        if (R.pipe && R.series && R.skip_budget > 0.0) {
+            // ||x|| = ||core_1||_F, read by the host only where the
+            // left-to-right sweep first needs its threshold (the sweep's
+            // first bonds are queued meanwhile)
+            R.norm_async(0);
+            R.lr_sweep_pipelined(delta / sqrt((double)(x->d - 1)));
+            nrm = R.norm_value();
+        } else {
+            nrm = R.core_norm(0);
+            R.lr_sweep(delta * nrm / sqrt((double)(x->d - 1)));
+        }
         if (!R.check_all_status()) {
             // a series pass met a Gram too far from I: redo with Cholesky passes
             ctx->stats.series_retries++;

@@ -96,7 +96,11 @@ sgemm_kernel(int M, int N, long K, float alpha, const float* __restrict__ A, lon
     __shared__ __align__(16) float Bs[2][SBK * LD];
     const int tid = threadIdx.x;
     const int tx = CW ? tid >> 4 : tid & 15, ty = CW ? tid & 15 : tid >> 4;
-    const int m0 = blockIdx.y * SBM, n0 = blockIdx.x * SBN;
+    // a lower-triangular op(A) gives the last row tiles the longest
+    // k-ranges: those are dispatched first (blocks start in x-then-y order),
+    // so the short tiles fill the end of the launch instead of the long ones
+    const int by = (MODE == 0 && (tri & TRI_A_LOWER)) ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+    const int m0 = by * SBM, n0 = blockIdx.x * SBN;
     // outputs 4 t.. precede 64 + 4 t.., so the first group decides
     const bool live = CW ? (n0 + 4 * tx < N) : (m0 + 4 * ty < M);
     long kbeg = 0, kend = K;
