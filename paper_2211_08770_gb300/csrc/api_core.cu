@@ -617,6 +617,10 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     // multiple of 32; 0 or unset: the per-order table)
     const char* nb = getenv("TTGB_CHOL_NB");
     if (nb) c->chol_nb = std::max(0, atoi(nb));
+    // TTGB_COLGRAM_STAGES=3 keeps three raw staging stages in the tensor-core
+    // column Gram (default five)
+    const char* cg = getenv("TTGB_COLGRAM_STAGES");
+    if (cg && cg[0] == '3') c->colgram_stages = 3;
     // TTGB_SERIES_PASS=0 keeps the Cholesky factorization for every second
     // Cholesky QR pass (no series pass); =retry treats every series pass as
     // invalid, so each rounding is redone with Cholesky passes (exercises

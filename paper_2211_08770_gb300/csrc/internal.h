@@ -267,6 +267,7 @@ struct Ctx {
     std::vector<Ctx*> lanes;      // lanes owned by this root (created on demand)
     int max_lanes = 8;            // concurrency of tt_round_batched
     int chol_nb = 0;              // block size of chol_inv (0: the per-order table)
+    int colgram_stages = 5;       // raw staging stages of the tensor-core column Gram (3 or 5)
     bool use_series = true;       // series second pass of Cholesky QR when it is accurate
     bool series_force_retry = false;  // treat series passes as invalid (tests the retry)
     bool series_no_skip = false;      // run every second pass (tests the series pass itself)

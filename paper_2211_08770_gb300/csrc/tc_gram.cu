@@ -176,8 +176,12 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int nt
 // converter warps round them to TF32 and write them transposed into the
 // K-major 128-byte-swizzled layout (column i of X becomes MMA row i), so the
 // MMA sees the same operand form as in the row Gram.
-constexpr int CSTG = 3, COP = 2;
+// CSTG raw staging stages (a template argument: 3 or 5; five keep about
+// 160 KB of loads in flight per SM, three 96 KB), COP converted operand
+// stages
+constexpr int COP = 2;
 
+template <int CSTG>
 struct __align__(8) ColCtl {
     uint64_t stg_full[CSTG], stg_empty[CSTG];
     uint64_t op_full[COP], op_empty[COP];
@@ -191,9 +195,11 @@ __device__ __forceinline__ uint32_t rna_tf32_bits(float x) {
     return r;
 }
 
+template <int CSTG>
 __global__ void __launch_bounds__(192, 1)
 gram_cols_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long m, int ntiles, long kchunk_steps,
                       float* __restrict__ G, int* __restrict__ err) {
+    using ColCtl = ColCtl<CSTG>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* opr = base;                           // [COP][A, B] swizzled TF32 tiles
@@ -424,12 +430,19 @@ bool gram_cols_tc_tf32(Ctx& c, int n, long m, const float* X, long ldx, float* G
     splits = (ksteps + kchunk - 1) / kchunk;
     const long blocks = (long)ntri * splits;
     if (blocks > 2147483647L) return false;
-    const size_t smem = 1024 + (COP + CSTG) * 2 * TILE_BYTES + sizeof(ColCtl) + 64;
-    static std::atomic<bool> attr{false};
-    set_smem_once(attr, gram_cols_tf32_kernel, (int)smem);
     TT_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n * n, c.stream));
     ProfScope ps(c, "gram_tf32_tc", (double)n * (n + 1) * (double)m, 4.0 * (double)n * m + 4.0 * n * n);
-    gram_cols_tf32_kernel<<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, m, ntiles, kchunk, G, c.tc_err);
+    if (c.colgram_stages == 3) {
+        const size_t smem = 1024 + (COP + 3) * 2 * TILE_BYTES + sizeof(ColCtl<3>) + 64;
+        static std::atomic<bool> attr{false};
+        set_smem_once(attr, gram_cols_tf32_kernel<3>, (int)smem);
+        gram_cols_tf32_kernel<3><<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, m, ntiles, kchunk, G, c.tc_err);
+    } else {
+        const size_t smem = 1024 + (COP + 5) * 2 * TILE_BYTES + sizeof(ColCtl<5>) + 64;  // 225 KB
+        static std::atomic<bool> attr{false};
+        set_smem_once(attr, gram_cols_tf32_kernel<5>, (int)smem);
+        gram_cols_tf32_kernel<5><<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, m, ntiles, kchunk, G, c.tc_err);
+    }
     TT_LAUNCHED(c);
     return true;
 }

@@ -8,6 +8,8 @@ profiling it in isolation (e.g. under ncu):
     python -m paper_2211_08770_gb300.kernel_driver rgemm  # r x r product, 400 x 400 x 400 (FP32)
     python -m paper_2211_08770_gb300.kernel_driver matvec # Laplacian TT-matrix x rank-400 TT (d = 5, n = 64)
     python -m paper_2211_08770_gb300.kernel_driver dotstack  # CGS2 passes against 48 rank-4 vectors (stacked dots)
+    python -m paper_2211_08770_gb300.kernel_driver grams  # event times of the row and column tensor-core Grams
+                                                          # at 400 x 25600 (column Gram with 3 and 5 staging stages)
     python -m paper_2211_08770_gb300.kernel_driver pipeline  # single-rounding step, sweeps pipelined vs sequential:
                                                              # ms per step and in-step device time per kernel family
 
@@ -65,11 +67,45 @@ def main(which, r=400, K=25600, n=256):
         T.tt_orthogonalize(c, "cgs2", A, 1e-6)
     elif which == "pipeline":
         pipeline_families()
+    elif which == "grams":
+        gram_times()
     else:
-        raise SystemExit("usage: kernel_driver gemm|gram|chol|chol400|rgemm|matvec|dotstack|pipeline")
+        raise SystemExit("usage: kernel_driver gemm|gram|chol|chol400|rgemm|matvec|dotstack|pipeline|grams")
     torch.cuda.synchronize()
     c.close()
     print("ok", which)
+
+
+def gram_times(reps=20, r=400, K=25600):
+    """Microseconds per call (CUDA events, mean of reps after a warm-up) of
+    the tensor-core row Gram X X^T (X r x K) and column Gram Y^T Y (Y K x r),
+    the latter with 3 and 5 raw staging stages (TTGB_COLGRAM_STAGES)."""
+    import json
+    import os
+    rng = np.random.default_rng(0)
+    X = torch.tensor(rng.standard_normal((r, K)), dtype=torch.float32, device="cuda")
+    Y = X.t().contiguous()
+    G = torch.empty((r, r), dtype=torch.float32, device="cuda")
+    out = {}
+    for stages in ("3", "5"):
+        os.environ["TTGB_COLGRAM_STAGES"] = stages
+        c = T.Ctx(0, "mixed_tf32")
+        for name, call in (("row", lambda: T.tt_gram_f32(c, r, K, X.data_ptr(), K, G.data_ptr(), 1)),
+                           ("col", lambda: T.tt_gram_f32(c, r, K, Y.data_ptr(), r, G.data_ptr(), 2))):
+            if name == "row" and stages == "3":
+                continue
+            call()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            out["%s%s" % (name, "" if name == "row" else "_stages" + stages)] = 1e3 * e0.elapsed_time(e1) / reps
+        c.close()
+    os.environ.pop("TTGB_COLGRAM_STAGES", None)
+    print(json.dumps(out))
 
 
 def pipeline_families(steps=10):
