@@ -8,7 +8,8 @@
 // G.  Warp 0 issues TMA loads of 128 x 32 FP32 boxes (128-byte swizzle) into
 // a 5-stage ring; warp 1 allocates 128 TMEM columns and issues 4 MMAs of
 // 128 x 128 x 8 per stage; warps 2-5 read the accumulator back with
-// tcgen05.ld.  Every mbarrier wait is bounded (the context's limit, about
+// tcgen05.ld and add it into G through shared memory, one row segment per
+// warp instruction.  Every mbarrier wait is bounded (the context's limit, about
 // 2 s by default); a timeout sets *err and the CTA winds down: it stops
 // issuing work, lets the copies already issued land and waits for its MMAs
 // (both with the long limit), and always frees TMEM.
@@ -39,6 +40,31 @@ struct __align__(8) GramSmem {
     uint64_t done;
     uint32_t tmem_base;
 };
+
+// Adds the 32 x 128 block of this CTA's accumulator held in TMEM lanes
+// [32 q, 32 q + 32) (taddr = its first column) into G[row0 + i][col0 + j]
+// (n x n, row-major), clipped to n.  Each 32 x 32 piece goes through a
+// padded shared-memory stage (stg: 32 x 33 floats of this warp), so that one
+// warp instruction adds 32 consecutive floats of one row (one cache line)
+// instead of one float of 32 rows.
+__device__ __forceinline__ void add_block_rows(uint32_t taddr, float* stg, float* __restrict__ G, int n, int row0,
+                                               int col0, int lane) {
+    float v[32];
+#pragma unroll 1
+    for (int c = 0; c < TB / 32; ++c) {
+        __syncwarp();
+        tc::tmem_ld32(taddr + c * 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
+        __syncwarp();
+        const int col = col0 + c * 32 + lane;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+            const int row = row0 + i;
+            if (row < n && col < n) atomicAdd(&G[(long)row * n + col], stg[i * 33 + lane]);
+        }
+    }
+}
 
 __global__ void __launch_bounds__(192, 1)
 gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int ntiles, long kchunk_steps,
@@ -140,21 +166,9 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int nt
             if (lane == 0) atomicExch(err, 1);
         } else if (e == 0) {
             tc::tc_fence_after();
-            const int row = ti * TB + q * 32 + lane;
-            float v[32];
-#pragma unroll 1
-            for (int c = 0; c < TB / 32; ++c) {
-                __syncwarp();
-                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c * 32, v);
-                if (row < n) {
-                    const int col0 = tj * TB + c * 32;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = col0 + j;
-                        if (col < n) atomicAdd(&G[(long)row * n + col], v[j]);
-                    }
-                }
-            }
+            // every MMA has completed (done): the operand ring is free
+            float* stg = reinterpret_cast<float*>(ring) + q * 32 * 33;
+            add_block_rows(tmem + ((uint32_t)(q * 32) << 16), stg, G, n, ti * TB + q * 32, tj * TB, lane);
         }
     }
     // the MMA issuer makes sure its MMAs have finished before TMEM is freed
@@ -321,19 +335,10 @@ gram_cols_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long m, i
             if (lane == 0) atomicExch(err, 1);
         } else if (e == 0) {
             tc::tc_fence_after();
-            const int row = ti * TB + q * 32 + lane;
-            float v[32];
-#pragma unroll 1
-            for (int c = 0; c < TB / 32; ++c) {
-                __syncwarp();
-                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c * 32, v);
-                if (row < n) {
-                    const int col0 = tj * TB + c * 32;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (col0 + j < n) atomicAdd(&G[(long)row * n + col0 + j], v[j]);
-                }
-            }
+            // every MMA has completed (done) and every staged box was
+            // converted: the operand and staging smem is free
+            float* stg = reinterpret_cast<float*>(base) + q * 32 * 33;
+            add_block_rows(tmem + ((uint32_t)(q * 32) << 16), stg, G, n, ti * TB + q * 32, tj * TB, lane);
         }
     }
     if (warp == 1 && lane == 0 && nsteps > 0) tc::mbar_wait_bounded(&ctl->done, 0, WAIT_LIMIT);
