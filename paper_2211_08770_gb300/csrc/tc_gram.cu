@@ -203,10 +203,12 @@ struct __align__(8) ColCtl {
     uint32_t tmem_base;
 };
 
-__device__ __forceinline__ uint32_t rna_tf32_bits(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
+// x rounded to TF32 (10 explicit mantissa bits), to nearest with ties away
+// from zero: half of the dropped 13 bits' unit added to the magnitude, then
+// the dropped bits cleared (a carry moves into the exponent as it should).
+// Finite inputs only matter: a NaN may come out as Inf, still non-finite.
+__device__ __forceinline__ float rna_tf32(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 template <int CSTG>
@@ -305,21 +307,23 @@ gram_cols_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long m, i
             if (!ok) break;
             const float* sA = reinterpret_cast<const float*>(stg + s * 2 * TILE_BYTES);  // [32 k][128 i]
             unsigned char* dA = opr + o * 2 * TILE_BYTES;
+            // thread t converts row t of each 128 x 32 operand tile: column
+            // t of the raw box, k = 4 c .. 4 c + 3 into 16-byte chunk c of
+            // the swizzled row.  Every load of a tile is issued before its
+            // stores (the compiler cannot reorder them: both are shared
+            // memory), so one warp per scheduler has 32 loads in flight.
             const int ntile_op = diag ? 1 : 2;
             for (int u = 0; u < ntile_op; ++u) {
-                const float* src = sA + u * (TILE_BYTES / 4);
-                unsigned char* dst = dA + u * TILE_BYTES;
+                const float* src = sA + u * (TILE_BYTES / 4) + t;
+                unsigned char* dst = dA + u * TILE_BYTES + t * 128;
+                float r[32];
 #pragma unroll
-                for (int qq = 0; qq < 8; ++qq) {
-                    const int idx = qq * 128 + t;
-                    const int ii = idx & 127, c4 = idx >> 7;
-                    const float* col = src + (c4 * 4) * TB + ii;
-                    const float4 v = make_float4(__uint_as_float(rna_tf32_bits(col[0])),
-                                                 __uint_as_float(rna_tf32_bits(col[TB])),
-                                                 __uint_as_float(rna_tf32_bits(col[2 * TB])),
-                                                 __uint_as_float(rna_tf32_bits(col[3 * TB])));
-                    *reinterpret_cast<float4*>(dst + ii * 128 + ((c4 ^ (ii & 7)) << 4)) = v;
-                }
+                for (int k = 0; k < 32; ++k) r[k] = src[k * TB];
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    *reinterpret_cast<float4*>(dst + ((c ^ (t & 7)) << 4)) =
+                        make_float4(rna_tf32(r[4 * c]), rna_tf32(r[4 * c + 1]), rna_tf32(r[4 * c + 2]),
+                                    rna_tf32(r[4 * c + 3]));
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc::mbar_arrive(&ctl->op_full[o]);
