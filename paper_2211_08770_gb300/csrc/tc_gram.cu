@@ -186,10 +186,11 @@ gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long K, int nt
 // ---------------------------------------------------------------------------
 // G = X^T X of the columns of X (m x n, row-major, n contiguous): the Gram
 // step of the left-to-right sweep, whose contraction runs over the rows of
-// the left unfolding.  TMA brings raw 32-row x 128-column FP32 boxes; the
-// converter warps round them to TF32 and write them transposed into the
-// K-major 128-byte-swizzled layout (column i of X becomes MMA row i), so the
-// MMA sees the same operand form as in the row Gram.
+// the left unfolding.  TMA brings raw 32-row x 128-column FP32 boxes; eight
+// converter warps (two per scheduler) round them to TF32 and write them
+// transposed into the K-major 128-byte-swizzled layout (column i of X
+// becomes MMA row i), so the MMA sees the same operand form as in the row
+// Gram; four of them then read the accumulator back.
 // CSTG raw staging stages (a template argument: 3 or 5; five keep about
 // 160 KB of loads in flight per SM, three 96 KB), COP converted operand
 // stages
@@ -211,8 +212,10 @@ __device__ __forceinline__ float rna_tf32(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
+constexpr int CCONV = 256;  // converter threads (warps 2-9, two per scheduler)
+
 template <int CSTG>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(64 + CCONV, 1)
 gram_cols_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long m, int ntiles, long kchunk_steps,
                       float* __restrict__ G, int* __restrict__ err) {
     using ColCtl = ColCtl<CSTG>;
@@ -237,10 +240,10 @@ gram_cols_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long m, i
     if (threadIdx.x == 0) {
         for (int s = 0; s < CSTG; ++s) {
             tc::mbar_init(&ctl->stg_full[s], 1);
-            tc::mbar_init(&ctl->stg_empty[s], 128);
+            tc::mbar_init(&ctl->stg_empty[s], CCONV);
         }
         for (int s = 0; s < COP; ++s) {
-            tc::mbar_init(&ctl->op_full[s], 128);
+            tc::mbar_init(&ctl->op_full[s], CCONV);
             tc::mbar_init(&ctl->op_empty[s], 1);
         }
         tc::mbar_init(&ctl->done, 1);
@@ -307,21 +310,22 @@ gram_cols_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long m, i
             if (!ok) break;
             const float* sA = reinterpret_cast<const float*>(stg + s * 2 * TILE_BYTES);  // [32 k][128 i]
             unsigned char* dA = opr + o * 2 * TILE_BYTES;
-            // thread t converts row t of each 128 x 32 operand tile: column
-            // t of the raw box, k = 4 c .. 4 c + 3 into 16-byte chunk c of
-            // the swizzled row.  Every load of a tile is issued before its
-            // stores (the compiler cannot reorder them: both are shared
-            // memory), so one warp per scheduler has 32 loads in flight.
+            // thread t converts half h = t / 128 of row i = t % 128 of each
+            // 128 x 32 operand tile: column i of the raw box, k = 4 c .. 4 c
+            // + 3 into 16-byte chunk c of the swizzled row, c = 4 h .. 4 h + 3.
+            // Every load of a tile is issued before its stores (the compiler
+            // cannot reorder them: both are shared memory).
+            const int i = t & 127, h = t >> 7;
             const int ntile_op = diag ? 1 : 2;
             for (int u = 0; u < ntile_op; ++u) {
-                const float* src = sA + u * (TILE_BYTES / 4) + t;
-                unsigned char* dst = dA + u * TILE_BYTES + t * 128;
-                float r[32];
+                const float* src = sA + u * (TILE_BYTES / 4) + i + 16 * h * TB;
+                unsigned char* dst = dA + u * TILE_BYTES + i * 128;
+                float r[16];
 #pragma unroll
-                for (int k = 0; k < 32; ++k) r[k] = src[k * TB];
+                for (int k = 0; k < 16; ++k) r[k] = src[k * TB];
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    *reinterpret_cast<float4*>(dst + ((c ^ (t & 7)) << 4)) =
+                for (int c = 0; c < 4; ++c)
+                    *reinterpret_cast<float4*>(dst + (((4 * h + c) ^ (i & 7)) << 4)) =
                         make_float4(rna_tf32(r[4 * c]), rna_tf32(r[4 * c + 1]), rna_tf32(r[4 * c + 2]),
                                     rna_tf32(r[4 * c + 3]));
             }
@@ -330,19 +334,22 @@ gram_cols_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, long m, i
             tc::mbar_arrive(&ctl->stg_empty[s]);
         }
         if (!ok && lane == 0) atomicExch(err, 1);
-        const int q = warp & 3;
-        const bool got = __all_sync(0xffffffffu, ok && tc::mbar_wait_bounded(&ctl->done, 0, 2 * WAIT_LIMIT));
-        int e = 0;
-        if (lane == 0) e = *(volatile int*)err;
-        e = __shfl_sync(0xffffffffu, e, 0);
-        if (!got) {
-            if (lane == 0) atomicExch(err, 1);
-        } else if (e == 0) {
-            tc::tc_fence_after();
-            // every MMA has completed (done) and every staged box was
-            // converted: the operand and staging smem is free
-            float* stg = reinterpret_cast<float*>(base) + q * 32 * 33;
-            add_block_rows(tmem + ((uint32_t)(q * 32) << 16), stg, G, n, ti * TB + q * 32, tj * TB, lane);
+        if (warp < 6) {
+            // epilogue on warps 2-5 (TMEM lane quarter = warp % 4)
+            const int q = warp & 3;
+            const bool got = __all_sync(0xffffffffu, ok && tc::mbar_wait_bounded(&ctl->done, 0, 2 * WAIT_LIMIT));
+            int e = 0;
+            if (lane == 0) e = *(volatile int*)err;
+            e = __shfl_sync(0xffffffffu, e, 0);
+            if (!got) {
+                if (lane == 0) atomicExch(err, 1);
+            } else if (e == 0) {
+                tc::tc_fence_after();
+                // every MMA has completed (done) and every staged box was
+                // converted: the operand and staging smem is free
+                float* stg = reinterpret_cast<float*>(base) + q * 32 * 33;
+                add_block_rows(tmem + ((uint32_t)(q * 32) << 16), stg, G, n, ti * TB + q * 32, tj * TB, lane);
+            }
         }
     }
     if (warp == 1 && lane == 0 && nsteps > 0) tc::mbar_wait_bounded(&ctl->done, 0, WAIT_LIMIT);
@@ -445,12 +452,12 @@ bool gram_cols_tc_tf32(Ctx& c, int n, long m, const float* X, long ldx, float* G
         const size_t smem = 1024 + (COP + 3) * 2 * TILE_BYTES + sizeof(ColCtl<3>) + 64;
         static std::atomic<bool> attr{false};
         set_smem_once(attr, gram_cols_tf32_kernel<3>, (int)smem);
-        gram_cols_tf32_kernel<3><<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, m, ntiles, kchunk, G, c.tc_err);
+        gram_cols_tf32_kernel<3><<<(unsigned)blocks, 64 + CCONV, smem, c.stream>>>(map, n, m, ntiles, kchunk, G, c.tc_err);
     } else {
         const size_t smem = 1024 + (COP + 5) * 2 * TILE_BYTES + sizeof(ColCtl<5>) + 64;  // 225 KB
         static std::atomic<bool> attr{false};
         set_smem_once(attr, gram_cols_tf32_kernel<5>, (int)smem);
-        gram_cols_tf32_kernel<5><<<(unsigned)blocks, 192, smem, c.stream>>>(map, n, m, ntiles, kchunk, G, c.tc_err);
+        gram_cols_tf32_kernel<5><<<(unsigned)blocks, 64 + CCONV, smem, c.stream>>>(map, n, m, ntiles, kchunk, G, c.tc_err);
     }
     TT_LAUNCHED(c);
     return true;
