@@ -119,9 +119,38 @@ struct Rounder {
             dq = (double*)p;
             hw = static_cast<HostSlot*>(c->pinned_words());
         }
-        for (int k = 0; k < d; ++k)
+        // the right-to-left sweep starts at the last cores: with the
+        // pipeline, cores d-3 .. 0 are copied on the second stream (last
+        // first) while the first bonds run, each bond waiting for the
+        // copies of the cores it touches
+        const int side_from = pipe ? d - 3 : -1;
+        for (int k = d - 1; k > side_from; --k)
             TT_CUDA(cudaMemcpyAsync(core[k], x->cores[k], sizeof(T) * x->core_elems(k), cudaMemcpyDeviceToDevice,
                                     c->stream));
+        if (side_from >= 0) {
+            copy_ev.assign(d, nullptr);
+            cudaEvent_t start = c->event();
+            TT_CUDA(cudaEventRecord(start, c->stream));
+            OnSide os(c);
+            side_used = true;
+            TT_CUDA(cudaStreamWaitEvent(c->stream, start, 0));
+            c->ev_pool.push_back(start);
+            for (int k = side_from; k >= 0; --k) {
+                TT_CUDA(cudaMemcpyAsync(core[k], x->cores[k], sizeof(T) * x->core_elems(k),
+                                        cudaMemcpyDeviceToDevice, c->stream));
+                copy_ev[k] = c->event();
+                TT_CUDA(cudaEventRecord(copy_ev[k], c->stream));
+            }
+        }
+    }
+
+    // the critical stream waits for core k's copy (pipelined construction)
+    std::vector<cudaEvent_t> copy_ev;
+    void await_core(int k) {
+        if (k < 0 || k >= (int)copy_ev.size() || !copy_ev[k]) return;
+        TT_CUDA(cudaStreamWaitEvent(c->stream, copy_ev[k], 0));
+        c->ev_pool.push_back(copy_ev[k]);
+        copy_ev[k] = nullptr;
     }
     ~Rounder() {
         // the second stream's work and the host copies still reading the
@@ -140,6 +169,8 @@ struct Rounder {
         }
         if (copied) cudaStreamSynchronize(c->copy_stream);
         if (ev_norm) c->ev_pool.push_back(ev_norm);
+        for (cudaEvent_t e : copy_ev)
+            if (e) c->ev_pool.push_back(e);
         for (cudaEvent_t e : copy_events) c->ev_pool.push_back(e);
         if (ws) c->release(ws, ws_bytes);
         if (ws64) c->release(ws64, ws64_bytes);
@@ -623,6 +654,8 @@ struct Rounder {
     // bond k of the right-to-left sweep: core k orthonormalized, its factor
     // absorbed into core k-1
     void rl_bond(int k) {
+        await_core(k);
+        await_core(k - 1);
         const int a = r[k];
         const long K = (long)n[k] * r[k + 1];
         const int M = r[k - 1] * n[k - 1];
@@ -963,6 +996,8 @@ struct Rounder {
     // The critical stream's part of bond k: Gram, Cholesky, absorb into
     // core k-1 (a fresh buffer)
     Spec main_rl(int k) {
+        await_core(k);
+        await_core(k - 1);
         Spec s;
         s.k = k;
         s.slot = k % kDepth;
