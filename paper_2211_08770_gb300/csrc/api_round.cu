@@ -977,6 +977,16 @@ struct Rounder {
         const double ratio_fast = tc ? 10.0 * ug_fast : 100.0 * ug_fast;
         return h.ndrop == 0 && h.min_ratio >= ratio_fast && series_valid(e) && e <= skip_budget;
     }
+    // returns the events of bonds still queued when a sweep is left by an
+    // exception (a normal exit leaves none)
+    struct EventGuard {
+        Rounder* R;
+        std::deque<Spec>* fl;
+        ~EventGuard() {
+            for (Spec& s : *fl) R->drop_events(s);
+        }
+    };
+
     // every stream drains and the pending bonds are undone, newest first:
     // the cores return to the buffers the oldest one started from
     void rollback_all(std::deque<Spec>& fl, bool rl) {
@@ -1056,6 +1066,7 @@ struct Rounder {
     // critical work ahead of it
     void rl_sweep_pipelined() {
         std::deque<Spec> fl;  // bonds queued, not yet decided (oldest first)
+        EventGuard eg{this, &fl};
         int k = d - 1;
         for (;;) {
             const bool spec = k >= 1 && (long)n[k] * r[k + 1] > r[k];
@@ -1154,6 +1165,7 @@ struct Rounder {
     void lr_sweep_pipelined(double eps_per_norm) {
         auto eps = [&]() { return eps_per_norm * norm_value(); };
         std::deque<Spec> fl;  // bonds queued, not yet decided (oldest first)
+        EventGuard eg{this, &fl};
         int k = 0;
         for (;;) {
             const bool spec = k + 1 < d && r[k] * n[k] >= r[k + 1] && !capped(r[k + 1]) && !pend[k + 1];
