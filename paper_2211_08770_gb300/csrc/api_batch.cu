@@ -48,6 +48,7 @@ std::vector<Ctx*> get_lanes(Ctx& root, int count) {
         l->use_tc_absorb = root.use_tc_absorb;
         l->chol_nb = root.chol_nb;
         l->colgram_stages = root.colgram_stages;
+        l->pipeline = root.pipeline;
         l->use_series = root.use_series;
         l->series_force_retry = root.series_force_retry;
         l->series_no_skip = root.series_no_skip;

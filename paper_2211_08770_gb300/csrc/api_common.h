@@ -59,7 +59,11 @@ tt_tensor* orth_step_internal(tt_ctx* ctx, tt_scheme scheme, double delta, tt_ro
                               const tt_tensor* a, int k, const tt_tensor* const* Q, double* col, int* nrounds,
                               const double* qgram = nullptr, int ldg = 0);
 // device bytes a rounding of x may hold at once: workspace plus output
-size_t round_footprint(const tt_tensor* x, tt_precision prec);
+// device bytes a rounding of x may hold at once (its workspace, with the
+// pipeline's buffers when pipelined, and its output)
+size_t round_footprint(const tt_tensor* x, tt_precision prec, bool pipelined);
+// whether roundings on ctx run the pipelined sweeps
+bool pipeline_on(const Ctx* ctx);
 void round_batched_internal(tt_ctx* ctx, int count, const tt_tensor* const* x, const double* delta, tt_tensor** out);
 
 // RAII owner for tensors created inside drivers

@@ -634,6 +634,11 @@ tt_status tt_ctx_create(tt_ctx** out, int device, tt_precision prec, void* strea
     // alone (no speculative overlap)
     const char* pl = getenv("TTGB_PIPELINE");
     if (pl && pl[0] == '0') c->pipeline = false;
+    // TTGB_LANE_PIPELINE=1: the lanes of batched rounding and of the server
+    // pipeline their sweeps as well (with the extra workspace in their
+    // footprints)
+    const char* lp = getenv("TTGB_LANE_PIPELINE");
+    if (lp && lp[0] == '1') c->lane_pipeline = true;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;

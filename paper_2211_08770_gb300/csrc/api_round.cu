@@ -1302,8 +1302,7 @@ tt_tensor* round_t(tt_ctx* ctx, const tt_tensor* x, double delta, double* err_es
         // where they run), and only where second passes may be skipped; the
         // sweeps then run on the context's critical stream, ordered after
         // and before the caller's
-        const bool pipe = attempt == 0 && ctx->pipeline && !ctx->root && !(ctx->prof && ctx->prof_only.empty()) &&
-                          ctx->use_series && !ctx->series_no_skip && !ctx->series_force_retry;
+        const bool pipe = attempt == 0 && pipeline_on(ctx);
         OnCritStream cs(ctx, pipe);
         std::unique_ptr<Rounder<T>> Rp;
         try {
@@ -1369,7 +1368,16 @@ double norm_t(tt_ctx* ctx, const tt_tensor* x) {
 
 }  // namespace
 
-size_t round_footprint(const tt_tensor* x, tt_precision prec) {
+// whether a rounding on this context runs the pipelined sweeps (the
+// retries after an invalid series pass never do)
+bool pipeline_on(const Ctx* ctx) {
+    const Ctx* root = ctx->root ? ctx->root : ctx;
+    if (!root->pipeline || (ctx->root && !root->lane_pipeline)) return false;
+    return !(ctx->prof && ctx->prof_only.empty()) && ctx->use_series && !ctx->series_no_skip &&
+           !ctx->series_force_retry;
+}
+
+size_t round_footprint(const tt_tensor* x, tt_precision prec, bool pipelined) {
     const size_t es = prec == TT_FP64 ? 8 : 4;
     int rmax = 1;
     size_t cap = 1, out = 0;
@@ -1378,8 +1386,8 @@ size_t round_footprint(const tt_tensor* x, tt_precision prec) {
         cap = std::max(cap, x->core_elems(k));
         out += (x->core_elems(k) * es + 255) & ~size_t(255);  // ranks never grow
     }
-    const size_t ws = es == 8 ? Rounder<double>::workspace_bytes(x->d, rmax, cap, es)
-                              : Rounder<float>::workspace_bytes(x->d, rmax, cap, es) +
+    const size_t ws = es == 8 ? Rounder<double>::workspace_bytes(x->d, rmax, cap, es, pipelined)
+                              : Rounder<float>::workspace_bytes(x->d, rmax, cap, es, pipelined) +
                                     Rounder<float>::fallback64_bytes(rmax, cap);
     return ws + out;
 }

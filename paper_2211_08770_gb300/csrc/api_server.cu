@@ -105,7 +105,8 @@ struct tt_server {
     // footprint bound of a request (bytes it may hold at once on the device)
     size_t bound_of(const Request& q) const {
         const size_t es = root->prec == TT_FP64 ? 8 : 4;
-        if (q.kind == TT_REQ_ROUND) return round_footprint(q.x, root->prec) + (1u << 20);
+        const bool pipe = root->pipeline && root->lane_pipeline;
+        if (q.kind == TT_REQ_ROUND) return round_footprint(q.x, root->prec, pipe) + (1u << 20);
         // the concatenated sum x - sum_j r_j q_j: ranks add up bond by bond
         const tt_tensor* x = q.x;
         const std::vector<tt_tensor*>& B = bases[q.basis].q;
@@ -119,7 +120,7 @@ struct tt_server {
         const size_t sb = tensor_bytes(&S, es);
         // the running sum and its successor (MGS), the rounding of the sum,
         // the normalised copy, and FP64 copies for the projections when FP32
-        size_t b = 2 * sb + round_footprint(&S, root->prec) + sb;
+        size_t b = 2 * sb + round_footprint(&S, root->prec, pipe) + sb;
         if (es == 4) b += 2 * tensor_bytes(&S, 8);
         // the stacked dots of a pass (x at most the concatenation's ranks)
         size_t wmax = 1, vmax = 1, pmax = 1;

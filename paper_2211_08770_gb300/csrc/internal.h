@@ -279,6 +279,7 @@ struct Ctx {
     // stream, the applies and second-pass checks on a second stream, and
     // the host reads each bond's decision from page-locked words
     bool pipeline = true;
+    bool lane_pipeline = false;  // lanes (batched, serving) pipeline their roundings too
     // when set, the next chol_inv records it on the stream just before its
     // first single-CTA tile kernel (after the factor's preparation), then
     // clears it: the pipelined sweeps release the previous bond's checks
