@@ -172,7 +172,9 @@ tt_status tt_ctx_set_tc_wait_limit(tt_ctx* ctx, long long cycles);
  * alone; timing one family keeps the pipeline, and its launches' events
  * are recorded on the stream each runs on.  The rounding stays ordered on the
  * context's stream: its internal streams wait for it and it waits for
- * them. */
+ * them.  Lanes of tt_round_batched and of the server run the sequential
+ * sweeps unless TTGB_LANE_PIPELINE=1 was set when the context was created
+ * (the lanes already overlap whole roundings). */
 tt_status tt_ctx_set_pipeline(tt_ctx* ctx, int on);
 
 /* Enables (on != 0) or disables event timing of the library's launches. */
