@@ -8,6 +8,8 @@ profiling it in isolation (e.g. under ncu):
     python -m paper_2211_08770_gb300.kernel_driver rgemm  # r x r product, 400 x 400 x 400 (FP32)
     python -m paper_2211_08770_gb300.kernel_driver matvec # Laplacian TT-matrix x rank-400 TT (d = 5, n = 64)
     python -m paper_2211_08770_gb300.kernel_driver dotstack  # CGS2 passes against 48 rank-4 vectors (stacked dots)
+    python -m paper_2211_08770_gb300.kernel_driver dots   # stacked multi-dot: the Gram of 64 resident rank-60 TTs
+                                                          # (d = 10, n = 64) by tt_server_add_basis, mixed
     python -m paper_2211_08770_gb300.kernel_driver grams  # event times of the row and column tensor-core Grams
                                                           # at 400 x 25600 (column Gram with 3 and 5 staging stages)
     python -m paper_2211_08770_gb300.kernel_driver pipeline  # single-rounding step, sweeps pipelined vs sequential:
@@ -69,8 +71,23 @@ def main(which, r=400, K=25600, n=256):
         pipeline_families()
     elif which == "grams":
         gram_times()
+    elif which == "dots":
+        from ttinputs import random_tt
+        Y = [T.tt_tensor_create(c, random_tt(rng, [64] * 10, [1] + [60] * 9 + [1], scale="unit-core"))
+             for _ in range(64)]
+        srv = T.Server(c, workers=1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        srv.add_basis(Y)
+        e1.record()
+        torch.cuda.synchronize()
+        print("add_basis of 64 rank-60 TTs: %.3f ms" % e0.elapsed_time(e1))
+        srv.close()
+        for y in Y:
+            y.free()
     else:
-        raise SystemExit("usage: kernel_driver gemm|gram|chol|chol400|rgemm|matvec|dotstack|pipeline|grams")
+        raise SystemExit("usage: kernel_driver gemm|gram|chol|chol400|rgemm|matvec|dotstack|pipeline|grams|dots")
     torch.cuda.synchronize()
     c.close()
     print("ok", which)
