@@ -415,8 +415,9 @@ void dot_many_f32_acc64(tt_ctx* ctx, const tt_tensor* x, int count, const tt_ten
 // <x, y_j> for all j at once: the contractions of all pairs advance
 // together, core by core.  W (rx x S, FP64) holds the pairs' W_j side by
 // side (S = sum_j ry_j).  Step A: V (rx n x S', storage type) with
-// V[(a n + i), off'_j + q] = sum_b W[a, off_j + b] Y_j(b, i, q) (FP64 sums of
-// ry_j terms).  Step B: W' = X_k^L^T V, one GEMM over all pairs, so X's
+// V[(a n + i), off'_j + q] = sum_b W[a, off_j + b] Y_j(b, i, q) (sums of ry_j
+// terms in the storage type, one small product per pair; FP64 sums in the
+// fallback for very large ranks).  Step B: W' = X_k^L^T V, one GEMM over all pairs, so X's
 // cores are read once for all pairs (the pair-by-pair chains read them once
 // per pair, in two small launches per core each).  FP64 storage: one FP64
 // GEMM.  FP32 storage: FP32 GEMMs over chunks of kDotChunk rows of X^L whose
@@ -454,6 +455,53 @@ __global__ void stack_a_kernel(const double* __restrict__ W, int S, const PairCo
         double acc = 0.0;
         for (int b = 0; b < pc.ry; ++b) acc += w[b] * (double)y[(long)b * n * pc.ry2];
         V[t] = (T)acc;
+    }
+}
+
+// Step A as one small product per pair, V_j = W_j Y_j (rx x n ry2_j): block
+// (x, y) takes 128 columns (i, q) of pair y, thread c one column, and runs
+// over the rows a in chunks of kStackRows with W_j's chunk in shared memory
+// (read by broadcast) and the column of Y_j read once per chunk, so Y_j is
+// read rx / kStackRows times instead of rx times.  Sums in the storage type:
+// FP32 storage sums the ry_j terms in FP32 (the FP32 products of step B sum
+// kDotChunk terms in FP32 as well); FP64 storage in FP64.
+constexpr int kStackRows = 16;
+
+template <class T>
+__global__ void __launch_bounds__(128) stack_a_tiled_kernel(const double* __restrict__ W, int S,
+                                                            const PairCols<T>* __restrict__ pairs, int rx, int n,
+                                                            int S2, T* __restrict__ V) {
+    extern __shared__ __align__(16) unsigned char stack_sm[];
+    T* Ws = reinterpret_cast<T*>(stack_sm);  // kStackRows x ry, row-major
+    const PairCols<T> pc = pairs[blockIdx.y];
+    const int ncols = n * pc.ry2;
+    if ((long)blockIdx.x * blockDim.x >= ncols) return;  // the whole block is past this pair's columns
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = c < ncols;
+    const int i = live ? c / pc.ry2 : 0;
+    const int q = live ? c - i * pc.ry2 : 0;
+    const T* y = pc.y + (long)i * pc.ry2 + q;  // Y(b, i, q) at y[b n ry2]
+    const long ystride = (long)n * pc.ry2;
+    for (int a0 = 0; a0 < rx; a0 += kStackRows) {
+        const int na = min(kStackRows, rx - a0);
+        __syncthreads();  // the previous chunk's W is no longer read
+        for (int e = threadIdx.x; e < kStackRows * pc.ry; e += blockDim.x) {
+            const int aa = e / pc.ry, b = e - aa * pc.ry;
+            Ws[e] = aa < na ? (T)W[(long)(a0 + aa) * S + pc.off + b] : T(0);
+        }
+        __syncthreads();
+        if (!live) continue;
+        T acc[kStackRows];
+#pragma unroll
+        for (int aa = 0; aa < kStackRows; ++aa) acc[aa] = T(0);
+        for (int b = 0; b < pc.ry; ++b) {
+            const T yb = y[(long)b * ystride];
+#pragma unroll
+            for (int aa = 0; aa < kStackRows; ++aa) acc[aa] = fma(Ws[aa * pc.ry + b], yb, acc[aa]);
+        }
+#pragma unroll
+        for (int aa = 0; aa < kStackRows; ++aa)
+            if (aa < na) V[((long)(a0 + aa) * n + i) * S2 + pc.off2 + q] = acc[aa];
     }
 }
 
@@ -525,8 +573,19 @@ void dot_many_stacked(tt_ctx* ctx, const tt_tensor* x, int count, const tt_tenso
         TT_CUDA(cudaMemcpyAsync(dpairs, hp.data(), count * sizeof(PairCols<T>), cudaMemcpyHostToDevice, ctx->stream));
         const long K = (long)rx * n;
         {
+            int rymax = 1, colmax = 1;
+            for (int j = 0; j < count; ++j) {
+                rymax = std::max(rymax, hp[j].ry);
+                colmax = std::max(colmax, n * hp[j].ry2);
+            }
+            const size_t smem = (size_t)kStackRows * rymax * sizeof(T);
             ProfScope ps(*ctx, "dot_stack", 2.0 * (double)K * S2 * 4.0, sizeof(T) * (double)K * S2);
-            stack_a_kernel<T><<<grid_of(*ctx, K * S2, 256), 256, 0, ctx->stream>>>(W, S, dpairs, count, rx, n, S2, V);
+            if (smem <= 48 * 1024 && count <= 65535)
+                stack_a_tiled_kernel<T><<<dim3((unsigned)((colmax + 127) / 128), (unsigned)count), 128, smem,
+                                          ctx->stream>>>(W, S, dpairs, rx, n, S2, V);
+            else
+                stack_a_kernel<T><<<grid_of(*ctx, K * S2, 256), 256, 0, ctx->stream>>>(W, S, dpairs, count, rx, n, S2,
+                                                                                      V);
             TT_LAUNCHED(*ctx);
         }
         const T* X = (const T*)x->cores[k];
