@@ -349,6 +349,7 @@ def run_ours(args):
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "delta": DELTA, "precision": prec, "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "256 MB buffer written between timed steps (working set ~0.5 GB > 129 MB L2)",
+                      "sweeps": "pipelined (three bonds in flight; tt_ctx_set_pipeline)",
                       "output_ranks": main["ranks"]},
            "gpu_launches": int(main["stats"]["kernel_launches"]),
            "host_syncs": int(main["stats"]["host_syncs"]),
